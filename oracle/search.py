@@ -1,0 +1,156 @@
+"""Search definitions: brute-force minimum, three-distance geometry, the
+continued-fraction lower bounds, and difference tables.
+
+TEST INFRASTRUCTURE ONLY (part of the CPU oracle).
+
+The quantity the hot path decides is Eq. (1) of Sect. II-A,
+    min { (b - a x) mod 1 : 0 <= x < N },
+here on integers scaled by a modulus M (M = 2^64 for the search words):
+    min { (B - A x) mod M : 0 <= x < N }.
+`brute_min` is that definition written out.  The other routines are the
+paper's machinery, kept here so the tests can pin it and compare the CUDA
+filter with it value by value:
+
+  gaps_in_order     lengths of the intervals cut by {a x mod 1 : x < n}
+                    (Thm. 1, Fig. 3);
+  cf_configurations the two-length configurations (i, t) with
+                    theta_{i-1,t}, theta_i, q_{i-1,t}, q_i, k_{i+1} (Sect.
+                    II-B recurrences, Table 1, Eq. 2, Property 1);
+  regular_lb        the regular lower bound of Algorithm 2;
+  regular_lb_unrolled
+                    the same computation unrolled twice (Algorithm 4),
+                    with the degenerate endings (a remainder reaching 0
+                    for rational a) made explicit;
+  forward_differences, tabulated_shift, straightforward_shift
+                    Sect. IV difference tables (Figs. 5 and 6).
+"""
+from __future__ import annotations
+
+from math import comb
+from typing import List, Tuple
+
+
+def brute_min(B: int, A: int, n: int, M: int = 1 << 64) -> Tuple[int, int]:
+    """(min, smallest argmin) of (B - A x) mod M over 0 <= x < n."""
+    best, arg = None, 0
+    for x in range(n):
+        v = (B - A * x) % M
+        if best is None or v < best:
+            best, arg = v, x
+    return best, arg
+
+
+def gaps_in_order(a: int, M: int, n: int) -> List[int]:
+    """Interval lengths, left to right, cut on [0, M) by {a x mod M : x < n}."""
+    pts = sorted({(a * x) % M for x in range(n)})
+    pts.append(M)
+    return [pts[i + 1] - pts[i] for i in range(len(pts) - 1)]
+
+
+def cf_configurations(a: int, M: int):
+    """Rows (i, t, q_{i-1,t}, q_i, theta_{i-1,t}, theta_i, k_{i+1}) of the
+    two-length configurations of a/M (lengths scaled by M), in the order of
+    Property 1, until theta_i = 0.  For the final row (theta_i = 0) k_{i+1}
+    is undefined and reported as None."""
+    rows = []
+    th_prev, th = M, a           # theta_{-1} = 1, theta_0 = a  (scaled)
+    q_prev, q = 0, 1             # q_{-1}, q_0
+    i = 0
+    while True:
+        if th == 0:
+            rows.append((i, 0, q_prev, q, th_prev, th, None))
+            return rows
+        k = th_prev // th
+        for t in range(k):
+            rows.append((i, t, q_prev + t * q, q, th_prev - t * th, th, k))
+        th_prev, th = th, th_prev - k * th
+        q_prev, q = q, q_prev + k * q
+        i += 1
+
+
+def regular_lb(B: int, A: int, N: int, M: int = 1 << 64) -> Tuple[int, int, int]:
+    """Algorithm 2 on integers: returns (lower bound d, points u+v, loop
+    iterations).  p <- A, q <- M, d <- B, u <- 1, v <- 0; each iteration
+    reduces the longer length by the division-based Euclidean step and
+    updates d; stops when u + v >= N.  A length reaching 0 ends the
+    expansion (rational a): d is then final (the points form a lattice)."""
+    p, q, d, u, v = A, M, B % M, 1, 0
+    it = 0
+    while True:
+        if p == 0:
+            return d % q, u + v, it
+        if q == 0:
+            return d, u + v, it
+        it += 1
+        if p < q:
+            k = q // p
+            q = q - k * p
+            u = u + k * v
+            d = d % p
+        else:
+            k = p // q
+            p = p - k * q
+            v = v + k * u
+            if d >= p:
+                d = (d - p) % q
+        if u + v >= N:
+            return d, u + v, it
+
+
+def regular_lb_unrolled(B: int, A: int, N: int, M: int = 1 << 64) -> Tuple[int, int, int]:
+    """Algorithm 4 on integers (the two branches of Algorithm 2 alternate,
+    so two iterations are written one after the other).  Returns
+    (d, u+v, half-steps).  Endings: p = 0 returns d mod q; q = 0 returns d."""
+    p, q, d, u, v = A, M, B % M, 1, 0
+    hs = 0
+    while True:
+        if p == 0:
+            return d % q, u + v, hs
+        k = q // p
+        q = q - k * p
+        u = u + k * v
+        d = d % p
+        hs += 1
+        if u + v >= N or q == 0:
+            return d, u + v, hs
+        k = p // q
+        p = p - k * q
+        v = v + k * u
+        if d >= p:
+            d = (d - p) % q
+        hs += 1
+        if u + v >= N:
+            return d, u + v, hs
+
+
+def forward_differences(values: List[int]) -> List[List[int]]:
+    """Rows Delta^0 .. Delta^n of the values (Def. of Delta, Fig. 5)."""
+    rows = [list(values)]
+    while len(rows[-1]) > 1:
+        r = rows[-1]
+        rows.append([r[i + 1] - r[i] for i in range(len(r) - 1)])
+    return rows
+
+
+def tabulated_shift(column: List[int], steps: int, mod: int = 0) -> List[List[int]]:
+    """Columns [Delta^0(i), ..., Delta^g(i)] for i = 0 .. steps-1 from the
+    column at i = 0, by Delta^(l-1)(i+1) = Delta^(l-1)(i) + Delta^l(i)
+    (Sect. IV-B, Fig. 6); optionally reduced mod `mod`."""
+    col = list(column)
+    out = []
+    for _ in range(steps):
+        out.append(list(col))
+        col = [col[l] + (col[l + 1] if l + 1 < len(col) else 0) for l in range(len(col))]
+        if mod:
+            col = [c % mod for c in col]
+    return out
+
+
+def straightforward_shift(column: List[int], n: int, mod: int = 0) -> List[int]:
+    """The column at i = n directly: Delta^l(n) = sum_{k>=l} binom(n, k-l)
+    Delta^k(0) (the upper-triangular Toeplitz binomial matrix of Sect. IV-B)."""
+    g = len(column) - 1
+    out = [sum(comb(n, k - l) * column[k] for k in range(l, g + 1)) for l in range(g + 1)]
+    if mod:
+        out = [c % mod for c in out]
+    return out

@@ -1,0 +1,131 @@
+"""Pins of the oracle's continued-fraction and three-distance machinery.
+
+Checked against the paper's printed examples (Fig. 3, Table 1, Fig. 7), the
+three-distance theorem (Thm. 1), Eq. (2) and Eq. (3), and brute force."""
+import random
+
+import pytest
+
+from conftest import read_golden
+from oracle import search
+
+
+def test_fig3_gap_lists():
+    for row in read_golden("fig3_gaps_a14_m45.txt"):
+        n = int(row[0])
+        lengths = [int(v) for v in row[2:]]
+        assert search.gaps_in_order(14, 45, n) == lengths, f"n={n}"
+
+
+def test_table1_rows():
+    want = read_golden("table1_a14_m45.txt")
+    got = search.cf_configurations(14, 45)
+    assert len(got) == len(want)
+    for g, w in zip(got, want):
+        assert list(g[:6]) == [int(v) for v in w[:6]]
+        if w[6] != "-":
+            assert g[6] == int(w[6])
+
+
+def test_fig3_labels_match_configurations():
+    """The labelled rows of Fig. 3 sit at n = q_i + q_{i-1,t} points."""
+    rows = {(r[0], r[2], r[3], r[4]) for r in search.cf_configurations(14, 45)}
+    labels = {}
+    for row in read_golden("fig3_gaps_a14_m45.txt"):
+        if row[1] != "-":
+            i, t = (int(v) for v in row[1].strip("()").split(","))
+            labels[(i, t)] = int(row[0])
+    cf = {(r[0], r[1]): r[2] + r[3] for r in search.cf_configurations(14, 45)}
+    for key, n in labels.items():
+        assert cf[key] == n, key
+
+
+@pytest.mark.parametrize("a,M", [(14, 45), (31, 45), (6, 45), (37, 64), (173, 256), (1000003, 1 << 24)])
+def test_eq2_two_length_counts(a, M):
+    """Eq. (2): after q_i + q_{i-1,t} points there are q_i intervals of
+    length theta_{i-1,t} and q_{i-1,t} of length theta_i (Eq. (3) is t=0)."""
+    for (i, t, q_im1t, q_i, th_im1t, th_i, k) in search.cf_configurations(a, M):
+        if th_i == 0 or q_i + q_im1t > 4000:
+            continue
+        n = q_i + q_im1t
+        assert q_i * th_im1t + q_im1t * th_i == M
+        gaps = search.gaps_in_order(a, M, n)
+        want = sorted([th_im1t] * q_i + [th_i] * q_im1t)
+        assert sorted(gaps) == want, (i, t)
+
+
+def test_fig7_gap_lists():
+    for row in read_golden("fig7_gaps_a31_m45.txt"):
+        n = int(row[1])
+        assert search.gaps_in_order(31, 45, n) == [int(v) for v in row[2:]]
+    # the configurations of Fig. 7 are two-length configurations of 31/45
+    cf = {(r[0], r[1]): r[2] + r[3] for r in search.cf_configurations(31, 45)}
+    for row in read_golden("fig7_gaps_a31_m45.txt"):
+        i, t = (int(v) for v in row[0].strip("()").split(","))
+        assert cf[(i, t)] == int(row[1])
+
+
+def test_three_distance_theorem_random():
+    """Thm. 1: at most three lengths, the largest the sum of the other two."""
+    rng = random.Random(7)
+    for _ in range(300):
+        M = rng.choice([45, 97, 256, 1009, 1 << 16, 1 << 20])
+        a = rng.randrange(1, M)
+        n = rng.randrange(1, min(M, 600))
+        lengths = sorted(set(search.gaps_in_order(a, M, n)))
+        assert len(lengths) <= 3
+        if len(lengths) == 3:
+            assert lengths[2] == lengths[0] + lengths[1]
+
+
+def test_fig7_trace_is_lower_bound():
+    """Algorithm 2 on a = 31/45, b = 39/45: each exit value bounds the true
+    minimum over x < N from below (Sect. III-A: it is a minimum over n >= N
+    points); brute force gives the true minimum."""
+    for N in range(1, 46):
+        lb, n, _ = search.regular_lb(39, 31, N, 45)
+        true, _ = search.brute_min(39, 31, N, 45)
+        # n < N only when the expansion of the rational a ended (theta = 0),
+        # where d is the distance over the whole lattice of points
+        assert n >= N or n == 42
+        assert lb <= true
+
+
+@pytest.mark.parametrize("M", [45, 64, 97])
+def test_regular_lb_exhaustive_small_moduli(M):
+    """Exhaustive over all (a, b, N) for small moduli: Algorithm 4 equals
+    Algorithm 2 and never exceeds the brute-force minimum over x < N; it
+    equals the minimum over its own u+v points when those are N exactly."""
+    for A in range(M):
+        for B in range(M):
+            run = []
+            best = None
+            for x in range(2 * M + 2):
+                v = (B - A * x) % M
+                best = v if best is None or v < best else best
+                run.append(best)
+            for N in range(1, M + 2):
+                lb2 = search.regular_lb(B, A, N, M)
+                lb4 = search.regular_lb_unrolled(B, A, N, M)
+                assert lb2[:2] == lb4[:2]
+                assert lb2[0] <= run[N - 1]
+                assert lb2[0] >= run[-1]
+
+
+def test_regular_lb_random_64bit():
+    rng = random.Random(11)
+    for _ in range(400):
+        N = rng.choice([16, 256, 1024])
+        A = rng.getrandbits(64)
+        B = rng.getrandbits(64)
+        lb, n, hs = search.regular_lb_unrolled(B, A, N)
+        true, _ = search.brute_min(B, A, N)
+        assert n >= N and lb <= true
+
+
+def test_brute_min_definition():
+    assert search.brute_min(5, 0, 10, 64) == (5, 0)
+    assert search.brute_min(0, 7, 3, 64) == (0, 0)
+    # ties: the smallest x wins (A*32 = 0 mod 64)
+    assert search.brute_min(3, 32, 4, 64) == (3, 0)
+    assert search.brute_min(10, 3, 5, 64) == (1, 3)

@@ -1,0 +1,230 @@
+/*
+ * tmd.h -- C ABI of the GB300 hard-to-round argument search library.
+ *
+ * The library decides, for a function f (exp, 2^x, log) over a slice of one
+ * binade at precision p, which sub-intervals of N consecutive arguments hold
+ * an argument X whose scaled value s f(X) lies within 2^-m of a rounding
+ * breakpoint on the degree-1 approximation of f -- the Boolean test of
+ * Eq. (1), Sect. II-A of Fortin, Gouicem, Graillat, "GPU-accelerated
+ * generation of correctly-rounded elementary functions" (arXiv 1211.3056).
+ *
+ * Stages (all arithmetic exact, integer or fixed point):
+ *   generate  Sect. IV: Taylor polynomial R_t of degree d per block of T
+ *             arguments (correctly rounded coefficients in W = 64*limbs-bit
+ *             fixed point), its step-N difference tables (hierarchical
+ *             method, Sect. IV-A), device packet starts by the
+ *             straightforward shift and tabulated-difference stepping
+ *             (Sect. IV-B, IV-C), giving one line b_i + alpha_i x per
+ *             sub-interval;
+ *   search    Sect. III-B: the regular continued-fraction lower bound
+ *             (Algorithm 4) per line as a filter, exact resolution of the
+ *             lines it flags, warp-ballot compaction of the candidates;
+ *   candidates  stream-ordered read-back, sorted.
+ *
+ * Conventions for every entry point:
+ *   - returns tmd_status; TMD_OK == 0.  Never aborts, exits or prints.
+ *   - "stream" is a cudaStream_t passed as void* (NULL = legacy default).
+ *   - device pointers ("d_" prefix) are caller-owned memory on the
+ *     context's device; the library never frees caller memory.
+ *   - host pointers ("h_" prefix or plain) are caller-owned host memory.
+ *   - the library synchronises the host only inside tmd_candidates,
+ *     tmd_stats_read, tmd_batch_wait and the serving calls that say so.
+ *   - a context is used by one host thread at a time.
+ */
+#ifndef TMD_H
+#define TMD_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    TMD_OK = 0,
+    TMD_EINVAL = 1,        /* a parameter failed validation                       */
+    TMD_ENOMEM = 2,        /* a buffer is too small or an allocation failed       */
+    TMD_EOVERFLOW = 3,     /* candidate capacity reached; the count is still exact */
+    TMD_ETIMEOUT = 4,      /* a bounded device wait expired                       */
+    TMD_ECUDA = 5,         /* a CUDA runtime call failed                          */
+    TMD_EUNSUPPORTED = 6   /* valid request outside what this build supports      */
+} tmd_status;
+
+typedef enum { TMD_EXP = 0, TMD_EXP2 = 1, TMD_LOG = 2 } tmd_func;
+
+/* flags */
+#define TMD_BP_DIRECTED 1u  /* scale s = 2^(p - e_out): floats only (directed rounding).
+                               Default s = 2^(p + 1 - e_out): floats and midpoints, i.e.
+                               the directed (p+1) cases that cover every IEEE mode
+                               (Sect. II-A).                                          */
+#define TMD_ALL_HITS 2u     /* report every argument below the threshold, not only the
+                               minimum of each sub-interval                            */
+
+/* One search job: a slice of one binade of one function (Sect. III-A).
+ * Argument index j in [0, 2^(p-1)) stands for X_j = (2^(p-1) + j) 2^(e_in - p).
+ * Supported here: exp and 2^x with -16 <= e_in <= 2, log with 2 <= e_in <= 16,
+ * 8 <= p <= 60, 2 <= m <= 63, 1 <= log2_N <= 16, log2_N <= log2_T <= 40,
+ * 1 <= d <= 4, 1 <= limbs <= 3, count >= 1, start + count <= 2^(p-1). */
+typedef struct {
+    int32_t  func;      /* tmd_func                                            */
+    int32_t  e_in;      /* arguments in [2^(e_in-1), 2^e_in)                   */
+    int32_t  p;         /* precision                                           */
+    int32_t  m;         /* report iff the minimum is below 2^-m                */
+    uint32_t log2_N;    /* sub-interval length N = #D_i                        */
+    int32_t  d;         /* Taylor degree of each block polynomial              */
+    uint32_t log2_T;    /* Taylor block length T = tau N                       */
+    uint32_t limbs;     /* fixed-point width W = 64 * limbs bits               */
+    uint64_t start;     /* first argument index                                */
+    uint64_t count;     /* number of arguments                                 */
+    uint32_t flags;     /* TMD_BP_DIRECTED | TMD_ALL_HITS                      */
+    uint32_t reserved;  /* must be 0                                           */
+} tmd_job;
+
+/* One reported sub-interval (or argument, with TMD_ALL_HITS): the index of the
+ * job in the call's array, the job-wide sub-interval number, the argument
+ * index j of the minimum (smallest one on ties) and the minimum itself,
+ * min (B - A x) mod 2^64 over the sub-interval, in units of 2^-64 (the
+ * threshold is 2^(65-m)). */
+typedef struct {
+    uint32_t job;
+    uint32_t subint;
+    uint64_t arg_index;
+    uint64_t value;
+} tmd_candidate;
+
+/* Plan summary of one job (Sect. III-A split, Sect. IV blocks). */
+typedef struct {
+    uint64_t n_blocks;       /* Taylor blocks                                  */
+    uint64_t n_subints;      /* sub-intervals (the last of a block may be short) */
+    uint32_t n_segments;     /* runs of constant output exponent               */
+    int32_t  e_out_first;    /* e(f(X)) at the first argument                  */
+    uint64_t cut[4];         /* first argument index of segments 1..3          */
+} tmd_plan_info;
+
+/* Per-block description returned by tmd_block_tables. */
+typedef struct {
+    uint64_t start;          /* argument index of the block's first argument   */
+    uint64_t length;         /* arguments in the block                         */
+    uint64_t first_sub;      /* job-wide index of the block's first sub-interval */
+    int32_t  e_out;          /* output exponent on the block                   */
+    int32_t  scale_log2;     /* log2 of the breakpoint scale s                 */
+} tmd_block_info;
+
+/* Counters of the last search on a context (device-side, read on demand). */
+typedef struct {
+    uint64_t lines;          /* lines (sub-intervals) searched                  */
+    uint64_t filter_fail;    /* lines whose lower bound fell below the threshold */
+    uint64_t candidates;     /* records produced (same as *d_count)             */
+    uint64_t half_steps;     /* continued-fraction half-steps, all lanes       */
+} tmd_stats;
+
+typedef struct tmd_ctx tmd_ctx;
+
+/* Version string of the library (static storage). */
+const char* tmd_version(void);
+/* Human-readable name of a status code (static storage). */
+const char* tmd_status_str(tmd_status s);
+
+/* Context on CUDA device `device`.  It owns device scratch (block tables,
+ * work lists, counters) and pinned staging memory, grown on demand and freed
+ * by tmd_destroy.  TMD_ECUDA when the device is unusable. */
+tmd_status tmd_create(tmd_ctx** ctx, int device);
+tmd_status tmd_destroy(tmd_ctx* ctx);
+
+/* Drop the resident plan (block tables, work lists) of the context so that
+ * the next tmd_generate / tmd_search plans and uploads again; the device
+ * memory is kept for reuse.  Synchronises nothing. */
+tmd_status tmd_evict(tmd_ctx* ctx);
+
+/* ---- host-only planning (no device work; usable without a GPU) ---------- */
+
+/* Validate a job and summarise its plan: output-binade cuts (first argument
+ * with a larger e(f(X)), decided exactly), blocks of T arguments from each
+ * segment start, sub-intervals of N from each block start (Sect. III-A, IV).
+ * TMD_EINVAL / TMD_EUNSUPPORTED on a bad job. */
+tmd_status tmd_plan(const tmd_job* job, tmd_plan_info* info);
+
+/* The table of block `block` (0-based, plan order) of `job`:
+ *   coeffs[k*limbs + l]  limb l (little-endian 64-bit limbs) of the Taylor
+ *                        coefficient c_k = RN(2^W s u^k f^(k)(X_t)/k!) mod 2^W,
+ *                        k = 0..d (Sect. IV Taylor polynomial R_t, correctly
+ *                        rounded; may be NULL);
+ *   table[w*limbs + l]   the 2d+1 difference-table words: w = 0..d are
+ *                        Delta^w g0(0) with g0(i) = R_t(iN), w = d+1..2d are
+ *                        Delta^(w-d-1) g1(0) with g1(i) = R_t(iN+1) - R_t(iN)
+ *                        (hierarchical method, Sect. IV-A), all mod 2^W
+ *                        (may be NULL);
+ *   info                 the block's place in the plan (may be NULL).
+ * Host memory, caller-owned: coeffs holds (d+1)*limbs, table (2d+1)*limbs
+ * words.  TMD_EINVAL if block is past the plan. */
+tmd_status tmd_block_tables(const tmd_job* job, uint64_t block, uint64_t* coeffs,
+                            uint64_t* table, tmd_block_info* info);
+
+/* ---- the three core calls ------------------------------------------------ */
+
+/* Stage 1: plan, correctly rounded block tables (host, multithreaded),
+ * upload, and the generation kernel: packet starts by the straightforward
+ * shift, then tabulated-difference stepping, writing the search words of
+ * every sub-interval of every job (jobs in order, sub-intervals in plan
+ * order) into d_lin as two arrays: B[n] then A[n] (uint64), where
+ *   B = floor(((b_i + 2^(W-m)) mod 2^W) / 2^(W-64)),
+ *   A = floor(((-alpha_i) mod 2^W) / 2^(W-64))
+ * (the one-sided test of Sect. II-A on the form b - a x of Eq. (1)).
+ * *lin_bytes_needed = 16 * total sub-intervals.  With d_lin == NULL or
+ * lin_bytes too small only the size is reported (TMD_ENOMEM if d_lin was
+ * given).  The plan and tables stay resident in the context for tmd_search.
+ * Asynchronous on `stream` apart from the host table computation. */
+tmd_status tmd_generate(tmd_ctx* ctx, const tmd_job* jobs, uint32_t njobs,
+                        void* d_lin, size_t lin_bytes, size_t* lin_bytes_needed,
+                        void* stream);
+
+/* Stage 2: search.  With d_lin != NULL, the lines written by tmd_generate
+ * for the same jobs are searched (one line per lane, Algorithm 4 filter,
+ * exact resolution, warp-ballot compaction).  With d_lin == NULL the fused
+ * kernel regenerates the lines in registers from the resident tables
+ * (planning them first if these jobs are not the resident ones).
+ * Records go to d_cand[0 .. cand_cap), unordered; *d_count (device uint64)
+ * receives the exact total even past cand_cap.  Asynchronous on `stream`. */
+tmd_status tmd_search(tmd_ctx* ctx, const tmd_job* jobs, uint32_t njobs,
+                      const void* d_lin, tmd_candidate* d_cand, uint64_t cand_cap,
+                      uint64_t* d_count, void* stream);
+
+/* Stage 3: copy the count and min(count, cand_cap, h_cap) records to the host
+ * after `stream` drains, sort them by (job, arg_index, value) and store them
+ * in h_out.  *n_out = the exact count.  TMD_EOVERFLOW when the count exceeds
+ * what was stored.  Synchronises `stream`. */
+tmd_status tmd_candidates(tmd_ctx* ctx, const tmd_candidate* d_cand,
+                          const uint64_t* d_count, uint64_t cand_cap,
+                          tmd_candidate* h_out, uint64_t h_cap, uint64_t* n_out,
+                          void* stream);
+
+/* ---- search on caller-supplied lines --------------------------------------- */
+
+/* Search n lines given directly as device arrays d_B[n], d_A[n] (search
+ * words as above) and d_len[n] (arguments per line, 1 .. 2^16).  Record i has
+ * job = 0, subint = i, arg_index = x*, value = min.  threshold = 2^(65-m);
+ * flags may hold TMD_ALL_HITS.  Same output contract as tmd_search. */
+tmd_status tmd_search_lines(tmd_ctx* ctx, const uint64_t* d_B, const uint64_t* d_A,
+                            const uint32_t* d_len, uint64_t n, int32_t m, uint32_t flags,
+                            tmd_candidate* d_cand, uint64_t cand_cap, uint64_t* d_count,
+                            void* stream);
+
+/* The Algorithm 4 lower bound alone, per line: d_lb[i] = the value d at exit,
+ * d_hs[i] = continued-fraction half-steps taken (may be NULL).  The loop
+ * stops once u + v >= d_len[i]; a remainder reaching 0 ends it early (p = 0
+ * returns d mod q, q = 0 returns d).  For tests and loop statistics
+ * (Table 3 / Fig. 8 NMDM). */
+tmd_status tmd_lower_bounds(tmd_ctx* ctx, const uint64_t* d_B, const uint64_t* d_A,
+                            const uint32_t* d_len, uint64_t n, uint64_t* d_lb,
+                            uint32_t* d_hs, void* stream);
+
+/* Counters of the most recent tmd_search / tmd_search_lines / batch run on
+ * this context.  Synchronises `stream`. */
+tmd_status tmd_stats_read(tmd_ctx* ctx, tmd_stats* out, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* TMD_H */

@@ -1,0 +1,189 @@
+"""GB300 hard-to-round argument search (arXiv 1211.3056 hot path).
+
+Thin Python binding of the C ABI in include/tmd.h: every function below only
+marshals arguments to libtmd.so, where all the work runs (host C++ planning
+and correctly rounded tables, CUDA kernels for generation and search).
+PyTorch supplies device memory and streams.  Importing this package raises
+ImportError when libtmd.so has not been built; there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+from typing import List, Optional, Sequence, Tuple
+
+from . import _lib
+from ._lib import (TMD_ALL_HITS, TMD_BP_DIRECTED, TMD_EXP, TMD_EXP2, TMD_LOG, TMD_OK,  # noqa: F401
+                   TMD_EOVERFLOW, TmdError, check, job_array, lib, make_job)
+
+lib()  # fail loudly at import when the extension is missing
+
+CANDIDATE_BYTES = ctypes.sizeof(_lib.tmd_candidate)
+
+
+def _stream_ptr(stream) -> Optional[int]:
+    if stream is None:
+        import torch
+        return torch.cuda.current_stream().cuda_stream
+    if isinstance(stream, int):
+        return stream
+    return stream.cuda_stream
+
+
+def _ptr(t) -> Optional[int]:
+    return None if t is None else t.data_ptr()
+
+
+class Context:
+    """Owns one tmd_ctx (device scratch, pinned staging, resident plan)."""
+
+    def __init__(self, device: int = 0):
+        h = ctypes.c_void_p()
+        check(lib().tmd_create(ctypes.byref(h), int(device)), "tmd_create")
+        self.handle = h
+        self.device = int(device)
+
+    def close(self):
+        if self.handle:
+            lib().tmd_destroy(self.handle)
+            self.handle = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def tmd_version() -> str:
+    return lib().tmd_version().decode()
+
+
+def tmd_create(device: int = 0) -> Context:
+    return Context(device)
+
+
+def tmd_destroy(ctx: Context) -> None:
+    ctx.close()
+
+
+def tmd_evict(ctx: Context) -> None:
+    check(lib().tmd_evict(ctx.handle), "tmd_evict")
+
+
+def tmd_plan(job) -> dict:
+    info = _lib.tmd_plan_info()
+    check(lib().tmd_plan(ctypes.byref(make_job(job)), ctypes.byref(info)), "tmd_plan")
+    return {"n_blocks": info.n_blocks, "n_subints": info.n_subints, "n_segments": info.n_segments,
+            "e_out_first": info.e_out_first, "cuts": [info.cut[i] for i in range(info.n_segments - 1)]}
+
+
+def _words_to_ints(arr, count: int, limbs: int) -> List[int]:
+    out = []
+    for w in range(count):
+        v = 0
+        for l in range(limbs):
+            v |= int(arr[w * limbs + l]) << (64 * l)
+        out.append(v)
+    return out
+
+
+def tmd_block_tables(job, block: int) -> Tuple[List[int], List[int], dict]:
+    """(coefficients c_0..c_d, the 2d+1 table words, block info) as ints."""
+    L, d = job.limbs, job.d
+    coeffs = (ctypes.c_uint64 * ((d + 1) * L))()
+    table = (ctypes.c_uint64 * ((2 * d + 1) * L))()
+    info = _lib.tmd_block_info()
+    check(lib().tmd_block_tables(ctypes.byref(make_job(job)), int(block), coeffs, table,
+                                 ctypes.byref(info)), "tmd_block_tables")
+    return (_words_to_ints(coeffs, d + 1, L), _words_to_ints(table, 2 * d + 1, L),
+            {"start": info.start, "length": info.length, "first_sub": info.first_sub,
+             "e_out": info.e_out, "scale_log2": info.scale_log2})
+
+
+def tmd_generate(ctx: Context, jobs: Sequence, d_lin=None, stream=None) -> int:
+    """Plan + tables + generation kernel; returns the bytes d_lin needs."""
+    arr = job_array(jobs)
+    need = ctypes.c_size_t(0)
+    nbytes = 0 if d_lin is None else d_lin.numel() * d_lin.element_size()
+    check(lib().tmd_generate(ctx.handle, arr, len(jobs), _ptr(d_lin), nbytes, ctypes.byref(need),
+                             _stream_ptr(stream)), "tmd_generate")
+    return need.value
+
+
+def tmd_search(ctx: Context, jobs: Sequence, d_lin, d_cand, d_count, stream=None) -> None:
+    arr = job_array(jobs)
+    cap = 0 if d_cand is None else (d_cand.numel() * d_cand.element_size()) // CANDIDATE_BYTES
+    check(lib().tmd_search(ctx.handle, arr, len(jobs), _ptr(d_lin), _ptr(d_cand), cap, _ptr(d_count),
+                           _stream_ptr(stream)), "tmd_search")
+
+
+def tmd_candidates(ctx: Context, d_cand, d_count, h_cap: Optional[int] = None, stream=None):
+    """(sorted records as (job, subint, arg_index, value) tuples, exact count)."""
+    cap = 0 if d_cand is None else (d_cand.numel() * d_cand.element_size()) // CANDIDATE_BYTES
+    if h_cap is None:
+        h_cap = cap
+    out = (_lib.tmd_candidate * max(1, h_cap))()
+    n = ctypes.c_uint64(0)
+    st = lib().tmd_candidates(ctx.handle, _ptr(d_cand), _ptr(d_count), cap, out, h_cap,
+                              ctypes.byref(n), _stream_ptr(stream))
+    check(st, "tmd_candidates", ok=(TMD_OK, TMD_EOVERFLOW))
+    k = min(n.value, cap, h_cap)
+    recs = [(out[i].job, out[i].subint, out[i].arg_index, out[i].value) for i in range(k)]
+    return recs, n.value
+
+
+def tmd_search_lines(ctx: Context, d_B, d_A, d_len, m: int, flags: int, d_cand, d_count,
+                     stream=None) -> None:
+    n = d_B.numel()
+    cap = 0 if d_cand is None else (d_cand.numel() * d_cand.element_size()) // CANDIDATE_BYTES
+    check(lib().tmd_search_lines(ctx.handle, _ptr(d_B), _ptr(d_A), _ptr(d_len), n, int(m), int(flags),
+                                 _ptr(d_cand), cap, _ptr(d_count), _stream_ptr(stream)),
+          "tmd_search_lines")
+
+
+def tmd_lower_bounds(ctx: Context, d_B, d_A, d_len, d_lb, d_hs=None, stream=None) -> None:
+    check(lib().tmd_lower_bounds(ctx.handle, _ptr(d_B), _ptr(d_A), _ptr(d_len), d_B.numel(),
+                                 _ptr(d_lb), _ptr(d_hs), _stream_ptr(stream)), "tmd_lower_bounds")
+
+
+def tmd_stats_read(ctx: Context, stream=None) -> dict:
+    s = _lib.tmd_stats()
+    check(lib().tmd_stats_read(ctx.handle, ctypes.byref(s), _stream_ptr(stream)), "tmd_stats_read")
+    return {"lines": s.lines, "filter_fail": s.filter_fail, "candidates": s.candidates,
+            "half_steps": s.half_steps}
+
+
+# ------------------------------------------------------------- conveniences
+def alloc_candidates(cap: int, device: int = 0):
+    """Device buffers for cap records and the count (torch tensors)."""
+    import torch
+    d_cand = torch.empty(cap * CANDIDATE_BYTES, dtype=torch.uint8, device=f"cuda:{device}")
+    d_count = torch.zeros(1, dtype=torch.int64, device=f"cuda:{device}")
+    return d_cand, d_count
+
+
+def run(jobs: Sequence, ctx: Optional[Context] = None, fused: bool = True, cap: int = 1 << 20,
+        device: int = 0, stream=None):
+    """Generate + search + read back; returns (sorted records, exact count)."""
+    import torch
+    own = ctx is None
+    if own:
+        ctx = Context(device)
+    try:
+        d_cand, d_count = alloc_candidates(cap, device)
+        d_lin = None
+        if not fused:
+            need = tmd_generate(ctx, jobs, None, stream)
+            d_lin = torch.empty(max(need, 16) // 8, dtype=torch.int64, device=f"cuda:{device}")
+            tmd_generate(ctx, jobs, d_lin, stream)
+        tmd_search(ctx, jobs, d_lin, d_cand, d_count, stream)
+        return tmd_candidates(ctx, d_cand, d_count, stream=stream)
+    finally:
+        if own:
+            ctx.close()

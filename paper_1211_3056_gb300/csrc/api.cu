@@ -1,0 +1,509 @@
+// C-ABI entry points (include/tmd.h): context, plan residency, uploads,
+// launches and read-back.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <atomic>
+#include <cstdlib>
+#include <cstring>
+#include <thread>
+#include <vector>
+
+#include "dev.hpp"
+#include "host.hpp"
+
+namespace tmd {
+cudaError_t launch_tasks(bool fused, uint32_t L, uint32_t D, const LaunchArgs& a, cudaStream_t s);
+cudaError_t launch_persistent(const LaunchArgs& a, int ctas, cudaStream_t s);
+cudaError_t persistent_occupancy(int* blocks_per_sm);
+}  // namespace tmd
+
+namespace tmd {
+cudaError_t launch_search_lines(bool raw, const LineArgs& a, cudaStream_t s);
+cudaError_t launch_lower_bounds(const uint64_t* B, const uint64_t* A, const uint32_t* len, uint64_t n,
+                                uint64_t* lb, uint32_t* hs, uint32_t* err, cudaStream_t s);
+}  // namespace tmd
+
+using namespace tmd;
+
+namespace {
+
+struct ClassRange {
+    uint32_t L, D;
+    uint64_t first, count;  // task range
+};
+
+// A plan resident on the device: jobs, blocks, tables, tasks.
+struct Plan {
+    std::vector<tmd_job> key;
+    std::vector<DevJob> jobs;
+    std::vector<DevBlock> blocks;
+    std::vector<uint64_t> tables;
+    std::vector<DevTask> tasks;
+    std::vector<ClassRange> classes;
+    uint64_t total_lines = 0;
+    uint64_t total_args = 0;
+};
+
+size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+}  // namespace
+
+struct tmd_ctx {
+    int device = 0;
+    int sms = 0;
+    // device arena holding the resident plan
+    char* d_arena = nullptr;
+    size_t arena_cap = 0;
+    size_t off_jobs = 0, off_blocks = 0, off_tables = 0, off_tasks = 0;
+    // counters: stats[4] u64, err u32, queue head u32
+    uint64_t* d_misc = nullptr;
+    // pinned staging for uploads
+    char* h_stage = nullptr;
+    size_t stage_cap = 0;
+    cudaEvent_t stage_done = nullptr;
+    bool stage_pending = false;
+    Plan plan;
+    bool resident = false;
+};
+
+namespace {
+
+uint64_t* stats_ptr(tmd_ctx* c) { return c->d_misc; }
+uint32_t* err_ptr(tmd_ctx* c) { return (uint32_t*)(c->d_misc + ST_COUNT); }
+uint32_t* queue_ptr(tmd_ctx* c) { return (uint32_t*)(c->d_misc + ST_COUNT) + 1; }
+
+#define CK(x)                                  \
+    do {                                       \
+        cudaError_t e_ = (x);                  \
+        if (e_ != cudaSuccess) return TMD_ECUDA; \
+    } while (0)
+
+unsigned host_threads() {
+    const char* env = getenv("TMD_HOST_THREADS");
+    if (env && atoi(env) > 0) return (unsigned)atoi(env);
+    unsigned n = std::thread::hardware_concurrency();
+    return n ? n : 1;
+}
+
+uint32_t choose_nu(const tmd_job& job, uint64_t n_sub_block) {
+    const char* env = getenv("TMD_NU");
+    uint32_t nu = 8;
+    if (env && atoi(env) > 0) nu = (uint32_t)atoi(env);
+    if (nu > n_sub_block) nu = (uint32_t)n_sub_block;
+    if (nu < 1) nu = 1;
+    (void)job;
+    return nu;
+}
+
+// Plan every job, compute all block tables (threads over blocks).
+tmd_status build_plan(const tmd_job* jobs, uint32_t njobs, Plan& P) {
+    P = Plan();
+    if (njobs == 0 || !jobs) return TMD_EINVAL;
+    P.key.assign(jobs, jobs + njobs);
+    std::vector<std::vector<Segment>> segs(njobs);
+    std::vector<BlockPlan> bplan;
+    std::vector<uint32_t> bjob;
+    uint64_t line = 0, packet = 0, toff = 0;
+    for (uint32_t j = 0; j < njobs; j++) {
+        const tmd_job& jb = jobs[j];
+        tmd_status st = validate_job(jb);
+        if (st != TMD_OK) return st;
+        st = plan_segments(jb, segs[j]);
+        if (st != TMD_OK) return st;
+        uint64_t nb, ns;
+        plan_counts(jb, segs[j], &nb, &ns);
+        if (P.blocks.size() + nb >= (1ull << 31)) return TMD_EUNSUPPORTED;
+        DevJob dj;
+        memset(&dj, 0, sizeof dj);
+        dj.line_off = line;
+        dj.n_lines = ns;
+        dj.Tm = 1ull << (65 - jb.m);
+        dj.block_off = (uint32_t)P.blocks.size();
+        dj.n_blocks = (uint32_t)nb;
+        dj.log2_N = jb.log2_N;
+        dj.d = (uint32_t)jb.d;
+        dj.L = jb.limbs;
+        dj.m = (uint32_t)jb.m;
+        dj.flags = jb.flags;
+        const uint64_t nsub_full = 1ull << (jb.log2_T - jb.log2_N);
+        dj.nu = choose_nu(jb, nsub_full);
+        const uint64_t words = (uint64_t)(2 * jb.d + 1) * jb.limbs;
+        const uint64_t job_pk0 = packet;
+        for (uint64_t b = 0; b < nb; b++) {
+            BlockPlan bp;
+            plan_block(jb, segs[j], b, &bp);
+            DevBlock db;
+            db.start = bp.start;
+            db.length = bp.length;
+            db.first_sub = bp.first_sub;
+            db.packet_off = packet;
+            db.table_off = toff;
+            db.job = j;
+            db.n_sub = (uint32_t)((bp.length + (1ull << jb.log2_N) - 1) >> jb.log2_N);
+            packet += (db.n_sub + dj.nu - 1) / dj.nu;
+            toff += words;
+            P.blocks.push_back(db);
+            bplan.push_back(bp);
+            bjob.push_back(j);
+        }
+        for (uint64_t g = job_pk0; g < packet; g += 32) {
+            DevTask t;
+            t.g0 = g;
+            t.count = (uint32_t)std::min<uint64_t>(32, packet - g);
+            t.job = j;
+            P.tasks.push_back(t);
+        }
+        P.jobs.push_back(dj);
+        line += ns;
+        P.total_args += jb.count;
+    }
+    P.total_lines = line;
+    P.tables.assign(toff, 0);
+    // correctly rounded tables, blocks spread over host threads
+    std::atomic<uint64_t> next(0);
+    std::atomic<int> bad(0);
+    const uint64_t nblk = P.blocks.size();
+    auto worker = [&]() {
+        for (;;) {
+            uint64_t b = next.fetch_add(16);
+            if (b >= nblk) break;
+            uint64_t e = std::min<uint64_t>(b + 16, nblk);
+            for (; b < e; b++) {
+                const tmd_job& jb = jobs[bjob[b]];
+                if (block_table(jb, bplan[b], nullptr, &P.tables[P.blocks[b].table_off]) != TMD_OK)
+                    bad.store(1);
+            }
+        }
+    };
+    unsigned nt = std::min<uint64_t>(host_threads(), (nblk + 15) / 16);
+    if (nt <= 1) {
+        worker();
+    } else {
+        std::vector<std::thread> th;
+        for (unsigned i = 0; i < nt; i++) th.emplace_back(worker);
+        for (auto& t : th) t.join();
+    }
+    if (bad.load()) return TMD_EUNSUPPORTED;
+    // group tasks by (L, D) so that the plain form launches one kernel per class
+    std::stable_sort(P.tasks.begin(), P.tasks.end(), [&](const DevTask& a, const DevTask& b) {
+        uint32_t ka = P.jobs[a.job].L * 8 + P.jobs[a.job].d, kb = P.jobs[b.job].L * 8 + P.jobs[b.job].d;
+        return ka < kb;
+    });
+    for (uint64_t i = 0; i < P.tasks.size(); i++) {
+        const DevJob& dj = P.jobs[P.tasks[i].job];
+        if (P.classes.empty() || P.classes.back().L != dj.L || P.classes.back().D != dj.d)
+            P.classes.push_back(ClassRange{dj.L, dj.d, i, 0});
+        P.classes.back().count++;
+    }
+    return TMD_OK;
+}
+
+tmd_status upload_plan(tmd_ctx* c, cudaStream_t s) {
+    Plan& P = c->plan;
+    size_t o_jobs = 0;
+    size_t o_blocks = align256(o_jobs + P.jobs.size() * sizeof(DevJob));
+    size_t o_tables = align256(o_blocks + P.blocks.size() * sizeof(DevBlock));
+    size_t o_tasks = align256(o_tables + P.tables.size() * sizeof(uint64_t));
+    size_t total = align256(o_tasks + P.tasks.size() * sizeof(DevTask));
+    if (c->stage_pending) {
+        CK(cudaEventSynchronize(c->stage_done));
+        c->stage_pending = false;
+    }
+    if (total > c->stage_cap) {
+        if (c->h_stage) CK(cudaFreeHost(c->h_stage));
+        c->h_stage = nullptr;
+        size_t cap = std::max(total, c->stage_cap * 2);
+        CK(cudaHostAlloc((void**)&c->h_stage, cap, cudaHostAllocDefault));
+        c->stage_cap = cap;
+    }
+    if (total > c->arena_cap) {
+        CK(cudaStreamSynchronize(s));
+        if (c->d_arena) CK(cudaFree(c->d_arena));
+        c->d_arena = nullptr;
+        size_t cap = std::max(total, c->arena_cap * 2);
+        CK(cudaMalloc((void**)&c->d_arena, cap));
+        c->arena_cap = cap;
+    }
+    memcpy(c->h_stage + o_jobs, P.jobs.data(), P.jobs.size() * sizeof(DevJob));
+    memcpy(c->h_stage + o_blocks, P.blocks.data(), P.blocks.size() * sizeof(DevBlock));
+    memcpy(c->h_stage + o_tables, P.tables.data(), P.tables.size() * sizeof(uint64_t));
+    memcpy(c->h_stage + o_tasks, P.tasks.data(), P.tasks.size() * sizeof(DevTask));
+    CK(cudaMemcpyAsync(c->d_arena, c->h_stage, total, cudaMemcpyHostToDevice, s));
+    CK(cudaEventRecord(c->stage_done, s));
+    c->stage_pending = true;
+    c->off_jobs = o_jobs;
+    c->off_blocks = o_blocks;
+    c->off_tables = o_tables;
+    c->off_tasks = o_tasks;
+    return TMD_OK;
+}
+
+bool same_jobs(const tmd_ctx* c, const tmd_job* jobs, uint32_t njobs) {
+    if (!c->resident || c->plan.key.size() != njobs) return false;
+    return memcmp(c->plan.key.data(), jobs, njobs * sizeof(tmd_job)) == 0;
+}
+
+tmd_status make_resident(tmd_ctx* c, const tmd_job* jobs, uint32_t njobs, cudaStream_t s) {
+    if (same_jobs(c, jobs, njobs)) return TMD_OK;
+    c->resident = false;
+    tmd_status st = build_plan(jobs, njobs, c->plan);
+    if (st != TMD_OK) return st;
+    st = upload_plan(c, s);
+    if (st != TMD_OK) return st;
+    c->resident = true;
+    return TMD_OK;
+}
+
+LaunchArgs task_args(tmd_ctx* c) {
+    LaunchArgs a;
+    memset(&a, 0, sizeof a);
+    a.jobs = (const DevJob*)(c->d_arena + c->off_jobs);
+    a.blocks = (const DevBlock*)(c->d_arena + c->off_blocks);
+    a.tables = (const uint64_t*)(c->d_arena + c->off_tables);
+    a.tasks = (const DevTask*)(c->d_arena + c->off_tasks);
+    a.n_tasks = c->plan.tasks.size();
+    a.stats = stats_ptr(c);
+    a.queue_head = queue_ptr(c);
+    return a;
+}
+
+tmd_status reset_counters(tmd_ctx* c, uint64_t* d_count, cudaStream_t s) {
+    CK(cudaMemsetAsync(c->d_misc, 0, sizeof(uint64_t) * (ST_COUNT + 1), s));
+    if (d_count) CK(cudaMemsetAsync(d_count, 0, sizeof(uint64_t), s));
+    return TMD_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* tmd_version(void) { return "tmd-gb300 0.1 (sm_103a)"; }
+
+const char* tmd_status_str(tmd_status s) {
+    switch (s) {
+        case TMD_OK: return "ok";
+        case TMD_EINVAL: return "invalid argument";
+        case TMD_ENOMEM: return "buffer too small or allocation failed";
+        case TMD_EOVERFLOW: return "candidate capacity exceeded (count is exact)";
+        case TMD_ETIMEOUT: return "bounded device wait expired";
+        case TMD_ECUDA: return "CUDA runtime error";
+        case TMD_EUNSUPPORTED: return "unsupported by this build";
+    }
+    return "unknown status";
+}
+
+tmd_status tmd_create(tmd_ctx** out, int device) {
+    if (!out) return TMD_EINVAL;
+    *out = nullptr;
+    int n = 0;
+    if (cudaGetDeviceCount(&n) != cudaSuccess || device < 0 || device >= n) return TMD_ECUDA;
+    CK(cudaSetDevice(device));
+    tmd_ctx* c = new tmd_ctx();
+    c->device = device;
+    if (cudaDeviceGetAttribute(&c->sms, cudaDevAttrMultiProcessorCount, device) != cudaSuccess ||
+        cudaMalloc((void**)&c->d_misc, 64) != cudaSuccess ||
+        cudaEventCreateWithFlags(&c->stage_done, cudaEventDisableTiming) != cudaSuccess) {
+        delete c;
+        return TMD_ECUDA;
+    }
+    cudaMemset(c->d_misc, 0, 64);
+    *out = c;
+    return TMD_OK;
+}
+
+tmd_status tmd_destroy(tmd_ctx* c) {
+    if (!c) return TMD_EINVAL;
+    cudaSetDevice(c->device);
+    if (c->stage_pending) cudaEventSynchronize(c->stage_done);
+    if (c->d_arena) cudaFree(c->d_arena);
+    if (c->d_misc) cudaFree(c->d_misc);
+    if (c->h_stage) cudaFreeHost(c->h_stage);
+    if (c->stage_done) cudaEventDestroy(c->stage_done);
+    delete c;
+    return TMD_OK;
+}
+
+tmd_status tmd_evict(tmd_ctx* c) {
+    if (!c) return TMD_EINVAL;
+    c->resident = false;
+    c->plan = Plan();
+    return TMD_OK;
+}
+
+tmd_status tmd_plan(const tmd_job* job, tmd_plan_info* info) {
+    if (!job || !info) return TMD_EINVAL;
+    tmd_status st = validate_job(*job);
+    if (st != TMD_OK) return st;
+    std::vector<Segment> segs;
+    st = plan_segments(*job, segs);
+    if (st != TMD_OK) return st;
+    memset(info, 0, sizeof *info);
+    plan_counts(*job, segs, &info->n_blocks, &info->n_subints);
+    info->n_segments = (uint32_t)segs.size();
+    info->e_out_first = segs[0].e_out;
+    for (size_t i = 1; i < segs.size() && i <= 4; i++) info->cut[i - 1] = segs[i].j0;
+    return TMD_OK;
+}
+
+tmd_status tmd_block_tables(const tmd_job* job, uint64_t block, uint64_t* coeffs, uint64_t* table,
+                            tmd_block_info* info) {
+    if (!job) return TMD_EINVAL;
+    tmd_status st = validate_job(*job);
+    if (st != TMD_OK) return st;
+    std::vector<Segment> segs;
+    st = plan_segments(*job, segs);
+    if (st != TMD_OK) return st;
+    BlockPlan bp;
+    if (!plan_block(*job, segs, block, &bp)) return TMD_EINVAL;
+    if (info) {
+        info->start = bp.start;
+        info->length = bp.length;
+        info->first_sub = bp.first_sub;
+        info->e_out = bp.e_out;
+        info->scale_log2 = scale_log2(*job, bp.e_out);
+    }
+    return block_table(*job, bp, coeffs, table);
+}
+
+tmd_status tmd_generate(tmd_ctx* c, const tmd_job* jobs, uint32_t njobs, void* d_lin, size_t lin_bytes,
+                        size_t* lin_bytes_needed, void* stream) {
+    if (!c || !jobs || njobs == 0) return TMD_EINVAL;
+    cudaStream_t s = (cudaStream_t)stream;
+    CK(cudaSetDevice(c->device));
+    tmd_status st = make_resident(c, jobs, njobs, s);
+    if (st != TMD_OK) return st;
+    const size_t need = (size_t)c->plan.total_lines * 16;
+    if (lin_bytes_needed) *lin_bytes_needed = need;
+    if (!d_lin) return TMD_OK;
+    if (lin_bytes < need) return TMD_ENOMEM;
+    LaunchArgs base = task_args(c);
+    base.lin_B = (uint64_t*)d_lin;
+    base.lin_A = (uint64_t*)d_lin + c->plan.total_lines;
+    for (const ClassRange& cr : c->plan.classes) {
+        LaunchArgs a = base;
+        a.tasks = base.tasks + cr.first;
+        a.n_tasks = cr.count;
+        CK(launch_tasks(false, cr.L, cr.D, a, s));
+    }
+    return TMD_OK;
+}
+
+tmd_status tmd_search(tmd_ctx* c, const tmd_job* jobs, uint32_t njobs, const void* d_lin,
+                      tmd_candidate* d_cand, uint64_t cand_cap, uint64_t* d_count, void* stream) {
+    if (!c || !jobs || njobs == 0 || !d_count || (cand_cap && !d_cand)) return TMD_EINVAL;
+    cudaStream_t s = (cudaStream_t)stream;
+    CK(cudaSetDevice(c->device));
+    tmd_status st = make_resident(c, jobs, njobs, s);
+    if (st != TMD_OK) return st;
+    st = reset_counters(c, d_count, s);
+    if (st != TMD_OK) return st;
+    if (d_lin) {
+        LineArgs a;
+        memset(&a, 0, sizeof a);
+        a.B = (const uint64_t*)d_lin;
+        a.A = (const uint64_t*)d_lin + c->plan.total_lines;
+        a.n_lines = c->plan.total_lines;
+        a.jobs = (const DevJob*)(c->d_arena + c->off_jobs);
+        a.n_jobs = (uint32_t)c->plan.jobs.size();
+        a.blocks = (const DevBlock*)(c->d_arena + c->off_blocks);
+        a.cand = d_cand;
+        a.cap = cand_cap;
+        a.count = d_count;
+        a.stats = stats_ptr(c);
+        a.err = err_ptr(c);
+        CK(launch_search_lines(false, a, s));
+        return TMD_OK;
+    }
+    LaunchArgs base = task_args(c);
+    base.cand = d_cand;
+    base.cap = cand_cap;
+    base.count = d_count;
+    for (const ClassRange& cr : c->plan.classes) {
+        LaunchArgs a = base;
+        a.tasks = base.tasks + cr.first;
+        a.n_tasks = cr.count;
+        CK(launch_tasks(true, cr.L, cr.D, a, s));
+    }
+    return TMD_OK;
+}
+
+tmd_status tmd_candidates(tmd_ctx* c, const tmd_candidate* d_cand, const uint64_t* d_count,
+                          uint64_t cand_cap, tmd_candidate* h_out, uint64_t h_cap, uint64_t* n_out,
+                          void* stream) {
+    if (!c || !d_count || !n_out || (h_cap && !h_out)) return TMD_EINVAL;
+    cudaStream_t s = (cudaStream_t)stream;
+    CK(cudaSetDevice(c->device));
+    uint64_t count = 0;
+    uint32_t err = 0;
+    CK(cudaMemcpyAsync(&count, d_count, sizeof count, cudaMemcpyDeviceToHost, s));
+    CK(cudaMemcpyAsync(&err, err_ptr(c), sizeof err, cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    *n_out = count;
+    uint64_t n = std::min(count, std::min(cand_cap, h_cap));
+    if (n) {
+        if (!d_cand) return TMD_EINVAL;
+        CK(cudaMemcpyAsync(h_out, d_cand, n * sizeof(tmd_candidate), cudaMemcpyDeviceToHost, s));
+        CK(cudaStreamSynchronize(s));
+        std::sort(h_out, h_out + n, [](const tmd_candidate& a, const tmd_candidate& b) {
+            if (a.job != b.job) return a.job < b.job;
+            if (a.arg_index != b.arg_index) return a.arg_index < b.arg_index;
+            return a.value < b.value;
+        });
+    }
+    if (err) return TMD_EINVAL;
+    return count > n ? TMD_EOVERFLOW : TMD_OK;
+}
+
+tmd_status tmd_search_lines(tmd_ctx* c, const uint64_t* d_B, const uint64_t* d_A, const uint32_t* d_len,
+                            uint64_t n, int32_t m, uint32_t flags, tmd_candidate* d_cand,
+                            uint64_t cand_cap, uint64_t* d_count, void* stream) {
+    if (!c || !d_count || (n && (!d_B || !d_A || !d_len)) || (cand_cap && !d_cand)) return TMD_EINVAL;
+    if (m < 2 || m > 63 || (flags & ~(uint32_t)TMD_ALL_HITS)) return TMD_EINVAL;
+    if (n >= (1ull << 32)) return TMD_EUNSUPPORTED;
+    cudaStream_t s = (cudaStream_t)stream;
+    CK(cudaSetDevice(c->device));
+    tmd_status st = reset_counters(c, d_count, s);
+    if (st != TMD_OK) return st;
+    LineArgs a;
+    memset(&a, 0, sizeof a);
+    a.B = d_B;
+    a.A = d_A;
+    a.len = d_len;
+    a.n_lines = n;
+    a.Tm = 1ull << (65 - m);
+    a.flags = flags;
+    a.cand = d_cand;
+    a.cap = cand_cap;
+    a.count = d_count;
+    a.stats = stats_ptr(c);
+    a.err = err_ptr(c);
+    CK(launch_search_lines(true, a, s));
+    return TMD_OK;
+}
+
+tmd_status tmd_lower_bounds(tmd_ctx* c, const uint64_t* d_B, const uint64_t* d_A, const uint32_t* d_len,
+                            uint64_t n, uint64_t* d_lb, uint32_t* d_hs, void* stream) {
+    if (!c || (n && (!d_B || !d_A || !d_len || !d_lb))) return TMD_EINVAL;
+    cudaStream_t s = (cudaStream_t)stream;
+    CK(cudaSetDevice(c->device));
+    CK(cudaMemsetAsync(err_ptr(c), 0, sizeof(uint32_t), s));
+    CK(launch_lower_bounds(d_B, d_A, d_len, n, d_lb, d_hs, err_ptr(c), s));
+    return TMD_OK;
+}
+
+tmd_status tmd_stats_read(tmd_ctx* c, tmd_stats* out, void* stream) {
+    if (!c || !out) return TMD_EINVAL;
+    cudaStream_t s = (cudaStream_t)stream;
+    CK(cudaSetDevice(c->device));
+    uint64_t h[ST_COUNT];
+    CK(cudaMemcpyAsync(h, stats_ptr(c), sizeof h, cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    out->lines = h[ST_LINES];
+    out->filter_fail = h[ST_FAIL];
+    out->candidates = h[ST_CAND];
+    out->half_steps = h[ST_HALF];
+    return TMD_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,81 @@
+// Device-visible plan records (written by the host layer, read by kernels).
+#pragma once
+
+#include <cstdint>
+
+#include "../../include/tmd.h"
+
+namespace tmd {
+
+// One job as the kernels see it.
+struct DevJob {
+    uint64_t line_off;     // global index of the job's first line (unfused layout)
+    uint64_t n_lines;      // sub-intervals of the job
+    uint64_t Tm;           // threshold 2^(65-m) on the search words
+    uint32_t block_off;    // global index of the job's first block
+    uint32_t n_blocks;
+    uint32_t log2_N;
+    uint32_t d;
+    uint32_t L;            // limbs of the fixed-point words
+    uint32_t m;
+    uint32_t flags;
+    uint32_t nu;           // sub-intervals per packet (lane)
+};
+
+// One Taylor block.
+struct DevBlock {
+    uint64_t start;        // argument index of the first argument
+    uint64_t length;       // arguments in the block
+    uint64_t first_sub;    // job-wide index of the first sub-interval
+    uint64_t packet_off;   // global index of the block's first packet
+    uint64_t table_off;    // offset (in 64-bit words) of the block's 2d+1 table words
+    uint32_t job;
+    uint32_t n_sub;        // sub-intervals in the block
+};
+
+// A warp's unit of work: up to 32 consecutive packets of one job.
+struct DevTask {
+    uint64_t g0;           // first global packet index
+    uint32_t count;        // packets (1..32)
+    uint32_t job;
+};
+
+// Counters (device uint64 each) in the order of tmd_stats.
+enum { ST_LINES = 0, ST_FAIL = 1, ST_CAND = 2, ST_HALF = 3, ST_COUNT = 4 };
+
+// Launch-side description of one fused/unfused launch.
+struct LaunchArgs {
+    const DevJob* jobs;
+    const DevBlock* blocks;
+    const uint64_t* tables;
+    const DevTask* tasks;
+    uint64_t n_tasks;
+    uint64_t* lin_B;        // unfused layout: B[total lines], A[total lines]
+    uint64_t* lin_A;
+    tmd_candidate* cand;
+    uint64_t cap;
+    uint64_t* count;
+    uint64_t* stats;
+    uint32_t* queue_head;   // persistent form: next task index
+};
+
+// Line search arguments.  JOBS mode: the lines written by the generation
+// kernel for the resident plan.  RAW mode: caller arrays with lengths.
+struct LineArgs {
+    const uint64_t* B;
+    const uint64_t* A;
+    const uint32_t* len;      // RAW only
+    uint64_t n_lines;
+    uint64_t Tm;              // RAW only
+    uint32_t flags;           // RAW only
+    const DevJob* jobs;       // JOBS only
+    uint32_t n_jobs;
+    const DevBlock* blocks;
+    tmd_candidate* cand;
+    uint64_t cap;
+    uint64_t* count;
+    uint64_t* stats;
+    uint32_t* err;
+};
+
+}  // namespace tmd

@@ -1,0 +1,483 @@
+// Host-side part of the generation stage: validation, output-binade cuts,
+// block plan, correctly rounded Taylor coefficients and difference tables.
+//
+// Values of f are enclosed in fixed point with P fractional bits,
+// lo/2^P <= value <= hi/2^P, from power series summed with truncating
+// arithmetic plus an explicit bound on the accumulated truncation and on the
+// series tail.  A coefficient is accepted only when both ends of its
+// enclosure round to the same integer; otherwise P grows (Ziv's strategy).
+#include "host.hpp"
+
+#include <cstring>
+
+#include "bigint.hpp"
+
+namespace tmd {
+
+namespace {
+
+struct Enc {
+    Big lo, hi;      // lo / 2^P <= value <= hi / 2^P
+    unsigned P;
+};
+
+// exp(y / 2^Q), y >= 0, with P fractional bits.
+// t_0 = 2^P, t_n = floor(t_{n-1} X / n); the truncation error e_n of t_n
+// obeys e_n <= e_{n-1} X / n + 1, tracked with X <= Xc = ceil(X).  Once
+// t_n = 0 with n >= 2 Xc + 2, the true term is at most e_n and the tail after
+// it at most the term itself (ratio X/(n+1) < 1/2).
+Enc exp_fixed(const Big& y, unsigned Q, unsigned P) {
+    Big yc = y;
+    yc.add(Big::pow2(Q).sub(Big(1)));
+    yc.shr(Q);
+    uint64_t Xc = yc.limb(0);
+    Big t = Big::pow2(P);
+    Big S = t;
+    uint64_t e = 0, E = 0;
+    for (uint64_t n = 1;; n++) {
+        t = Big::mul(t, y);
+        t.shr(Q);
+        t.div_u64(n);
+        e = (e * Xc + n - 1) / n + 1;
+        S.add(t);
+        E += e;
+        if (t.zero() && n >= 2 * Xc + 2) {
+            E += e + 1;
+            break;
+        }
+    }
+    Enc r;
+    r.lo = S;
+    r.hi = S;
+    r.hi.add(Big(E));
+    r.P = P;
+    return r;
+}
+
+// ln 2 = sum_k 2 / ((2k+1) 3^(2k+1)):  w_0 = floor(2^(P+1)/3),
+// w_k = floor(w_{k-1}/9) (error <= 2), term_k = floor(w_k/(2k+1)) (error <= 2).
+Enc ln2_fixed(unsigned P) {
+    Big w = Big::pow2(P + 1);
+    w.div_u64(3);
+    Big S = w;
+    uint64_t E = 1;
+    for (uint64_t k = 1;; k++) {
+        w.div_u64(9);
+        Big t = w;
+        t.div_u64(2 * k + 1);
+        S.add(t);
+        E += 2;
+        if (t.zero()) {
+            E += 1;
+            break;
+        }
+    }
+    Enc r;
+    r.lo = S;
+    r.hi = S;
+    r.hi.add(Big(E));
+    r.P = P;
+    return r;
+}
+
+// 2^X with X = M / 2^q: exact at integers, else exp(X ln 2) with the argument
+// enclosed from both sides (exp is increasing).
+Enc exp2_fixed(uint64_t M, unsigned q, unsigned P) {
+    Enc r;
+    r.P = P;
+    if (q == 0 || (M & ((1ull << q) - 1)) == 0) {
+        uint64_t X = q >= 64 ? 0 : (M >> q);
+        r.lo = Big::pow2(P + (unsigned)X);
+        r.hi = r.lo;
+        return r;
+    }
+    unsigned P2 = P + 16;
+    Enc L = ln2_fixed(P2);
+    Big ylo = L.lo;
+    ylo.mul_u64(M);
+    ylo.shr(q);
+    Big yhi = L.hi;
+    yhi.mul_u64(M);
+    yhi = shr_ceil(yhi, q);
+    r.lo = exp_fixed(ylo, P2, P).lo;
+    r.hi = exp_fixed(yhi, P2, P).hi;
+    return r;
+}
+
+// log X for X = M 2^(e_in - p), 2^(p-1) <= M < 2^p, e_in >= 2:
+// log X = e_in ln 2 - 2 atanh(z), z = (2^p - M) / (2^p + M) in (0, 1/3].
+// w_0 = floor(2^P num/den) (error <= 1); w_k = w_{k-1} z^2 by two
+// truncating multiply-divides (error <= e/9 + 2 <= 3); term_k =
+// floor(w_k / (2k+1)) (error <= 2); tail after a zero term <= 1.
+Enc log_fixed(uint64_t M, int p, int e_in, unsigned P) {
+    uint64_t num = (1ull << p) - M, den = (1ull << p) + M;
+    Big w = Big::pow2(P);
+    w.mul_u64(num);
+    w.div_u64(den);
+    Big S = w;
+    uint64_t E = 1;
+    for (uint64_t k = 1;; k++) {
+        w.mul_u64(num);
+        w.div_u64(den);
+        w.mul_u64(num);
+        w.div_u64(den);
+        Big t = w;
+        t.div_u64(2 * k + 1);
+        S.add(t);
+        E += 2;
+        if (t.zero()) {
+            E += 1;
+            break;
+        }
+    }
+    Enc L = ln2_fixed(P);
+    Enc r;
+    r.P = P;
+    Big two_hi = S;
+    two_hi.add(Big(E));
+    two_hi.mul_u64(2);
+    Big two_lo = S;
+    two_lo.mul_u64(2);
+    r.lo = L.lo;
+    r.lo.mul_u64((uint64_t)e_in);
+    r.lo.sub(two_hi);
+    r.hi = L.hi;
+    r.hi.mul_u64((uint64_t)e_in);
+    r.hi.sub(two_lo);
+    return r;
+}
+
+uint64_t factorial(int k) {
+    uint64_t r = 1;
+    for (int i = 2; i <= k; i++) r *= (uint64_t)i;
+    return r;
+}
+
+// Enclosure of f^(k)(X)/k! (k = 0: f itself) for the positive cases:
+// exp (any k), 2^x (any k), log (k = 0).  X = M 2^(e_in - p).
+Enc coeff_enclosure(int func, uint64_t M, int p, int e_in, int k, unsigned P) {
+    unsigned q = (unsigned)(p - e_in);
+    uint64_t kf = factorial(k);
+    Enc r;
+    if (func == TMD_EXP) {
+        r = exp_fixed(Big(M), q, P);
+    } else if (func == TMD_EXP2) {
+        unsigned P2 = P + 8 + 2 * (unsigned)k;
+        Enc e = exp2_fixed(M, q, P2);
+        if (k > 0) {
+            Enc L = ln2_fixed(P2);
+            Big lo = e.lo, hi = e.hi;
+            for (int i = 0; i < k; i++) {
+                lo = Big::mul(lo, L.lo);
+                lo.shr(P2);
+                hi = Big::mul(hi, L.hi);
+                hi = shr_ceil(hi, P2);
+            }
+            e.lo = lo;
+            e.hi = hi;
+        }
+        r.lo = e.lo;
+        r.lo.shr(P2 - P);
+        r.hi = shr_ceil(e.hi, P2 - P);
+        r.P = P;
+    } else {
+        r = log_fixed(M, p, e_in, P);
+    }
+    if (kf > 1) {
+        r.lo.div_u64(kf);
+        uint64_t rem = r.hi.div_u64(kf);
+        if (rem) r.hi.add_u64(1);
+    }
+    return r;
+}
+
+// RN(v) = floor(v + 1/2) of v = x / 2^s for x >= 0 (s >= 1).
+Big rn_shift(const Big& x, unsigned s) {
+    Big t = x;
+    t.add(Big::pow2(s - 1));
+    t.shr(s);
+    return t;
+}
+
+// Signed result of RN(2^E f^(k)(X)/k!) reduced mod 2^W into `limbs` words.
+bool scaled_coeff(int func, uint64_t M, int p, int e_in, int k, int E, unsigned limbs,
+                  uint64_t* out) {
+    Big mag;
+    bool neg = false;
+    if (func == TMD_LOG && k >= 1) {
+        // exact rational: (-1)^(k-1) 2^(E + k q) / (k M^k)
+        int q = p - e_in;
+        int sh = E + k * q;
+        if (sh < 0) return false;
+        neg = (k % 2) == 0;
+        Big den = Big((uint64_t)k);
+        for (int i = 0; i < k; i++) den.mul_u64(M);
+        Big x = Big::pow2((unsigned)sh + 1);
+        x.add(den);
+        if (neg) x.sub(Big(1));
+        // floor((2 num + den [- 1]) / (2 den)) by a chain of exact floors
+        x.div_u64(2);
+        x.div_u64((uint64_t)k);
+        for (int i = 0; i < k; i++) x.div_u64(M);
+        mag = x;
+    } else {
+        bool done = false;
+        for (int step = 0; step < 16 && !done; step++) {
+            int base = E > 0 ? E : 0;
+            unsigned P = (unsigned)(base + 64 + 64 * step);
+            Enc c = coeff_enclosure(func, M, p, e_in, k, P);
+            int s = (int)P - E;
+            if (s < 1) continue;
+            Big rl = rn_shift(c.lo, (unsigned)s);
+            Big rh = rn_shift(c.hi, (unsigned)s);
+            if (rl.cmp(rh) == 0) {
+                mag = rl;
+                done = true;
+            }
+        }
+        if (!done) return false;
+    }
+    // reduce mod 2^W, negate in two's complement if needed
+    uint64_t w[MAX_LIMBS] = {0, 0, 0};
+    for (unsigned l = 0; l < limbs; l++) w[l] = mag.limb(l);
+    if (neg) {
+        uint64_t c = 1;
+        for (unsigned l = 0; l < limbs; l++) {
+            uint64_t x = ~w[l];
+            w[l] = x + c;
+            c = (w[l] < x) ? 1 : 0;
+        }
+    }
+    for (unsigned l = 0; l < limbs; l++) out[l] = w[l];
+    return true;
+}
+
+// ---- W-bit words (mod 2^W), little-endian limbs ----
+struct Word {
+    uint64_t l[MAX_LIMBS];
+};
+
+Word w_zero() {
+    Word r;
+    memset(&r, 0, sizeof r);
+    return r;
+}
+Word w_add(const Word& a, const Word& b, unsigned L) {
+    Word r = w_zero();
+    uint64_t c = 0;
+    for (unsigned i = 0; i < L; i++) {
+        u128 s = (u128)a.l[i] + b.l[i] + c;
+        r.l[i] = (uint64_t)s;
+        c = (uint64_t)(s >> 64);
+    }
+    return r;
+}
+Word w_sub(const Word& a, const Word& b, unsigned L) {
+    Word r = w_zero();
+    uint64_t br = 0;
+    for (unsigned i = 0; i < L; i++) {
+        u128 d = (u128)a.l[i] - b.l[i] - br;
+        r.l[i] = (uint64_t)d;
+        br = (uint64_t)(d >> 64) ? 1 : 0;
+    }
+    return r;
+}
+Word w_mul_u64(const Word& a, uint64_t m, unsigned L) {
+    Word r = w_zero();
+    uint64_t c = 0;
+    for (unsigned i = 0; i < L; i++) {
+        u128 p = (u128)a.l[i] * m + c;
+        r.l[i] = (uint64_t)p;
+        c = (uint64_t)(p >> 64);
+    }
+    return r;
+}
+// R(y) = sum_k c_k y^k mod 2^W by Horner's rule
+Word horner(const Word* c, int d, uint64_t y, unsigned L) {
+    Word acc = c[d];
+    for (int k = d - 1; k >= 0; k--) acc = w_add(w_mul_u64(acc, y, L), c[k], L);
+    return acc;
+}
+
+// f(X) enclosure used for the output exponent
+Enc f_enclosure(const tmd_job& job, uint64_t M, unsigned P) {
+    return coeff_enclosure(job.func, M, job.p, job.e_in, 0, P);
+}
+
+uint64_t arg_mantissa(const tmd_job& job, uint64_t j) { return (1ull << (job.p - 1)) + j; }
+
+// First j (possibly outside the slice) with e(f(X_j)) >= e, by the inverse
+// function: f(X) >= 2^(e-1) iff X >= t_e with t_e = (e-1) ln 2 (exp),
+// e - 1 (2^x), exp(2^(e-1)) (log).  X_j = M_j 2^-q, so the cut is
+// ceil(t_e 2^q) - 2^(p-1); t_e 2^q is irrational except for 2^x.
+bool cut_index(const tmd_job& job, int e, int64_t* out) {
+    int q = job.p - job.e_in;
+    int64_t half = (int64_t)1 << (job.p - 1);
+    if (job.func == TMD_EXP2) {
+        *out = (int64_t)(e - 1) * ((int64_t)1 << q) - half;
+        return true;
+    }
+    for (unsigned P = (unsigned)q + 96; P < (unsigned)q + 96 + 64 * 12; P += 64) {
+        Big lo, hi;
+        if (job.func == TMD_EXP) {
+            if (e - 1 <= 0) return false;
+            Enc L = ln2_fixed(P);
+            lo = L.lo;
+            lo.mul_u64((uint64_t)(e - 1));
+            hi = L.hi;
+            hi.mul_u64((uint64_t)(e - 1));
+        } else {
+            Enc x;
+            if (e - 1 >= 0)
+                x = exp_fixed(Big(1ull << (e - 1)), 0, P);
+            else
+                x = exp_fixed(Big(1), (unsigned)(1 - e), P);
+            lo = x.lo;
+            hi = x.hi;
+        }
+        // floor(value 2^q) = floor(lo / 2^(P - q))
+        lo.shr(P - (unsigned)q);
+        hi.shr(P - (unsigned)q);
+        if (lo.cmp(hi) == 0) {
+            if (lo.v.size() > 1) return false;
+            *out = (int64_t)lo.limb(0) + 1 - half;
+            return true;
+        }
+    }
+    return false;
+}
+
+}  // namespace
+
+tmd_status validate_job(const tmd_job& job) {
+    if (job.reserved != 0) return TMD_EINVAL;
+    if (job.func < TMD_EXP || job.func > TMD_LOG) return TMD_EINVAL;
+    if (job.p < 8 || job.p > 60) return TMD_EUNSUPPORTED;
+    if (job.m < 2 || job.m > 63) return TMD_EINVAL;
+    if (job.log2_N < 1 || job.log2_N > 16) return TMD_EUNSUPPORTED;
+    if (job.log2_T < job.log2_N || job.log2_T > 40) return TMD_EINVAL;
+    if (job.log2_T - job.log2_N > 16) return TMD_EUNSUPPORTED;
+    if (job.d < 1 || job.d > MAX_DEG) return TMD_EUNSUPPORTED;
+    if (job.limbs < 1 || job.limbs > MAX_LIMBS) return TMD_EUNSUPPORTED;
+    if (job.flags & ~(uint32_t)(TMD_BP_DIRECTED | TMD_ALL_HITS)) return TMD_EINVAL;
+    if (job.func == TMD_LOG) {
+        if (job.e_in < 2 || job.e_in > 16) return TMD_EUNSUPPORTED;
+    } else {
+        if (job.e_in < -16 || job.e_in > 2) return TMD_EUNSUPPORTED;
+    }
+    uint64_t span = 1ull << (job.p - 1);
+    if (job.count == 0 || job.start >= span || job.count > span - job.start) return TMD_EINVAL;
+    // the sub-interval numbering of a job must fit 32 bits
+    if ((job.count >> job.log2_N) + (job.count >> job.log2_T) + 8 >= (1ull << 32)) return TMD_EUNSUPPORTED;
+    return TMD_OK;
+}
+
+int output_exponent(const tmd_job& job, uint64_t j) {
+    uint64_t M = arg_mantissa(job, j);
+    for (unsigned P = 64; P < 64 * 20; P += 64) {
+        Enc f = f_enclosure(job, M, P);
+        int elo = (int)f.lo.bits() - (int)P;
+        int ehi = (int)f.hi.bits() - (int)P;
+        if (elo == ehi) return elo;
+    }
+    return 0x7fffffff;
+}
+
+tmd_status plan_segments(const tmd_job& job, std::vector<Segment>& segs) {
+    segs.clear();
+    uint64_t a = job.start, b = job.start + job.count;
+    int e0 = output_exponent(job, a);
+    int e1 = output_exponent(job, b - 1);
+    if (e0 == 0x7fffffff || e1 == 0x7fffffff) return TMD_EUNSUPPORTED;
+    if (e1 - e0 + 1 > MAX_SEGMENTS) return TMD_EUNSUPPORTED;
+    uint64_t cur = a;
+    int e = e0;
+    for (int en = e0 + 1; en <= e1; en++) {
+        int64_t c;
+        if (!cut_index(job, en, &c)) return TMD_EUNSUPPORTED;
+        if (c <= (int64_t)cur || c >= (int64_t)b) return TMD_EUNSUPPORTED;
+        // the cut must be the first argument with the new exponent
+        if (output_exponent(job, (uint64_t)c) != en || output_exponent(job, (uint64_t)c - 1) != en - 1)
+            return TMD_EUNSUPPORTED;
+        segs.push_back(Segment{cur, (uint64_t)c, e});
+        cur = (uint64_t)c;
+        e = en;
+    }
+    segs.push_back(Segment{cur, b, e});
+    return TMD_OK;
+}
+
+void plan_counts(const tmd_job& job, const std::vector<Segment>& segs, uint64_t* n_blocks,
+                 uint64_t* n_subints) {
+    uint64_t T = 1ull << job.log2_T, N = 1ull << job.log2_N;
+    uint64_t nb = 0, ns = 0;
+    for (const Segment& s : segs) {
+        uint64_t len = s.j1 - s.j0;
+        uint64_t full = len / T, rest = len % T;
+        nb += full + (rest ? 1 : 0);
+        ns += full * (T / N) + (rest + N - 1) / N;
+    }
+    *n_blocks = nb;
+    *n_subints = ns;
+}
+
+bool plan_block(const tmd_job& job, const std::vector<Segment>& segs, uint64_t b, BlockPlan* out) {
+    uint64_t T = 1ull << job.log2_T, N = 1ull << job.log2_N;
+    uint64_t sub = 0;
+    for (const Segment& s : segs) {
+        uint64_t len = s.j1 - s.j0;
+        uint64_t nb = (len + T - 1) / T;
+        if (b < nb) {
+            out->start = s.j0 + b * T;
+            out->length = (b + 1 < nb) ? T : len - b * T;
+            out->first_sub = sub + b * (T / N);
+            out->e_out = s.e_out;
+            return true;
+        }
+        b -= nb;
+        uint64_t full = len / T, rest = len % T;
+        sub += full * (T / N) + (rest + N - 1) / N;
+    }
+    return false;
+}
+
+int scale_log2(const tmd_job& job, int e_out) {
+    return (job.flags & TMD_BP_DIRECTED) ? job.p - e_out : job.p + 1 - e_out;
+}
+
+tmd_status block_table(const tmd_job& job, const BlockPlan& blk, uint64_t* coeffs, uint64_t* table) {
+    const unsigned L = job.limbs;
+    const int W = 64 * (int)L;
+    const int d = job.d;
+    const uint64_t N = 1ull << job.log2_N;
+    uint64_t M = arg_mantissa(job, blk.start);
+    int sl = scale_log2(job, blk.e_out);
+    Word c[MAX_DEG + 1];
+    for (int k = 0; k <= d; k++) {
+        c[k] = w_zero();
+        int E = W + sl + k * (job.e_in - job.p);
+        if (!scaled_coeff(job.func, M, job.p, job.e_in, k, E, L, c[k].l)) return TMD_EUNSUPPORTED;
+        if (coeffs)
+            for (unsigned l = 0; l < L; l++) coeffs[k * L + l] = c[k].l[l];
+    }
+    if (!table) return TMD_OK;
+    // g0(i) = R(iN) for i = 0..d, g1(i) = R(iN+1) - R(iN) for i = 0..d-1,
+    // then forward differences at 0 (Sect. IV-A hierarchical method)
+    Word g0[MAX_DEG + 1], g1[MAX_DEG];
+    for (int i = 0; i <= d; i++) {
+        Word r0 = horner(c, d, (uint64_t)i * N, L);
+        g0[i] = r0;
+        if (i < d) g1[i] = w_sub(horner(c, d, (uint64_t)i * N + 1, L), r0, L);
+    }
+    for (int lev = 0; lev <= d; lev++) {
+        for (unsigned l = 0; l < L; l++) table[lev * L + l] = g0[0].l[l];
+        for (int i = 0; i + lev < d; i++) g0[i] = w_sub(g0[i + 1], g0[i], L);
+    }
+    for (int lev = 0; lev < d; lev++) {
+        for (unsigned l = 0; l < L; l++) table[(d + 1 + lev) * L + l] = g1[0].l[l];
+        for (int i = 0; i + lev + 1 < d; i++) g1[i] = w_sub(g1[i + 1], g1[i], L);
+    }
+    return TMD_OK;
+}
+
+}  // namespace tmd

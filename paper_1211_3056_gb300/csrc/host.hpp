@@ -1,0 +1,48 @@
+// Host-side planning and block tables (shared by the C-ABI layer).
+#pragma once
+
+#include <cstdint>
+#include <vector>
+
+#include "../../include/tmd.h"
+
+namespace tmd {
+
+enum { MAX_LIMBS = 3, MAX_DEG = 4, MAX_WORDS = 2 * MAX_DEG + 1, MAX_SEGMENTS = 4 };
+
+struct Segment {
+    uint64_t j0, j1;   // [j0, j1) argument indices
+    int e_out;
+};
+
+struct BlockPlan {
+    uint64_t start, length, first_sub;
+    int e_out;
+};
+
+// Validation of one job (domain of this build); TMD_OK when usable.
+tmd_status validate_job(const tmd_job& job);
+
+// e(f(X_j)) (Def. 1) for argument index j.
+int output_exponent(const tmd_job& job, uint64_t j);
+
+// Output-binade segments of the job's slice (cuts decided exactly).
+tmd_status plan_segments(const tmd_job& job, std::vector<Segment>& segs);
+
+// Number of blocks / sub-intervals of a job from its segments.
+void plan_counts(const tmd_job& job, const std::vector<Segment>& segs,
+                 uint64_t* n_blocks, uint64_t* n_subints);
+
+// The block with plan index b (0-based).  Returns false past the end.
+bool plan_block(const tmd_job& job, const std::vector<Segment>& segs, uint64_t b,
+                BlockPlan* out);
+
+// log2 of the breakpoint scale s on a segment with output exponent e_out.
+int scale_log2(const tmd_job& job, int e_out);
+
+// Coefficients c_0..c_d (limbs each, little-endian) and the 2d+1 table words
+// of the block.  TMD_EUNSUPPORTED if the rounding could not be decided.
+tmd_status block_table(const tmd_job& job, const BlockPlan& blk, uint64_t* coeffs,
+                       uint64_t* table);
+
+}  // namespace tmd

@@ -1,0 +1,586 @@
+// CUDA kernels of the hot path (sm_103a).
+//
+//   generation  Sect. IV-B/IV-C: each lane owns a packet of nu consecutive
+//               sub-intervals of one Taylor block; it jumps to the packet's
+//               first sub-interval with the straightforward shift (binomial
+//               Toeplitz product of the block's difference column) and then
+//               steps the tabulated differences with W-bit carry-chain adds.
+//   search      Sect. III-B: Algorithm 4 (regular continued-fraction lower
+//               bound, unrolled twice) on the 64-bit search words of each
+//               line, one line per lane; lines whose bound falls below the
+//               threshold are resolved exactly by the whole warp (every
+//               argument of the line, smallest argmin kept) and emitted by
+//               warp ballot with one atomic per warp (Sect. III-C
+//               compaction of failing sub-domains).
+//
+// Quotients: GB300 has no integer divide instruction and a slow FP64 unit,
+// so floor(a/b) comes from an FP32 estimate built from 32-bit halves
+// (I2F.U32 + FFMA), one reciprocal (MUFU) shared by both divisions of a
+// half-step, and one integer correction.  With kf = fl(a) * rcp(fl(b)) the
+// relative error is below 2^-21 (two round-toward-zero conversions of at most
+// 2^-22 each after the FMA, 1 ulp for rcp.approx, half an ulp for the
+// product), so for kf < 2^19 the estimate floor(max(kf - 1/2, 0)) is
+// floor(a/b) or one less; one compare-and-subtract finishes it.  Larger
+// quotients (rare: Gauss-Kuzmin tail) take an exact shift-subtract division.
+#include <cuda_runtime.h>
+
+#include "dev.hpp"
+
+namespace tmd {
+
+#define FULLMASK 0xffffffffu
+
+// ---------------------------------------------------------------- W-bit words
+template <int L>
+struct Word {
+    uint64_t l[L];
+};
+
+template <int L>
+__device__ __forceinline__ void w_add(Word<L>& a, const Word<L>& b) {
+    if constexpr (L == 1) {
+        a.l[0] += b.l[0];
+    } else if constexpr (L == 2) {
+        asm("add.cc.u64 %0, %0, %2;\n\taddc.u64 %1, %1, %3;"
+            : "+l"(a.l[0]), "+l"(a.l[1])
+            : "l"(b.l[0]), "l"(b.l[1]));
+    } else {
+        asm("add.cc.u64 %0, %0, %3;\n\taddc.cc.u64 %1, %1, %4;\n\taddc.u64 %2, %2, %5;"
+            : "+l"(a.l[0]), "+l"(a.l[1]), "+l"(a.l[2])
+            : "l"(b.l[0]), "l"(b.l[1]), "l"(b.l[2]));
+    }
+}
+
+// a * c mod 2^W
+template <int L>
+__device__ __forceinline__ Word<L> w_mul_u64(const Word<L>& a, uint64_t c) {
+    Word<L> r;
+    uint64_t carry = 0;
+#pragma unroll
+    for (int i = 0; i < L; i++) {
+        uint64_t lo = a.l[i] * c;
+        uint64_t hi = __umul64hi(a.l[i], c);
+        r.l[i] = lo + carry;
+        carry = hi + (r.l[i] < lo ? 1ull : 0ull);
+    }
+    return r;
+}
+
+// binom(n, j), j = 0..4, exact for n <= 2^16
+__device__ __forceinline__ void binomials(uint64_t n, uint64_t* c) {
+    c[0] = 1;
+    c[1] = n;
+    c[2] = n * (n - 1) / 2;
+    c[3] = c[2] * (n - 2) / 3;
+    c[4] = c[3] * (n - 3) / 4;
+}
+
+// ------------------------------------------------------------------ quotients
+__device__ __forceinline__ float u64_to_f32_rz(uint64_t x) {
+    return __fmaf_rz(__uint2float_rz((uint32_t)(x >> 32)), 4294967296.0f,
+                     __uint2float_rz((uint32_t)x));
+}
+
+__device__ __forceinline__ float rcp_approx(float x) {
+    float r;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
+
+// floor(a/b) and a mod b for b > 0 given rb ~ 1/b; false if the quotient
+// estimate is too large for the fast path.
+__device__ __forceinline__ bool divmod_fast(uint64_t a, uint64_t b, float rb, uint64_t& k,
+                                            uint64_t& r) {
+    float kf = u64_to_f32_rz(a) * rb;
+    bool ok = kf < 524288.0f;  // 2^19
+    float y = fmaxf(fminf(kf, 524288.0f) - 0.5f, 0.0f);
+    uint32_t k0 = __float_as_uint(__fadd_rz(y, 8388608.0f)) - 0x4B000000u;
+    uint64_t rr = a - (uint64_t)k0 * b;
+    bool up = rr >= b;
+    r = up ? rr - b : rr;
+    k = (uint64_t)k0 + (up ? 1u : 0u);
+    return ok;
+}
+
+// exact floor(a/b), a mod b (b > 0) by shift-subtract
+__device__ __noinline__ void divmod_slow(uint64_t a, uint64_t b, uint64_t& k, uint64_t& r) {
+    uint64_t quo = 0, rem = 0;
+    int top = a ? 63 - __clzll((long long)a) : -1;
+    for (int i = top; i >= 0; i--) {
+        bool hi = (rem >> 63) != 0;
+        rem = (rem << 1) | ((a >> i) & 1ull);
+        if (hi || rem >= b) {
+            rem -= b;
+            quo |= 1ull << i;
+        }
+    }
+    k = quo;
+    r = rem;
+}
+
+__device__ __forceinline__ uint32_t sat_madd(uint32_t u, uint64_t k, uint32_t v, uint32_t n) {
+    uint32_t kc = (uint32_t)(k < (uint64_t)n ? k : (uint64_t)n);
+    uint32_t s = u + kc * v;  // u, v < n <= 2^16, kc <= 2^16: no wrap
+    return s < n ? s : n;
+}
+
+// Algorithm 4 lower bound of min_{0<=x<n} (B - A x) mod 2^64 on integers
+// scaled by 2^64: p <- A, q <- 2^64, d <- B, u <- 1, v <- 0; returns d when
+// u + v >= n.  Endings of a rational expansion: p = 0 -> d mod q (already
+// reduced), q = 0 -> d.  *hs counts half-steps.
+__device__ __forceinline__ uint64_t cf_lower_bound(uint64_t B, uint64_t A, uint32_t n, uint32_t* hs) {
+    if (A == 0) {
+        *hs = 0;
+        return B;
+    }
+    uint64_t p = A, q, d = B, k, r, kd, rd;
+    uint32_t u = 1, v = 0, h = 1;
+    // first half-step with q = 2^64: floor(2^64/p) = floor((2^64 - p)/p) + 1
+    {
+        float rp = rcp_approx(u64_to_f32_rz(p));
+        bool ok = divmod_fast(0ull - p, p, rp, k, r);
+        ok &= divmod_fast(d, p, rp, kd, rd);
+        if (!ok) {
+            divmod_slow(0ull - p, p, k, r);
+            divmod_slow(d, p, kd, rd);
+        }
+        q = r;
+        d = rd;
+        // u = 1 + (k + 1) * 0
+    }
+    if (1u >= n || q == 0) {
+        *hs = h;
+        return d;
+    }
+#pragma unroll 1
+    for (int guard = 0; guard < 64; guard++) {
+        // second half: k = floor(p/q); p -= k q; v += k u; if d >= p: d = (d - p) mod q
+        {
+            float rq = rcp_approx(u64_to_f32_rz(q));
+            bool ok = divmod_fast(p, q, rq, k, r);
+            if (!ok) divmod_slow(p, q, k, r);
+            p = r;
+            v = sat_madd(v, k, u, n);
+            bool ge = d >= p;
+            uint64_t e = ge ? d - p : 0ull;  // < k q: the quotient is at most k
+            bool ok2 = divmod_fast(e, q, rq, kd, rd);
+            if (!ok2) divmod_slow(e, q, kd, rd);
+            d = ge ? rd : d;
+            h++;
+            if (u + v >= n) break;
+        }
+        if (p == 0) break;  // d was reduced mod q just above
+        // first half: k = floor(q/p); q -= k p; u += k v; d = d mod p
+        {
+            float rp = rcp_approx(u64_to_f32_rz(p));
+            bool ok = divmod_fast(q, p, rp, k, r);
+            ok &= divmod_fast(d, p, rp, kd, rd);
+            if (!ok) {
+                divmod_slow(q, p, k, r);
+                divmod_slow(d, p, kd, rd);
+            }
+            q = r;
+            d = rd;
+            u = sat_madd(u, k, v, n);
+            h++;
+            if (u + v >= n || q == 0) break;
+        }
+    }
+    *hs = h;
+    return d;
+}
+
+// -------------------------------------------------------------- compaction
+__device__ __forceinline__ void emit_warp(bool has, uint32_t job, uint32_t sub, uint64_t arg,
+                                          uint64_t val, tmd_candidate* cand, uint64_t cap,
+                                          uint64_t* count) {
+    unsigned mask = __ballot_sync(FULLMASK, has);
+    if (mask == 0) return;
+    const int lane = threadIdx.x & 31;
+    const int leader = __ffs(mask) - 1;
+    unsigned long long base = 0;
+    if (lane == leader) base = atomicAdd((unsigned long long*)count, (unsigned long long)__popc(mask));
+    base = __shfl_sync(FULLMASK, base, leader);
+    if (has) {
+        uint64_t idx = base + (uint64_t)__popc(mask & ((1u << lane) - 1u));
+        if (idx < cap) {
+            tmd_candidate c;
+            c.job = job;
+            c.subint = sub;
+            c.arg_index = arg;
+            c.value = val;
+            cand[idx] = c;
+        }
+    }
+}
+
+// Exact resolution of the flagged lines of a warp, one line at a time by all
+// 32 lanes (x = lane, lane + 32, ...), then compaction.
+__device__ __noinline__ void resolve_and_emit(bool fail, uint64_t B, uint64_t A, uint32_t n,
+                                              uint64_t Tm, bool all_hits, uint32_t job,
+                                              uint32_t sub, uint64_t arg_base,
+                                              tmd_candidate* cand, uint64_t cap, uint64_t* count) {
+    const int lane = threadIdx.x & 31;
+    unsigned fails = __ballot_sync(FULLMASK, fail);
+    bool have = false;
+    uint64_t my_min = 0;
+    uint32_t my_x = 0;
+    while (fails) {
+        const int src = __ffs(fails) - 1;
+        fails &= fails - 1u;
+        const uint64_t Bs = __shfl_sync(FULLMASK, B, src);
+        const uint64_t As = __shfl_sync(FULLMASK, A, src);
+        const uint32_t ns = __shfl_sync(FULLMASK, n, src);
+        const uint32_t js = __shfl_sync(FULLMASK, job, src);
+        const uint32_t ss = __shfl_sync(FULLMASK, sub, src);
+        const uint64_t ab = __shfl_sync(FULLMASK, arg_base, src);
+        uint64_t best = ~0ull;
+        uint32_t bx = 0xffffffffu;
+        uint64_t val = Bs - As * (uint64_t)lane;
+        const uint64_t step = As * 32ull;
+        const uint32_t trips = (ns + 31u) >> 5;
+        for (uint32_t t = 0; t < trips; t++) {
+            const uint32_t x = t * 32u + (uint32_t)lane;
+            const bool ok = x < ns;
+            if (ok && val < best) {
+                best = val;
+                bx = x;
+            }
+            if (all_hits) emit_warp(ok && val < Tm, js, ss, ab + x, val, cand, cap, count);
+            val -= step;
+        }
+#pragma unroll
+        for (int off = 16; off; off >>= 1) {
+            uint64_t ob = __shfl_xor_sync(FULLMASK, best, off);
+            uint32_t ox = __shfl_xor_sync(FULLMASK, bx, off);
+            if (ob < best || (ob == best && ox < bx)) {
+                best = ob;
+                bx = ox;
+            }
+        }
+        if (lane == src) {
+            have = true;
+            my_min = best;
+            my_x = bx;
+        }
+    }
+    if (!all_hits) emit_warp(have && my_min < Tm, job, sub, arg_base + my_x, my_min, cand, cap, count);
+}
+
+__device__ __forceinline__ void flush_stats(uint64_t* stats, uint64_t lines, uint64_t fail, uint64_t half) {
+#pragma unroll
+    for (int off = 16; off; off >>= 1) {
+        lines += __shfl_xor_sync(FULLMASK, lines, off);
+        fail += __shfl_xor_sync(FULLMASK, fail, off);
+        half += __shfl_xor_sync(FULLMASK, half, off);
+    }
+    if ((threadIdx.x & 31) == 0) {
+        atomicAdd((unsigned long long*)&stats[ST_LINES], (unsigned long long)lines);
+        atomicAdd((unsigned long long*)&stats[ST_FAIL], (unsigned long long)fail);
+        atomicAdd((unsigned long long*)&stats[ST_HALF], (unsigned long long)half);
+    }
+}
+
+// ---------------------------------------------------------- packet machinery
+template <int L, int D>
+struct Packet {
+    Word<L> d0[D + 1];  // Delta^l g0 at the current sub-interval, l = 0..D
+    Word<L> d1[D];      // Delta^l g1, l = 0..D-1
+    DevBlock blk;
+    uint32_t i0, i1;    // sub-interval range of the packet within the block
+    bool active;
+};
+
+template <int L, int D>
+__device__ __forceinline__ void packet_init(Packet<L, D>& P, const DevTask& t, const DevJob& job,
+                                            const LaunchArgs& a) {
+    const int lane = threadIdx.x & 31;
+    P.active = (uint32_t)lane < t.count;
+    const uint64_t g = t.g0 + (P.active ? (uint64_t)lane : 0ull);
+    uint32_t lo = job.block_off, hi = job.block_off + job.n_blocks - 1;
+    while (lo < hi) {
+        uint32_t mid = (lo + hi + 1) >> 1;
+        if (a.blocks[mid].packet_off <= g)
+            lo = mid;
+        else
+            hi = mid - 1;
+    }
+    P.blk = a.blocks[lo];
+    const uint64_t pk = g - P.blk.packet_off;
+    P.i0 = (uint32_t)(pk * job.nu);
+    P.i1 = min(P.i0 + job.nu, P.blk.n_sub);
+    const uint64_t* tw = a.tables + P.blk.table_off;
+    Word<L> t0[D + 1], t1[D];
+#pragma unroll
+    for (int w = 0; w <= D; w++)
+#pragma unroll
+        for (int l = 0; l < L; l++) t0[w].l[l] = __ldg(tw + w * L + l);
+#pragma unroll
+    for (int w = 0; w < D; w++)
+#pragma unroll
+        for (int l = 0; l < L; l++) t1[w].l[l] = __ldg(tw + (D + 1 + w) * L + l);
+    // straightforward shift to sub-interval i0: Delta^l(i0) = sum_{k>=l} binom(i0, k-l) Delta^k(0)
+    uint64_t c[5];
+    binomials(P.i0, c);
+#pragma unroll
+    for (int l = 0; l <= D; l++) {
+        P.d0[l] = t0[l];
+#pragma unroll
+        for (int k = l + 1; k <= D; k++) w_add<L>(P.d0[l], w_mul_u64<L>(t0[k], c[k - l]));
+    }
+#pragma unroll
+    for (int l = 0; l < D; l++) {
+        P.d1[l] = t1[l];
+#pragma unroll
+        for (int k = l + 1; k < D; k++) w_add<L>(P.d1[l], w_mul_u64<L>(t1[k], c[k - l]));
+    }
+}
+
+// one tabulated-difference step: Delta^l(i+1) = Delta^l(i) + Delta^(l+1)(i), l ascending
+template <int L, int D>
+__device__ __forceinline__ void packet_step(Packet<L, D>& P) {
+#pragma unroll
+    for (int l = 0; l < D; l++) w_add<L>(P.d0[l], P.d0[l + 1]);
+#pragma unroll
+    for (int l = 0; l + 1 < D; l++) w_add<L>(P.d1[l], P.d1[l + 1]);
+}
+
+// search words of the current line (top limb of b + 2^(W-m), top limb of -alpha)
+template <int L, int D>
+__device__ __forceinline__ void packet_words(const Packet<L, D>& P, uint32_t m, uint64_t& B, uint64_t& A) {
+    B = P.d0[0].l[L - 1] + (1ull << (64 - m));
+    uint64_t low = 0;
+#pragma unroll
+    for (int l = 0; l + 1 < L; l++) low |= P.d1[0].l[l];
+    A = ~P.d1[0].l[L - 1] + (low == 0 ? 1ull : 0ull);
+}
+
+template <int L, int D>
+__device__ __forceinline__ void fused_task(const DevTask& t, const LaunchArgs& a, uint64_t& st_lines,
+                                           uint64_t& st_fail, uint64_t& st_half) {
+    const DevJob job = a.jobs[t.job];
+    Packet<L, D> P;
+    packet_init<L, D>(P, t, job, a);
+    const uint32_t N = 1u << job.log2_N;
+    const bool all_hits = (job.flags & TMD_ALL_HITS) != 0;
+#pragma unroll 1
+    for (uint32_t it = 0; it < job.nu; it++) {
+        const uint32_t i = P.i0 + it;
+        const bool valid = P.active && i < P.i1;
+        uint64_t B, A;
+        packet_words<L, D>(P, job.m, B, A);
+        const uint64_t off = (uint64_t)i * N;
+        const uint32_t n = valid ? (uint32_t)min((uint64_t)N, P.blk.length - off) : 1u;
+        uint32_t hs = 0;
+        uint64_t lb = ~0ull;
+        if (valid) lb = cf_lower_bound(B, A, n, &hs);
+        const bool fail = valid && lb < job.Tm;
+        st_lines += valid ? 1 : 0;
+        st_fail += fail ? 1 : 0;
+        st_half += hs;
+        if (__any_sync(FULLMASK, fail))
+            resolve_and_emit(fail, B, A, n, job.Tm, all_hits, t.job, (uint32_t)(P.blk.first_sub + i),
+                             P.blk.start + off, a.cand, a.cap, a.count);
+        packet_step<L, D>(P);
+    }
+}
+
+template <int L, int D>
+__device__ __forceinline__ void generate_task(const DevTask& t, const LaunchArgs& a) {
+    const DevJob job = a.jobs[t.job];
+    Packet<L, D> P;
+    packet_init<L, D>(P, t, job, a);
+#pragma unroll 1
+    for (uint32_t it = 0; it < job.nu; it++) {
+        const uint32_t i = P.i0 + it;
+        if (P.active && i < P.i1) {
+            uint64_t B, A;
+            packet_words<L, D>(P, job.m, B, A);
+            const uint64_t line = job.line_off + P.blk.first_sub + i;
+            a.lin_B[line] = B;
+            a.lin_A[line] = A;
+        }
+        packet_step<L, D>(P);
+    }
+}
+
+// ------------------------------------------------------------------- kernels
+template <int L, int D>
+__global__ void __launch_bounds__(256) k_fused(LaunchArgs a) {
+    const uint64_t w = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    if (w >= a.n_tasks) return;  // whole warp
+    uint64_t sl = 0, sf = 0, sh = 0;
+    const DevTask t = a.tasks[w];
+    fused_task<L, D>(t, a, sl, sf, sh);
+    flush_stats(a.stats, sl, sf, sh);
+}
+
+template <int L, int D>
+__global__ void __launch_bounds__(256) k_generate(LaunchArgs a) {
+    const uint64_t w = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    if (w >= a.n_tasks) return;
+    const DevTask t = a.tasks[w];
+    generate_task<L, D>(t, a);
+}
+
+// Persistent form: a grid of resident CTAs; each warp takes the next task
+// from a device counter until the list is exhausted (no waiting on other
+// warps: a single atomicAdd per task).
+__global__ void __launch_bounds__(256) k_persistent(LaunchArgs a) {
+    const int lane = threadIdx.x & 31;
+    uint64_t sl = 0, sf = 0, sh = 0;
+    for (;;) {
+        uint32_t t = 0;
+        if (lane == 0) t = atomicAdd(a.queue_head, 1u);
+        t = __shfl_sync(FULLMASK, t, 0);
+        if ((uint64_t)t >= a.n_tasks) break;
+        const DevTask task = a.tasks[t];
+        const uint32_t key = a.jobs[task.job].L * 8u + a.jobs[task.job].d;
+        switch (key) {
+            case 9: fused_task<1, 1>(task, a, sl, sf, sh); break;
+            case 10: fused_task<1, 2>(task, a, sl, sf, sh); break;
+            case 11: fused_task<1, 3>(task, a, sl, sf, sh); break;
+            case 12: fused_task<1, 4>(task, a, sl, sf, sh); break;
+            case 17: fused_task<2, 1>(task, a, sl, sf, sh); break;
+            case 18: fused_task<2, 2>(task, a, sl, sf, sh); break;
+            case 19: fused_task<2, 3>(task, a, sl, sf, sh); break;
+            case 20: fused_task<2, 4>(task, a, sl, sf, sh); break;
+            case 25: fused_task<3, 1>(task, a, sl, sf, sh); break;
+            case 26: fused_task<3, 2>(task, a, sl, sf, sh); break;
+            case 27: fused_task<3, 3>(task, a, sl, sf, sh); break;
+            case 28: fused_task<3, 4>(task, a, sl, sf, sh); break;
+            default: break;
+        }
+    }
+    flush_stats(a.stats, sl, sf, sh);
+}
+
+// Line search.  JOBS: the lines written by k_generate for the resident plan
+// (line index -> job -> block by binary search).  RAW: caller arrays with
+// per-line lengths; record = (0, line, x, value).
+
+template <bool RAW>
+__global__ void __launch_bounds__(256) k_search_lines(LineArgs a) {
+    const uint64_t w = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const uint64_t s = (w << 5) + (threadIdx.x & 31);
+    if ((w << 5) >= a.n_lines) return;  // whole warp
+    const bool valid = s < a.n_lines;
+    uint64_t B = 0, A = 0, Tm = a.Tm, arg_base = 0;
+    uint32_t n = 1, job = 0, sub = 0, flags = a.flags;
+    if (valid) {
+        B = a.B[s];
+        A = a.A[s];
+        if (RAW) {
+            uint32_t ln = a.len[s];
+            if (ln == 0 || ln > 65536u) {
+                atomicOr(a.err, 1u);
+                ln = ln == 0 ? 1u : 65536u;
+            }
+            n = ln;
+            sub = (uint32_t)s;
+        } else {
+            uint32_t lo = 0, hi = a.n_jobs - 1;
+            while (lo < hi) {
+                uint32_t mid = (lo + hi + 1) >> 1;
+                if (a.jobs[mid].line_off <= s) lo = mid; else hi = mid - 1;
+            }
+            const DevJob& jb = a.jobs[lo];
+            job = lo;
+            Tm = jb.Tm;
+            flags = jb.flags;
+            const uint64_t js = s - jb.line_off;
+            uint32_t b0 = jb.block_off, b1 = jb.block_off + jb.n_blocks - 1;
+            while (b0 < b1) {
+                uint32_t mid = (b0 + b1 + 1) >> 1;
+                if (a.blocks[mid].first_sub <= js) b0 = mid; else b1 = mid - 1;
+            }
+            const DevBlock& bk = a.blocks[b0];
+            const uint64_t i = js - bk.first_sub;
+            const uint64_t N = 1ull << jb.log2_N;
+            n = (uint32_t)min(N, bk.length - i * N);
+            sub = (uint32_t)js;
+            arg_base = bk.start + i * N;
+        }
+    }
+    uint32_t hs = 0;
+    uint64_t lb = ~0ull;
+    if (valid) lb = cf_lower_bound(B, A, n, &hs);
+    const bool fail = valid && lb < Tm;
+    // all lanes of a warp share ALL_HITS in practice; take the warp's OR
+    const bool all_hits = __any_sync(FULLMASK, valid && (flags & TMD_ALL_HITS));
+    if (__any_sync(FULLMASK, fail))
+        resolve_and_emit(fail, B, A, n, Tm, all_hits, job, sub, arg_base, a.cand, a.cap, a.count);
+    flush_stats(a.stats, valid ? 1 : 0, fail ? 1 : 0, hs);
+}
+
+__global__ void __launch_bounds__(256) k_lower_bounds(const uint64_t* B, const uint64_t* A,
+                                                      const uint32_t* len, uint64_t n, uint64_t* lb,
+                                                      uint32_t* hs_out, uint32_t* err) {
+    const uint64_t s = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= n) return;
+    uint32_t ln = len[s];
+    if (ln == 0 || ln > 65536u) {
+        atomicOr(err, 1u);
+        ln = ln == 0 ? 1u : 65536u;
+    }
+    uint32_t hs = 0;
+    lb[s] = cf_lower_bound(B[s], A[s], ln, &hs);
+    if (hs_out) hs_out[s] = hs;
+}
+
+// --------------------------------------------------------------- launchers
+typedef void (*TaskKernel)(LaunchArgs);
+
+static TaskKernel fused_kernel(uint32_t L, uint32_t D) {
+    static const TaskKernel tab[3][4] = {
+        {k_fused<1, 1>, k_fused<1, 2>, k_fused<1, 3>, k_fused<1, 4>},
+        {k_fused<2, 1>, k_fused<2, 2>, k_fused<2, 3>, k_fused<2, 4>},
+        {k_fused<3, 1>, k_fused<3, 2>, k_fused<3, 3>, k_fused<3, 4>}};
+    return tab[L - 1][D - 1];
+}
+
+static TaskKernel generate_kernel(uint32_t L, uint32_t D) {
+    static const TaskKernel tab[3][4] = {
+        {k_generate<1, 1>, k_generate<1, 2>, k_generate<1, 3>, k_generate<1, 4>},
+        {k_generate<2, 1>, k_generate<2, 2>, k_generate<2, 3>, k_generate<2, 4>},
+        {k_generate<3, 1>, k_generate<3, 2>, k_generate<3, 3>, k_generate<3, 4>}};
+    return tab[L - 1][D - 1];
+}
+
+cudaError_t launch_tasks(bool fused, uint32_t L, uint32_t D, const LaunchArgs& a, cudaStream_t s) {
+    if (a.n_tasks == 0) return cudaSuccess;
+    const uint64_t warps_per_cta = 8;
+    const uint64_t ctas = (a.n_tasks + warps_per_cta - 1) / warps_per_cta;
+    TaskKernel k = fused ? fused_kernel(L, D) : generate_kernel(L, D);
+    k<<<(unsigned)ctas, 256, 0, s>>>(a);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_persistent(const LaunchArgs& a, int ctas, cudaStream_t s) {
+    k_persistent<<<ctas, 256, 0, s>>>(a);
+    return cudaGetLastError();
+}
+
+cudaError_t persistent_occupancy(int* blocks_per_sm) {
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, k_persistent, 256, 0);
+}
+
+cudaError_t launch_search_lines(bool raw, const LineArgs& a, cudaStream_t s) {
+    if (a.n_lines == 0) return cudaSuccess;
+    const uint64_t warps = (a.n_lines + 31) / 32;
+    const uint64_t ctas = (warps + 7) / 8;
+    if (raw)
+        k_search_lines<true><<<(unsigned)ctas, 256, 0, s>>>(a);
+    else
+        k_search_lines<false><<<(unsigned)ctas, 256, 0, s>>>(a);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_lower_bounds(const uint64_t* B, const uint64_t* A, const uint32_t* len, uint64_t n,
+                                uint64_t* lb, uint32_t* hs, uint32_t* err, cudaStream_t s) {
+    if (n == 0) return cudaSuccess;
+    k_lower_bounds<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(B, A, len, n, lb, hs, err);
+    return cudaGetLastError();
+}
+
+}  // namespace tmd

@@ -1,0 +1,162 @@
+"""GPU parity of the search stage through the C ABI: the Algorithm 4 lower
+bound value by value, and candidate lists record by record against brute
+force, on random and degenerate lines."""
+import random
+
+import pytest
+
+from gpu_util import to_u32_list, to_u64_list, u32_tensor, u64_tensor
+from oracle import candidates as oc
+from oracle import search
+
+torch = pytest.importorskip("torch")
+tmd = pytest.importorskip("paper_1211_3056_gb300")
+pytestmark = pytest.mark.gpu
+
+M64 = (1 << 64) - 1
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    c = tmd.Context(0)
+    yield c
+    c.close()
+
+
+def edge_lines():
+    """Degenerate lines: a = 0, powers of two (the expansion ends), tiny a
+    (huge first quotient: exact slow division), a near 1, b = 0, N = 1."""
+    out = []
+    for A in [0, 1, 2, 3, 1 << 20, 1 << 44, 1 << 63, M64, M64 - 1, (1 << 63) + 1, 12345,
+              0x9E3779B97F4A7C15, 1 << 62, 3 << 61, 0x5555555555555555]:
+        for B in [0, 1, M64, 1 << 63, 0x243F6A8885A308D3]:
+            for n in [1, 2, 31, 32, 33, 1000, 1 << 14, 1 << 16]:
+                out.append((B, A, n))
+    return out
+
+
+def random_lines(n, seed):
+    rng = random.Random(seed)
+    out = []
+    for _ in range(n):
+        kind = rng.random()
+        if kind < 0.7:
+            A = rng.getrandbits(64)
+        elif kind < 0.85:
+            A = rng.getrandbits(rng.randrange(1, 64))       # small a: large quotients
+        else:
+            A = M64 - rng.getrandbits(rng.randrange(1, 64))  # a near 1
+        out.append((rng.getrandbits(64), A, rng.choice([1, 7, 64, 256, 1000, 1 << 12, 1 << 14, 1 << 16])))
+    return out
+
+
+def run_lower_bounds(ctx, lines):
+    B = u64_tensor([l[0] for l in lines])
+    A = u64_tensor([l[1] for l in lines])
+    n = u32_tensor([l[2] for l in lines])
+    lb = torch.empty_like(B)
+    hs = torch.empty_like(n)
+    tmd.tmd_lower_bounds(ctx, B, A, n, lb, hs)
+    torch.cuda.synchronize()
+    return to_u64_list(lb), to_u32_list(hs)
+
+
+def test_lower_bound_equals_algorithm4_edges(ctx):
+    lines = edge_lines()
+    lb, hs = run_lower_bounds(ctx, lines)
+    for (B, A, n), g, h in zip(lines, lb, hs):
+        want, _, whs = search.regular_lb_unrolled(B, A, n)
+        assert (g, h) == (want, whs), (hex(B), hex(A), n)
+
+
+def test_lower_bound_equals_algorithm4_random(ctx):
+    lines = random_lines(20000, 5)
+    lb, hs = run_lower_bounds(ctx, lines)
+    for (B, A, n), g, h in zip(lines, lb, hs):
+        want, _, whs = search.regular_lb_unrolled(B, A, n)
+        assert (g, h) == (want, whs), (hex(B), hex(A), n)
+
+
+def brute_records(lines, m, all_hits=False):
+    import numpy as np
+    T = 1 << (65 - m)
+    B = np.array([l[0] for l in lines], dtype=np.uint64)
+    A = np.array([l[1] for l in lines], dtype=np.uint64)
+    n = np.array([l[2] for l in lines], dtype=np.uint32)
+    if all_hits:
+        recs = [(0, i, x, v) for (i, x, v) in oc.brute_hits_many(B, A, n, T)]
+    else:
+        mins, args = oc.brute_min_many(B, A, n)
+        recs = [(0, i, int(args[i]), int(mins[i])) for i in range(len(lines)) if int(mins[i]) < T]
+    return sorted(recs, key=lambda r: (r[0], r[2], r[3]))
+
+
+def sort_by_line(recs):
+    return sorted(recs, key=lambda r: (r[1], r[2], r[3]))
+
+
+@pytest.mark.parametrize("m", [6, 10, 20])
+def test_search_lines_match_brute_force(ctx, m):
+    lines = random_lines(3000, 100 + m) + edge_lines()
+    B = u64_tensor([l[0] for l in lines])
+    A = u64_tensor([l[1] for l in lines])
+    n = u32_tensor([l[2] for l in lines])
+    d_cand, d_count = tmd.alloc_candidates(len(lines) + 16)
+    tmd.tmd_search_lines(ctx, B, A, n, m, 0, d_cand, d_count)
+    got, count = tmd.tmd_candidates(ctx, d_cand, d_count)
+    want = brute_records(lines, m)
+    assert count == len(want)
+    assert sort_by_line(got) == sort_by_line(want)
+    st = tmd.tmd_stats_read(ctx)
+    assert st["lines"] == len(lines)
+    # the filter flags exactly the lines whose Algorithm 4 bound is below T_m
+    T = 1 << (65 - m)
+    flagged = sum(1 for (Bv, Av, nv) in lines if search.regular_lb_unrolled(Bv, Av, nv)[0] < T)
+    assert st["filter_fail"] == flagged
+
+
+def test_search_lines_all_hits(ctx):
+    rng = random.Random(9)
+    lines = [(rng.getrandbits(64), rng.getrandbits(64), rng.choice([100, 4096, 65536])) for _ in range(400)]
+    lines += [(5, 1 << 60, 64), (0, 0, 100), (7, 1 << 63, 1000)]     # ties and repeated values
+    B = u64_tensor([l[0] for l in lines])
+    A = u64_tensor([l[1] for l in lines])
+    n = u32_tensor([l[2] for l in lines])
+    d_cand, d_count = tmd.alloc_candidates(1 << 16)
+    tmd.tmd_search_lines(ctx, B, A, n, 12, tmd.TMD_ALL_HITS, d_cand, d_count)
+    got, count = tmd.tmd_candidates(ctx, d_cand, d_count)
+    want = brute_records(lines, 12, all_hits=True)
+    assert count == len(want)
+    assert sort_by_line(got) == sort_by_line(want)
+
+
+def test_overflow_keeps_exact_count(ctx):
+    rng = random.Random(3)
+    lines = [(rng.getrandbits(64), rng.getrandbits(64), 4096) for _ in range(2000)]
+    B = u64_tensor([l[0] for l in lines])
+    A = u64_tensor([l[1] for l in lines])
+    n = u32_tensor([l[2] for l in lines])
+    want = brute_records(lines, 6)
+    d_cand, d_count = tmd.alloc_candidates(10)
+    tmd.tmd_search_lines(ctx, B, A, n, 6, 0, d_cand, d_count)
+    got, count = tmd.tmd_candidates(ctx, d_cand, d_count)
+    assert count == len(want) > 10
+    assert len(got) == 10 and set(got) <= set(want)
+
+
+def test_empty_input(ctx):
+    B = torch.empty(0, dtype=torch.int64, device="cuda:0")
+    d_cand, d_count = tmd.alloc_candidates(4)
+    tmd.tmd_search_lines(ctx, B, B, torch.empty(0, dtype=torch.int32, device="cuda:0"), 20, 0,
+                         d_cand, d_count)
+    got, count = tmd.tmd_candidates(ctx, d_cand, d_count)
+    assert got == [] and count == 0
+
+
+def test_bad_lengths_reported(ctx):
+    B = u64_tensor([1, 2, 3])
+    n = u32_tensor([5, 0, 70000])
+    d_cand, d_count = tmd.alloc_candidates(4)
+    tmd.tmd_search_lines(ctx, B, B, n, 20, 0, d_cand, d_count)
+    with pytest.raises(tmd.TmdError):
+        tmd.tmd_candidates(ctx, d_cand, d_count)

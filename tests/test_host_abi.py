@@ -1,0 +1,112 @@
+"""CPU tests of the C ABI: the library loads, exports every declared symbol,
+and its host-side planning and correctly rounded tables equal the oracle's."""
+import os
+import random
+import re
+
+import pytest
+
+import workloads as wl
+from conftest import ROOT
+from oracle import plan, poly, search
+
+tmd = pytest.importorskip("paper_1211_3056_gb300")
+
+
+def declared_functions():
+    names = set()
+    for fn in os.listdir(os.path.join(ROOT, "include")):
+        if fn.endswith(".h"):
+            src = open(os.path.join(ROOT, "include", fn)).read()
+            src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+            names |= set(re.findall(r"\b(tmd_\w+)\s*\(", src))
+    return names
+
+
+def test_exports_every_declared_symbol():
+    import ctypes
+    lib = ctypes.CDLL(tmd._lib.LIB_PATH)
+    names = declared_functions()
+    assert len(names) >= 12
+    for n in sorted(names):
+        assert hasattr(lib, n), n
+    assert set(tmd._lib.SIGNATURES) <= names
+
+
+def test_version_and_status_strings():
+    assert "sm_103a" in tmd.tmd_version()
+    assert tmd._lib.status_str(0) == "ok"
+
+
+def oracle_table(job, blk):
+    W = 64 * job.limbs
+    N = 1 << job.log2_N
+    mod = 1 << W
+    c = poly.taylor_coeffs(job, blk)
+    g0 = [poly.horner(c, i * N, W) for i in range(job.d + 1)]
+    g1 = [(poly.horner(c, i * N + 1, W) - poly.horner(c, i * N, W)) % mod for i in range(job.d)]
+    t0 = [r[0] % mod for r in search.forward_differences(g0)]
+    t1 = [r[0] % mod for r in search.forward_differences(g1)]
+    return c, t0 + t1
+
+
+HOST_JOBS = [
+    wl.toy_job(),
+    wl.plain_job(),
+    wl.Job(wl.FUNC_EXP2, 1, 24, 16, 8, 2, 12, 1, 0, 1 << 12),
+    wl.Job(wl.FUNC_EXP, 1, 53, 40, 12, 4, 20, 3, 1 << 40, 1 << 30),
+    wl.Job(wl.FUNC_EXP, 2, 40, 30, 10, 3, 20, 2, 0, 1 << 39),             # three cuts (8, 16, 32)
+    wl.Job(wl.FUNC_LOG, 2, 53, 40, 14, 3, 24, 3, 3 << 49, 1 << 44),        # crosses e
+    wl.Job(wl.FUNC_LOG, 3, 30, 20, 8, 2, 12, 2, 0, 1 << 29, wl.FLAG_BP_DIRECTED),
+    wl.Job(wl.FUNC_EXP2, 0, 53, 42, 16, 1, 20, 1, 12345 << 20, 1 << 24),
+    wl.Job(wl.FUNC_EXP, -5, 53, 40, 14, 2, 18, 2, 999 << 18, 1 << 22),
+] + wl.batched_jobs()[:6]
+
+
+@pytest.mark.parametrize("job", HOST_JOBS, ids=lambda j: f"f{j.func}e{j.e_in}p{j.p}d{j.d}L{j.limbs}")
+def test_plan_and_tables_match_oracle(job):
+    info = tmd.tmd_plan(job)
+    ob = plan.blocks(job)
+    assert info["n_blocks"] == len(ob)
+    assert info["n_subints"] == plan.n_subintervals(job)
+    assert info["cuts"] == [s[0] for s in plan.segments(job)[1:]]
+    rng = random.Random(job.start ^ job.count)
+    picks = sorted(set([0, len(ob) - 1] + [rng.randrange(len(ob)) for _ in range(4)]))
+    for b in picks:
+        c, tab, bi = tmd.tmd_block_tables(job, b)
+        oc, ot = oracle_table(job, ob[b])
+        assert (bi["start"], bi["length"], bi["first_sub"], bi["e_out"]) == \
+            (ob[b].start, ob[b].length, ob[b].first_sub, ob[b].e_out)
+        assert c == oc
+        assert tab == ot
+
+
+def test_toy_every_block_table():
+    job = wl.toy_job()
+    for b, blk in enumerate(plan.blocks(job)):
+        if b % 7:
+            continue
+        c, tab, _ = tmd.tmd_block_tables(job, b)
+        assert (c, tab) == oracle_table(job, blk)
+
+
+@pytest.mark.parametrize("field,value,status", [
+    ("m", 1, tmd._lib.TMD_EINVAL), ("m", 64, tmd._lib.TMD_EINVAL),
+    ("log2_N", 17, tmd._lib.TMD_EUNSUPPORTED), ("d", 5, tmd._lib.TMD_EUNSUPPORTED),
+    ("limbs", 4, tmd._lib.TMD_EUNSUPPORTED), ("count", 0, tmd._lib.TMD_EINVAL),
+    ("start", 1 << 52, tmd._lib.TMD_EINVAL), ("e_in", 3, tmd._lib.TMD_EUNSUPPORTED),
+    ("log2_T", 13, tmd._lib.TMD_EINVAL), ("func", 7, tmd._lib.TMD_EINVAL),
+    ("flags", 8, tmd._lib.TMD_EINVAL)])
+def test_validation(field, value, status):
+    job = wl.plain_job().replace(**{field: value})
+    if field == "log2_T":
+        job = job.replace(log2_N=14)
+    with pytest.raises(tmd.TmdError) as e:
+        tmd.tmd_plan(job)
+    assert e.value.status == status
+
+
+def test_log_binade_near_one_rejected():
+    job = wl.Job(wl.FUNC_LOG, 1, 53, 40, 14, 3, 24, 3, 0, 1 << 30)
+    with pytest.raises(tmd.TmdError):
+        tmd.tmd_plan(job)

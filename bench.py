@@ -1,0 +1,376 @@
+"""Benchmark: binary64 arguments checked per second on the plain exp workload.
+
+Workload (one step): exp over a contiguous 2^36-argument slice of the
+binary64 binade [1/2, 1) (seeded block-aligned start), degree-3 Taylor blocks
+of 2^24 arguments in 192-bit fixed point, sub-intervals of N = 2^14
+arguments, threshold m = 40: packet starts, tabulated-difference stepping,
+Algorithm 4 filter, exact resolution and compaction over all 2^22 lines.
+
+  value   device throughput of the fused step (tables resident in HBM when
+          the timed region starts), arguments / s, whole job over all ranks.
+  plain   the same work as two launches (generate lines to HBM, then search
+          them), for the batched-vs-plain comparison.
+  e2e     the public C-ABI call from host job descriptors to the sorted host
+          candidate list: host planning and correctly rounded tables, the
+          host->device upload of the tables, the kernel, the device->host
+          read of the count and records, every step.
+
+Between timed steps a 256 MiB buffer (> the 129 MB L2) is written so that no
+step starts with a warm L2.  `--impl reference` times the CPU oracle instead
+(exact enclosures, direct Horner, brute force over every argument) on a
+bounded sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import workloads as wl  # noqa: E402
+
+METRIC = "binary64 args checked/s (exp, binade slice) batched vs plain; % int-pipe peak"
+UNIT = "args/s"
+
+# Integer/FP32 issue ceiling: 152 SMs x 4 schedulers x 32 lanes per clock at
+# the 2070 MHz maximum SM clock (every instruction of the path is a 32-bit
+# integer, logic, conversion or FP32 operation; one warp instruction per
+# scheduler per clock).
+SMS, LANES_PER_SM, SM_MAX_HZ = 152, 128, 2.070e9
+ISSUE_PEAK_OPS = SMS * LANES_PER_SM * SM_MAX_HZ
+
+# Algorithmic 32-bit operations (definitions in the design doc):
+#   per line:       tabulated stepping (2d-1) W-bit adds = 2 (2d-1) L 32-bit
+#                   add-with-carry, plus 4 to form the search words;
+#   per half-step:  35 (divisor and dividend to FP32, reciprocal, two
+#                   quotient estimates, two 64x32 multiply-subtracts, two
+#                   corrections, the u/v update, the exit test).
+OPS_PER_HALF_STEP = 35
+
+
+def ops_per_line(job) -> int:
+    return 2 * (2 * job.d - 1) * job.limbs + 4
+
+
+def rank_info():
+    r = int(os.environ.get("RANK", "0"))
+    w = int(os.environ.get("WORLD_SIZE", "1"))
+    lr = int(os.environ.get("LOCAL_RANK", str(r)))
+    return r, w, lr
+
+
+def rank_job(job, rank: int):
+    """Weak scaling: rank r searches the r-th neighbouring 2^36 slice."""
+    span = (1 << (job.p - 1))
+    start = (job.start + rank * job.count) % (span - job.count)
+    start -= start % (1 << job.log2_T)
+    return job.replace(start=start)
+
+
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons while it runs."""
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+        self.thread = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "100", "-i", str(self.gpu)], stdout=subprocess.PIPE,
+                stderr=subprocess.DEVNULL, text=True)
+        except (OSError, ValueError):
+            self.proc = None
+            return
+        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread.start()
+        time.sleep(0.3)
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        if self.thread:
+            self.thread.join(timeout=2)
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def cuda_index(local_rank: int) -> int:
+    vis = os.environ.get("CUDA_VISIBLE_DEVICES")
+    if vis:
+        ids = [v.strip() for v in vis.split(",") if v.strip()]
+        if local_rank < len(ids) and ids[local_rank].isdigit():
+            return int(ids[local_rank])
+    return local_rank
+
+
+# ------------------------------------------------------------ oracle timing
+def oracle_sample(job, seconds_target: float = 12.0, threads: int = 0):
+    """Time the CPU oracle on consecutive blocks of the job until about
+    `seconds_target` seconds of work; returns (args, seconds, blocks, threads)."""
+    from oracle import candidates as oc
+    from oracle import plan
+    oc.build_brute() if not os.path.exists(os.path.join(ROOT, "oracle", "_brute.so")) else None
+    lib = oc._brute_lib()
+    nthreads = threads or (os.cpu_count() or 1)
+    blocks = plan.blocks(job)
+    t0 = time.perf_counter()
+    done_args, nb = 0, 0
+    for blk in blocks:
+        oc.job_candidates(job, blocks=[blk], threads=nthreads)
+        done_args += blk.length
+        nb += 1
+        if time.perf_counter() - t0 >= seconds_target:
+            break
+    dt = time.perf_counter() - t0
+    used = lib.oracle_threads_available() if lib is not None else 1
+    return done_args, dt, nb, min(used, nthreads)
+
+
+def run_reference(args):
+    r, w, _ = rank_info()
+    if w > 1:
+        import torch.distributed as dist
+        if not dist.is_initialized():
+            dist.init_process_group("gloo")
+        if r != 0:
+            dist.barrier()
+            return
+    job = wl.plain_job()
+    per_step = []
+    sample = None
+    # the whole reference run stays within a few minutes: each step is a
+    # bounded sample (at least one Taylor block) of the workload
+    target = min(args.ref_seconds, 150.0 / (args.warmup + args.steps))
+    for k in range(args.warmup + args.steps):
+        a, dt, nb, th = oracle_sample(job, seconds_target=target)
+        if k >= args.warmup:
+            per_step.append((a, dt))
+            sample = (nb, th)
+    args_total = sum(a for a, _ in per_step)
+    t_total = sum(d for _, d in per_step)
+    value = args_total / t_total
+    nb, th = sample
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": w,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * t_total / len(per_step),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int64",
+        "data": "synthetic",
+        "config": {"workload": "exp binary64 [1/2,1) 2^36-arg slice, d=3, W=192, N=2^14, m=40",
+                   "sample": f"{nb} Taylor blocks of 2^24 args per step"},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": th, "kind": "oracle",
+                         "sample": f"first {nb} blocks (2^24 args each) of the 2^36 slice per step"},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    if w > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+# ------------------------------------------------------------- native arm
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=400)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="native", choices=["native", "reference"])
+    ap.add_argument("--e2e-steps", type=int, default=5)
+    ap.add_argument("--ref-seconds", type=float, default=12.0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--m", type=int, default=40)
+    ap.add_argument("--count-log2", type=int, default=36,
+                    help="slice size (smaller only for profiling captures)")
+    args = ap.parse_args()
+    args.warmup = max(args.warmup, 3)
+    if args.impl == "reference":
+        run_reference(args)
+        return
+
+    import torch
+    import paper_1211_3056_gb300 as tmd
+
+    rank, world, local_rank = rank_info()
+    torch.cuda.set_device(local_rank)
+    dev = f"cuda:{local_rank}"
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+
+    job = rank_job(wl.plain_job(m=args.m, count_log2=args.count_log2), rank)
+    stream = torch.cuda.current_stream()
+    ctx = tmd.Context(local_rank)
+    cap = 1 << 16
+    d_cand, d_count = tmd.alloc_candidates(cap, local_rank)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+
+    # resident plan and tables (host work happens here, outside the timed region)
+    tmd.tmd_search(ctx, [job], None, d_cand, d_count)
+    torch.cuda.synchronize()
+    need = tmd.tmd_generate(ctx, [job], None)
+    d_lin = torch.empty(need // 8, dtype=torch.int64, device=dev)
+
+    def fused_step():
+        tmd.tmd_search(ctx, [job], None, d_cand, d_count)
+
+    # batched form: the persistent work-queue kernel, captured once as a graph
+    d_cand_b, d_count_b = tmd.alloc_candidates(cap, local_rank)
+    batch = tmd.Batch(ctx, [job], d_cand_b, d_count_b)
+
+    def batched_step():
+        batch.launch()
+
+    def plain_step():
+        tmd.tmd_generate(ctx, [job], d_lin)
+        tmd.tmd_search(ctx, [job], d_lin, d_cand, d_count)
+
+    def timed(fn, steps, warmup):
+        for _ in range(warmup):
+            flush.fill_(1)
+            fn()
+        torch.cuda.synchronize()
+        evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+               for _ in range(steps)]
+        barrier()
+        torch.cuda.synchronize()
+        for e0, e1 in evs:
+            flush.fill_(1)
+            e0.record(stream)
+            fn()
+            e1.record(stream)
+        torch.cuda.synchronize()
+        barrier()
+        return [e0.elapsed_time(e1) for e0, e1 in evs]
+
+    sampler = ClockSampler(cuda_index(local_rank))
+    sampler.start()
+    batched_ms = timed(batched_step, args.steps, args.warmup)
+    fused_ms = timed(fused_step, args.steps, args.warmup)
+    clocks = sampler.stop()
+    stats = batch.stats()
+    recs_b, count_b = tmd.tmd_candidates(ctx, d_cand_b, d_count_b)
+    recs, count = tmd.tmd_candidates(ctx, d_cand, d_count)
+    assert (recs_b, count_b) == (recs, count), "batched and plain forms disagree"
+    plain_ms = timed(plain_step, max(args.steps // 4, 3), args.warmup)
+
+    def max_over_ranks(x: float) -> float:
+        if dist is None:
+            return x
+        t = torch.tensor([x], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        return float(t.item())
+
+    ms = max_over_ranks(statistics.mean(batched_ms))
+    ms_fused = max_over_ranks(statistics.mean(fused_ms))
+    ms_plain = max_over_ranks(statistics.mean(plain_ms))
+    total_args = job.count * world
+    value = total_args / (ms / 1e3)
+    fused_value = total_args / (ms_fused / 1e3)
+    plain_value = total_args / (ms_plain / 1e3)
+
+    # end to end through the C ABI: host descriptors in, host records out
+    e2e_times = []
+    h2d = 0
+    for k in range(args.e2e_steps + 1):
+        tmd.tmd_evict(ctx)
+        torch.cuda.synchronize()
+        barrier()
+        t0 = time.perf_counter()
+        tmd.tmd_search(ctx, [job], None, d_cand, d_count)
+        got, n = tmd.tmd_candidates(ctx, d_cand, d_count)
+        t1 = time.perf_counter()
+        if k > 0:
+            e2e_times.append(t1 - t0)
+    e2e_s = max_over_ranks(statistics.mean(e2e_times))
+    h2d = tmd.tmd_stats_read(ctx)["upload_bytes"]
+    d2h = 8 + 4 + n * tmd.CANDIDATE_BYTES
+
+    # roofline of the persistent kernel (the step is that one launch plus two
+    # 8-byte memsets in the same graph)
+    alg_ops = stats["lines"] * ops_per_line(job) + stats["half_steps"] * OPS_PER_HALF_STEP
+    achieved = alg_ops / (statistics.mean(batched_ms) / 1e3)
+    roofline = {"bound": "alu", "achieved": achieved / 1e12, "peak": ISSUE_PEAK_OPS / 1e12,
+                "unit": "Tops/s", "frac": achieved / ISSUE_PEAK_OPS,
+                "traffic": None,
+                "peak_note": "derived: 152 SMs x 128 lanes x 2.07 GHz (issue ceiling, of derived)",
+                "half_steps_per_line": stats["half_steps"] / max(1, stats["lines"]),
+                "filter_fail_per_line": stats["filter_fail"] / max(1, stats["lines"])}
+
+    cpu = None
+    if rank == 0 and not args.no_cpu_baseline:
+        a, dt, nb, th = oracle_sample(job, seconds_target=args.ref_seconds)
+        cpu = {"value": a / dt, "unit": UNIT, "cores": th, "kind": "oracle",
+               "sample": f"first {nb} Taylor blocks (2^24 args each) of the slice, {dt:.1f} s"}
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "int64", "data": "synthetic",
+            "config": {"workload": f"exp binary64 [1/2,1) 2^{args.count_log2}-arg slice per GPU, "
+                                   f"d=3, W=192, N=2^14, m={args.m}",
+                       "l2": "256 MiB flush before every step",
+                       "form": "batched: persistent work-queue kernel replayed as a CUDA graph",
+                       "candidates": count},
+            "plain": {"value": fused_value, "ms_per_step": ms_fused,
+                      "form": "per-job fused launch (tmd_search)"},
+            "unfused": {"value": plain_value, "ms_per_step": ms_plain,
+                        "form": "generate lines to HBM, then search them (two launches)"},
+            "e2e": {"value": total_args / e2e_s, "unit": UNIT, "h2d_bytes_per_step": h2d,
+                    "d2h_bytes_per_step": d2h, "ms_per_step": e2e_s * 1e3},
+            "gpu_launches": args.steps * 1,
+            "roofline": roofline, "cpu_baseline": cpu, "clocks": clocks,
+        }
+        print(json.dumps(line), flush=True)
+    batch.close()
+    ctx.close()
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -117,6 +117,8 @@ typedef struct {
     uint64_t filter_fail;    /* lines whose lower bound fell below the threshold */
     uint64_t candidates;     /* records produced (same as *d_count)             */
     uint64_t half_steps;     /* continued-fraction half-steps, all lanes       */
+    uint64_t upload_bytes;   /* bytes of the last plan upload (host -> device)  */
+    uint64_t count;          /* the last search's *d_count                      */
 } tmd_stats;
 
 typedef struct tmd_ctx tmd_ctx;
@@ -220,8 +222,34 @@ tmd_status tmd_lower_bounds(tmd_ctx* ctx, const uint64_t* d_B, const uint64_t* d
                             uint32_t* d_hs, void* stream);
 
 /* Counters of the most recent tmd_search / tmd_search_lines / batch run on
- * this context.  Synchronises `stream`. */
+ * this context, the size of the last plan upload and the last count.
+ * Synchronises `stream`. */
 tmd_status tmd_stats_read(tmd_ctx* ctx, tmd_stats* out, void* stream);
+
+/* ---- batched form: one persistent launch over many jobs, as a CUDA graph ---- */
+
+typedef struct tmd_batch tmd_batch;
+
+/* Plan and tabulate every job of the batch (host), upload the plan into
+ * device memory owned by the batch, and capture one CUDA graph that resets
+ * the counters and runs the persistent kernel: a grid of resident CTAs whose
+ * warps take tasks (32 packets of one job) from a device counter until none
+ * remain -- uneven jobs balance themselves.  Records go to d_cand/d_count as
+ * in tmd_search (job = index in this batch).  The batch keeps pointers to
+ * d_cand and d_count: they must outlive it.  *upload_bytes (may be NULL)
+ * receives the plan size.  Synchronises `stream` once (the upload). */
+tmd_status tmd_batch_create(tmd_ctx* ctx, const tmd_job* jobs, uint32_t njobs,
+                            tmd_candidate* d_cand, uint64_t cand_cap, uint64_t* d_count,
+                            void* stream, tmd_batch** batch, uint64_t* upload_bytes);
+
+/* Replay the batch's graph on `stream` (asynchronous). */
+tmd_status tmd_batch_launch(tmd_batch* batch, void* stream);
+
+/* Counters of the batch's last replay (see tmd_stats).  Synchronises. */
+tmd_status tmd_batch_stats(tmd_batch* batch, tmd_stats* out, void* stream);
+
+/* Free the batch's device memory and graph (after its replays finished). */
+tmd_status tmd_batch_destroy(tmd_batch* batch);
 
 #ifdef __cplusplus
 }

@@ -156,7 +156,60 @@ def tmd_stats_read(ctx: Context, stream=None) -> dict:
     s = _lib.tmd_stats()
     check(lib().tmd_stats_read(ctx.handle, ctypes.byref(s), _stream_ptr(stream)), "tmd_stats_read")
     return {"lines": s.lines, "filter_fail": s.filter_fail, "candidates": s.candidates,
-            "half_steps": s.half_steps}
+            "half_steps": s.half_steps, "upload_bytes": s.upload_bytes, "count": s.count}
+
+
+class Batch:
+    """A tmd_batch: resident plan of many jobs plus its captured graph."""
+
+    def __init__(self, ctx: Context, jobs: Sequence, d_cand, d_count, stream=None):
+        self.ctx = ctx
+        self.jobs = list(jobs)
+        self.d_cand, self.d_count = d_cand, d_count   # kept alive with the batch
+        cap = 0 if d_cand is None else (d_cand.numel() * d_cand.element_size()) // CANDIDATE_BYTES
+        h = ctypes.c_void_p()
+        up = ctypes.c_uint64(0)
+        check(lib().tmd_batch_create(ctx.handle, job_array(self.jobs), len(self.jobs), _ptr(d_cand),
+                                     cap, _ptr(d_count), _stream_ptr(stream), ctypes.byref(h),
+                                     ctypes.byref(up)), "tmd_batch_create")
+        self.handle = h
+        self.upload_bytes = up.value
+
+    def launch(self, stream=None):
+        check(lib().tmd_batch_launch(self.handle, _stream_ptr(stream)), "tmd_batch_launch")
+
+    def stats(self, stream=None) -> dict:
+        s = _lib.tmd_stats()
+        check(lib().tmd_batch_stats(self.handle, ctypes.byref(s), _stream_ptr(stream)), "tmd_batch_stats")
+        return {"lines": s.lines, "filter_fail": s.filter_fail, "candidates": s.candidates,
+                "half_steps": s.half_steps, "upload_bytes": s.upload_bytes, "count": s.count}
+
+    def close(self):
+        if getattr(self, "handle", None):
+            lib().tmd_batch_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def tmd_batch_create(ctx: Context, jobs: Sequence, d_cand, d_count, stream=None) -> Batch:
+    return Batch(ctx, jobs, d_cand, d_count, stream)
+
+
+def tmd_batch_launch(batch: Batch, stream=None) -> None:
+    batch.launch(stream)
+
+
+def tmd_batch_stats(batch: Batch, stream=None) -> dict:
+    return batch.stats(stream)
+
+
+def tmd_batch_destroy(batch: Batch) -> None:
+    batch.close()
 
 
 # ------------------------------------------------------------- conveniences

@@ -46,7 +46,8 @@ class tmd_block_info(ctypes.Structure):
 
 class tmd_stats(ctypes.Structure):
     _fields_ = [("lines", ctypes.c_uint64), ("filter_fail", ctypes.c_uint64),
-                ("candidates", ctypes.c_uint64), ("half_steps", ctypes.c_uint64)]
+                ("candidates", ctypes.c_uint64), ("half_steps", ctypes.c_uint64),
+                ("upload_bytes", ctypes.c_uint64), ("count", ctypes.c_uint64)]
 
 
 _vp = ctypes.c_void_p
@@ -72,6 +73,11 @@ SIGNATURES = {
     "tmd_search_lines": (ctypes.c_int, [_vp, _vp, _vp, _vp, _u64, _i32, _u32, _vp, _u64, _vp, _vp]),
     "tmd_lower_bounds": (ctypes.c_int, [_vp, _vp, _vp, _vp, _u64, _vp, _vp, _vp]),
     "tmd_stats_read": (ctypes.c_int, [_vp, ctypes.POINTER(tmd_stats), _vp]),
+    "tmd_batch_create": (ctypes.c_int, [_vp, ctypes.POINTER(tmd_job), _u32, _vp, _u64, _vp, _vp,
+                                        ctypes.POINTER(_vp), ctypes.POINTER(_u64)]),
+    "tmd_batch_launch": (ctypes.c_int, [_vp, _vp]),
+    "tmd_batch_stats": (ctypes.c_int, [_vp, ctypes.POINTER(tmd_stats), _vp]),
+    "tmd_batch_destroy": (ctypes.c_int, [_vp]),
 }
 
 _LIB = None

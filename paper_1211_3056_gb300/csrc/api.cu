@@ -65,6 +65,8 @@ struct tmd_ctx {
     bool stage_pending = false;
     Plan plan;
     bool resident = false;
+    uint64_t upload_bytes = 0;
+    const uint64_t* last_count = nullptr;
 };
 
 namespace {
@@ -88,8 +90,9 @@ unsigned host_threads() {
 
 uint32_t choose_nu(const tmd_job& job, uint64_t n_sub_block) {
     const char* env = getenv("TMD_NU");
-    uint32_t nu = 8;
+    uint32_t nu = 8;  // at most the kernels' shared-memory stage (8 lines per lane)
     if (env && atoi(env) > 0) nu = (uint32_t)atoi(env);
+    if (nu > 8) nu = 8;
     if (nu > n_sub_block) nu = (uint32_t)n_sub_block;
     if (nu < 1) nu = 1;
     (void)job;
@@ -231,6 +234,7 @@ tmd_status upload_plan(tmd_ctx* c, cudaStream_t s) {
     memcpy(c->h_stage + o_tasks, P.tasks.data(), P.tasks.size() * sizeof(DevTask));
     CK(cudaMemcpyAsync(c->d_arena, c->h_stage, total, cudaMemcpyHostToDevice, s));
     CK(cudaEventRecord(c->stage_done, s));
+    c->upload_bytes = total;
     c->stage_pending = true;
     c->off_jobs = o_jobs;
     c->off_blocks = o_blocks;
@@ -398,6 +402,7 @@ tmd_status tmd_search(tmd_ctx* c, const tmd_job* jobs, uint32_t njobs, const voi
     if (st != TMD_OK) return st;
     st = reset_counters(c, d_count, s);
     if (st != TMD_OK) return st;
+    c->last_count = d_count;
     if (d_lin) {
         LineArgs a;
         memset(&a, 0, sizeof a);
@@ -465,6 +470,7 @@ tmd_status tmd_search_lines(tmd_ctx* c, const uint64_t* d_B, const uint64_t* d_A
     CK(cudaSetDevice(c->device));
     tmd_status st = reset_counters(c, d_count, s);
     if (st != TMD_OK) return st;
+    c->last_count = d_count;
     LineArgs a;
     memset(&a, 0, sizeof a);
     a.B = d_B;
@@ -497,13 +503,151 @@ tmd_status tmd_stats_read(tmd_ctx* c, tmd_stats* out, void* stream) {
     cudaStream_t s = (cudaStream_t)stream;
     CK(cudaSetDevice(c->device));
     uint64_t h[ST_COUNT];
+    uint64_t cnt = 0;
     CK(cudaMemcpyAsync(h, stats_ptr(c), sizeof h, cudaMemcpyDeviceToHost, s));
+    if (c->last_count) CK(cudaMemcpyAsync(&cnt, c->last_count, sizeof cnt, cudaMemcpyDeviceToHost, s));
     CK(cudaStreamSynchronize(s));
     out->lines = h[ST_LINES];
     out->filter_fail = h[ST_FAIL];
-    out->candidates = h[ST_CAND];
+    out->candidates = cnt;
     out->half_steps = h[ST_HALF];
+    out->upload_bytes = c->upload_bytes;
+    out->count = cnt;
+    return TMD_OK;
+}
+
+// ---------------------------------------------------------------- batches
+}  // extern "C"
+
+struct tmd_batch {
+    tmd_ctx* ctx = nullptr;
+    Plan plan;
+    char* d_arena = nullptr;
+    uint64_t* d_misc = nullptr;
+    size_t off_jobs = 0, off_blocks = 0, off_tables = 0, off_tasks = 0;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    cudaStream_t cap_stream = nullptr;
+    uint64_t upload_bytes = 0;
+    const uint64_t* d_count = nullptr;
+};
+
+namespace {
+
+void batch_free(tmd_batch* b) {
+    if (!b) return;
+    if (b->exec) cudaGraphExecDestroy(b->exec);
+    if (b->graph) cudaGraphDestroy(b->graph);
+    if (b->cap_stream) cudaStreamDestroy(b->cap_stream);
+    if (b->d_arena) cudaFree(b->d_arena);
+    if (b->d_misc) cudaFree(b->d_misc);
+    delete b;
+}
+
+}  // namespace
+
+extern "C" {
+
+tmd_status tmd_batch_create(tmd_ctx* c, const tmd_job* jobs, uint32_t njobs, tmd_candidate* d_cand,
+                            uint64_t cand_cap, uint64_t* d_count, void* stream, tmd_batch** out,
+                            uint64_t* upload_bytes) {
+    if (!c || !jobs || njobs == 0 || !d_count || !out || (cand_cap && !d_cand)) return TMD_EINVAL;
+    *out = nullptr;
+    CK(cudaSetDevice(c->device));
+    cudaStream_t s = (cudaStream_t)stream;
+    tmd_batch* b = new tmd_batch();
+    b->ctx = c;
+    b->d_count = d_count;
+    tmd_status st = build_plan(jobs, njobs, b->plan);
+    if (st != TMD_OK) {
+        batch_free(b);
+        return st;
+    }
+    Plan& P = b->plan;
+    size_t o_blocks = align256(P.jobs.size() * sizeof(DevJob));
+    size_t o_tables = align256(o_blocks + P.blocks.size() * sizeof(DevBlock));
+    size_t o_tasks = align256(o_tables + P.tables.size() * sizeof(uint64_t));
+    size_t total = align256(o_tasks + P.tasks.size() * sizeof(DevTask));
+    std::vector<char> host(total, 0);
+    memcpy(host.data(), P.jobs.data(), P.jobs.size() * sizeof(DevJob));
+    memcpy(host.data() + o_blocks, P.blocks.data(), P.blocks.size() * sizeof(DevBlock));
+    memcpy(host.data() + o_tables, P.tables.data(), P.tables.size() * sizeof(uint64_t));
+    memcpy(host.data() + o_tasks, P.tasks.data(), P.tasks.size() * sizeof(DevTask));
+    if (cudaMalloc((void**)&b->d_arena, total) != cudaSuccess ||
+        cudaMalloc((void**)&b->d_misc, 64) != cudaSuccess ||
+        cudaMemcpyAsync(b->d_arena, host.data(), total, cudaMemcpyHostToDevice, s) != cudaSuccess ||
+        cudaStreamSynchronize(s) != cudaSuccess) {
+        batch_free(b);
+        return TMD_ECUDA;
+    }
+    b->upload_bytes = total;
+    if (upload_bytes) *upload_bytes = total;
+    b->off_blocks = o_blocks;
+    b->off_tables = o_tables;
+    b->off_tasks = o_tasks;
+    // persistent grid: every SM filled to its occupancy, no more CTAs than tasks need
+    int per_sm = 0;
+    if (persistent_occupancy(&per_sm) != cudaSuccess || per_sm < 1) per_sm = 1;
+    uint64_t want = (P.tasks.size() + 7) / 8;
+    int ctas = (int)std::min<uint64_t>((uint64_t)c->sms * (uint64_t)per_sm, std::max<uint64_t>(want, 1));
+    LaunchArgs a;
+    memset(&a, 0, sizeof a);
+    a.jobs = (const DevJob*)b->d_arena;
+    a.blocks = (const DevBlock*)(b->d_arena + o_blocks);
+    a.tables = (const uint64_t*)(b->d_arena + o_tables);
+    a.tasks = (const DevTask*)(b->d_arena + o_tasks);
+    a.n_tasks = P.tasks.size();
+    a.cand = d_cand;
+    a.cap = cand_cap;
+    a.count = d_count;
+    a.stats = b->d_misc;
+    a.queue_head = (uint32_t*)(b->d_misc + ST_COUNT) + 1;
+    if (cudaStreamCreateWithFlags(&b->cap_stream, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaStreamBeginCapture(b->cap_stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+        batch_free(b);
+        return TMD_ECUDA;
+    }
+    cudaMemsetAsync(b->d_misc, 0, sizeof(uint64_t) * (ST_COUNT + 1), b->cap_stream);
+    cudaMemsetAsync(d_count, 0, sizeof(uint64_t), b->cap_stream);
+    launch_persistent(a, ctas, b->cap_stream);
+    if (cudaStreamEndCapture(b->cap_stream, &b->graph) != cudaSuccess ||
+        cudaGraphInstantiate(&b->exec, b->graph, 0) != cudaSuccess) {
+        batch_free(b);
+        return TMD_ECUDA;
+    }
+    *out = b;
+    return TMD_OK;
+}
+
+tmd_status tmd_batch_launch(tmd_batch* b, void* stream) {
+    if (!b) return TMD_EINVAL;
+    CK(cudaGraphLaunch(b->exec, (cudaStream_t)stream));
+    return TMD_OK;
+}
+
+tmd_status tmd_batch_stats(tmd_batch* b, tmd_stats* out, void* stream) {
+    if (!b || !out) return TMD_EINVAL;
+    cudaStream_t s = (cudaStream_t)stream;
+    uint64_t h[ST_COUNT];
+    uint64_t cnt = 0;
+    CK(cudaMemcpyAsync(h, b->d_misc, sizeof h, cudaMemcpyDeviceToHost, s));
+    CK(cudaMemcpyAsync(&cnt, b->d_count, sizeof cnt, cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    out->lines = h[ST_LINES];
+    out->filter_fail = h[ST_FAIL];
+    out->candidates = cnt;
+    out->half_steps = h[ST_HALF];
+    out->upload_bytes = b->upload_bytes;
+    out->count = cnt;
+    return TMD_OK;
+}
+
+tmd_status tmd_batch_destroy(tmd_batch* b) {
+    if (!b) return TMD_EINVAL;
+    cudaSetDevice(b->ctx->device);
+    batch_free(b);
     return TMD_OK;
 }
 
 }  // extern "C"
+

@@ -56,7 +56,7 @@ Enc exp_fixed(const Big& y, unsigned Q, unsigned P) {
 
 // ln 2 = sum_k 2 / ((2k+1) 3^(2k+1)):  w_0 = floor(2^(P+1)/3),
 // w_k = floor(w_{k-1}/9) (error <= 2), term_k = floor(w_k/(2k+1)) (error <= 2).
-Enc ln2_fixed(unsigned P) {
+Enc ln2_series(unsigned P) {
     Big w = Big::pow2(P + 1);
     w.div_u64(3);
     Big S = w;
@@ -77,6 +77,17 @@ Enc ln2_fixed(unsigned P) {
     r.hi = S;
     r.hi.add(Big(E));
     r.P = P;
+    return r;
+}
+
+// ln 2 enclosures are reused across blocks: one cache per host thread.
+Enc ln2_fixed(unsigned P) {
+    thread_local std::vector<std::pair<unsigned, Enc>> cache;
+    for (const auto& e : cache)
+        if (e.first == P) return e.second;
+    Enc r = ln2_series(P);
+    if (cache.size() > 32) cache.clear();
+    cache.emplace_back(P, r);
     return r;
 }
 
@@ -154,16 +165,35 @@ uint64_t factorial(int k) {
 }
 
 // Enclosure of f^(k)(X)/k! (k = 0: f itself) for the positive cases:
-// exp (any k), 2^x (any k), log (k = 0).  X = M 2^(e_in - p).
-Enc coeff_enclosure(int func, uint64_t M, int p, int e_in, int k, unsigned P) {
+// exp (any k), 2^x (any k), log (k = 0).  X = M 2^(e_in - p).  `base`, when
+// given, is an enclosure of f(X) (exp, 2^x) at precision base->P >= the
+// precision this order needs; it is reused instead of summing the series
+// again.
+Enc coeff_enclosure(int func, uint64_t M, int p, int e_in, int k, unsigned P,
+                    const Enc* base = nullptr) {
     unsigned q = (unsigned)(p - e_in);
     uint64_t kf = factorial(k);
     Enc r;
     if (func == TMD_EXP) {
-        r = exp_fixed(Big(M), q, P);
+        if (base && base->P >= P) {
+            r.lo = base->lo;
+            r.lo.shr(base->P - P);
+            r.hi = shr_ceil(base->hi, base->P - P);
+            r.P = P;
+        } else {
+            r = exp_fixed(Big(M), q, P);
+        }
     } else if (func == TMD_EXP2) {
         unsigned P2 = P + 8 + 2 * (unsigned)k;
-        Enc e = exp2_fixed(M, q, P2);
+        Enc e;
+        if (base && base->P >= P2) {
+            e.lo = base->lo;
+            e.lo.shr(base->P - P2);
+            e.hi = shr_ceil(base->hi, base->P - P2);
+            e.P = P2;
+        } else {
+            e = exp2_fixed(M, q, P2);
+        }
         if (k > 0) {
             Enc L = ln2_fixed(P2);
             Big lo = e.lo, hi = e.hi;
@@ -200,8 +230,9 @@ Big rn_shift(const Big& x, unsigned s) {
 }
 
 // Signed result of RN(2^E f^(k)(X)/k!) reduced mod 2^W into `limbs` words.
+// `base` (optional) is a shared enclosure of f(X) for exp and 2^x.
 bool scaled_coeff(int func, uint64_t M, int p, int e_in, int k, int E, unsigned limbs,
-                  uint64_t* out) {
+                  uint64_t* out, const Enc* base = nullptr) {
     Big mag;
     bool neg = false;
     if (func == TMD_LOG && k >= 1) {
@@ -223,9 +254,9 @@ bool scaled_coeff(int func, uint64_t M, int p, int e_in, int k, int E, unsigned 
     } else {
         bool done = false;
         for (int step = 0; step < 16 && !done; step++) {
-            int base = E > 0 ? E : 0;
-            unsigned P = (unsigned)(base + 64 + 64 * step);
-            Enc c = coeff_enclosure(func, M, p, e_in, k, P);
+            int e_pos = E > 0 ? E : 0;
+            unsigned P = (unsigned)(e_pos + 64 + 64 * step);
+            Enc c = coeff_enclosure(func, M, p, e_in, k, P, step == 0 ? base : nullptr);
             int s = (int)P - E;
             if (s < 1) continue;
             Big rl = rn_shift(c.lo, (unsigned)s);
@@ -453,10 +484,21 @@ tmd_status block_table(const tmd_job& job, const BlockPlan& blk, uint64_t* coeff
     uint64_t M = arg_mantissa(job, blk.start);
     int sl = scale_log2(job, blk.e_out);
     Word c[MAX_DEG + 1];
+    // one enclosure of f(X_t) serves every order (exp, 2^x): the order-0
+    // scale is the largest, so its precision covers the others
+    Enc base;
+    const Enc* basep = nullptr;
+    if (job.func != TMD_LOG) {
+        int E0 = W + sl;
+        unsigned P0 = (unsigned)((E0 > 0 ? E0 : 0) + 64) + 8 + 2 * (unsigned)d;
+        base = job.func == TMD_EXP ? exp_fixed(Big(M), (unsigned)(job.p - job.e_in), P0)
+                                   : exp2_fixed(M, (unsigned)(job.p - job.e_in), P0);
+        basep = &base;
+    }
     for (int k = 0; k <= d; k++) {
         c[k] = w_zero();
         int E = W + sl + k * (job.e_in - job.p);
-        if (!scaled_coeff(job.func, M, job.p, job.e_in, k, E, L, c[k].l)) return TMD_EUNSUPPORTED;
+        if (!scaled_coeff(job.func, M, job.p, job.e_in, k, E, L, c[k].l, basep)) return TMD_EUNSUPPORTED;
         if (coeffs)
             for (unsigned l = 0; l < L; l++) coeffs[k * L + l] = c[k].l[l];
     }

@@ -87,23 +87,36 @@ __device__ __forceinline__ float rcp_approx(float x) {
     return r;
 }
 
-// floor(a/b) and a mod b for b > 0 given rb ~ 1/b; false if the quotient
-// estimate is too large for the fast path.
-__device__ __forceinline__ bool divmod_fast(uint64_t a, uint64_t b, float rb, uint64_t& k,
-                                            uint64_t& r) {
-    float kf = u64_to_f32_rz(a) * rb;
-    bool ok = kf < 524288.0f;  // 2^19
-    float y = fmaxf(fminf(kf, 524288.0f) - 0.5f, 0.0f);
-    uint32_t k0 = __float_as_uint(__fadd_rz(y, 8388608.0f)) - 0x4B000000u;
-    uint64_t rr = a - (uint64_t)k0 * b;
-    bool up = rr >= b;
-    r = up ? rr - b : rr;
-    k = (uint64_t)k0 + (up ? 1u : 0u);
-    return ok;
+// Quotient estimate.  af = fl(a) and bf = fl(b) come from u64_to_f32_rz
+// (a (1 - 2^-22) <= af <= a), rbs = fl(rcp(bf) (1 - 2^-20)) carries a
+// deliberate downward bias, kf = fl(af rbs).  With 1 ulp for rcp.approx and
+// half an ulp for each product,
+//     (a/b)(1 - 1.5 2^-20) <= kf <= (a/b)(1 - 2^-21) < a/b,
+// so for kf < 2^19: floor(a/b) - 1 <= floor(kf) <= floor(a/b).  floor(kf) is
+// read off the bits of 2^23 + kf rounded toward zero.  *ok is false when the
+// estimate is outside the fast range (the caller then divides exactly).
+__device__ __forceinline__ uint32_t quot_estimate(float af, float rbs, bool& ok) {
+    const float kf = af * rbs;
+    ok = kf < 524288.0f;  // 2^19
+    return __float_as_uint(__fadd_rz(kf, 8388608.0f)) - 0x4B000000u;
 }
 
-// exact floor(a/b), a mod b (b > 0) by shift-subtract
-__device__ __noinline__ void divmod_slow(uint64_t a, uint64_t b, uint64_t& k, uint64_t& r) {
+__device__ __forceinline__ float scaled_rcp(float bf) {
+    return rcp_approx(bf) * 0.99999904632568359375f;  // 1 - 2^-20
+}
+
+// r = a - k b for an estimate k in {floor(a/b) - 1, floor(a/b)}, then one
+// compare-and-subtract; k is raised when the subtract happens.
+__device__ __forceinline__ uint64_t rem_fix(uint64_t a, uint64_t b, uint32_t& k) {
+    const uint64_t r = a - (uint64_t)k * b;
+    const bool up = r >= b;
+    k += up ? 1u : 0u;
+    return up ? r - b : r;
+}
+
+// exact floor(a/b), a mod b (b > 0) by shift-subtract; the quotient is
+// returned clamped to 2^20 (it only feeds the saturating u/v update)
+__device__ __noinline__ uint64_t divmod_slow(uint64_t a, uint64_t b, uint32_t& k) {
     uint64_t quo = 0, rem = 0;
     int top = a ? 63 - __clzll((long long)a) : -1;
     for (int i = top; i >= 0; i--) {
@@ -114,77 +127,95 @@ __device__ __noinline__ void divmod_slow(uint64_t a, uint64_t b, uint64_t& k, ui
             quo |= 1ull << i;
         }
     }
-    k = quo;
-    r = rem;
+    k = quo < (1ull << 20) ? (uint32_t)quo : (1u << 20);
+    return rem;
 }
 
-__device__ __forceinline__ uint32_t sat_madd(uint32_t u, uint64_t k, uint32_t v, uint32_t n) {
-    uint32_t kc = (uint32_t)(k < (uint64_t)n ? k : (uint64_t)n);
-    uint32_t s = u + kc * v;  // u, v < n <= 2^16, kc <= 2^16: no wrap
-    return s < n ? s : n;
+__device__ __forceinline__ uint32_t sat_madd(uint32_t u, uint32_t k, uint32_t v, uint32_t n) {
+    const uint32_t kc = min(k, n);
+    const uint32_t s = u + kc * v;  // u, v < n <= 2^16, kc <= 2^16: no wrap
+    return min(s, n);
 }
 
 // Algorithm 4 lower bound of min_{0<=x<n} (B - A x) mod 2^64 on integers
 // scaled by 2^64: p <- A, q <- 2^64, d <- B, u <- 1, v <- 0; returns d when
 // u + v >= n.  Endings of a rational expansion: p = 0 -> d mod q (already
-// reduced), q = 0 -> d.  *hs counts half-steps.
+// reduced), q = 0 -> d.  *hs counts half-steps.  Each half-step converts its
+// new divisor and d to FP32; the dividend's conversion is the divisor's of
+// the half-step before.
 __device__ __forceinline__ uint64_t cf_lower_bound(uint64_t B, uint64_t A, uint32_t n, uint32_t* hs) {
     if (A == 0) {
         *hs = 0;
         return B;
     }
-    uint64_t p = A, q, d = B, k, r, kd, rd;
+    uint64_t p = A, q, d = B;
     uint32_t u = 1, v = 0, h = 1;
-    // first half-step with q = 2^64: floor(2^64/p) = floor((2^64 - p)/p) + 1
+    float pf = u64_to_f32_rz(p), qf;
+    // first half-step with q = 2^64: floor(2^64/p) = floor((2^64 - p)/p) + 1,
+    // and u = 1 + k * 0 stays 1
     {
-        float rp = rcp_approx(u64_to_f32_rz(p));
-        bool ok = divmod_fast(0ull - p, p, rp, k, r);
-        ok &= divmod_fast(d, p, rp, kd, rd);
-        if (!ok) {
-            divmod_slow(0ull - p, p, k, r);
-            divmod_slow(d, p, kd, rd);
+        const float rps = scaled_rcp(pf);
+        bool ok1, ok2;
+        uint32_t k = quot_estimate(u64_to_f32_rz(0ull - p), rps, ok1);
+        uint32_t kd = quot_estimate(u64_to_f32_rz(d), rps, ok2);
+        uint64_t qn = rem_fix(0ull - p, p, k);
+        uint64_t dn = rem_fix(d, p, kd);
+        if (!(ok1 && ok2)) {
+            qn = divmod_slow(0ull - p, p, k);
+            dn = divmod_slow(d, p, kd);
         }
-        q = r;
-        d = rd;
-        // u = 1 + (k + 1) * 0
+        q = qn;
+        d = dn;
     }
     if (1u >= n || q == 0) {
         *hs = h;
         return d;
     }
+    qf = u64_to_f32_rz(q);
 #pragma unroll 1
     for (int guard = 0; guard < 64; guard++) {
         // second half: k = floor(p/q); p -= k q; v += k u; if d >= p: d = (d - p) mod q
         {
-            float rq = rcp_approx(u64_to_f32_rz(q));
-            bool ok = divmod_fast(p, q, rq, k, r);
-            if (!ok) divmod_slow(p, q, k, r);
-            p = r;
+            const float rqs = scaled_rcp(qf);
+            bool ok1, ok2;
+            uint32_t k = quot_estimate(pf, rqs, ok1);
+            uint64_t pn = rem_fix(p, q, k);
+            const bool ge = d >= pn;
+            const uint64_t e = ge ? d - pn : 0ull;  // < k q: the quotient is at most k
+            uint32_t ke = quot_estimate(u64_to_f32_rz(e), rqs, ok2);
+            uint64_t en = rem_fix(e, q, ke);
+            if (!(ok1 && ok2)) {
+                pn = divmod_slow(p, q, k);
+                const bool ge2 = d >= pn;
+                en = divmod_slow(ge2 ? d - pn : 0ull, q, ke);
+            }
+            d = (d >= pn) ? en : d;
+            p = pn;
             v = sat_madd(v, k, u, n);
-            bool ge = d >= p;
-            uint64_t e = ge ? d - p : 0ull;  // < k q: the quotient is at most k
-            bool ok2 = divmod_fast(e, q, rq, kd, rd);
-            if (!ok2) divmod_slow(e, q, kd, rd);
-            d = ge ? rd : d;
             h++;
             if (u + v >= n) break;
         }
         if (p == 0) break;  // d was reduced mod q just above
+        pf = u64_to_f32_rz(p);
         // first half: k = floor(q/p); q -= k p; u += k v; d = d mod p
         {
-            float rp = rcp_approx(u64_to_f32_rz(p));
-            bool ok = divmod_fast(q, p, rp, k, r);
-            ok &= divmod_fast(d, p, rp, kd, rd);
-            if (!ok) {
-                divmod_slow(q, p, k, r);
-                divmod_slow(d, p, kd, rd);
+            const float rps = scaled_rcp(pf);
+            bool ok1, ok2;
+            uint32_t k = quot_estimate(qf, rps, ok1);
+            uint32_t kd = quot_estimate(u64_to_f32_rz(d), rps, ok2);
+            uint64_t qn = rem_fix(q, p, k);
+            uint64_t dn = rem_fix(d, p, kd);
+            if (!(ok1 && ok2)) {
+                qn = divmod_slow(q, p, k);
+                dn = divmod_slow(d, p, kd);
             }
-            q = r;
-            d = rd;
+            q = qn;
+            d = dn;
             u = sat_madd(u, k, v, n);
             h++;
             if (u + v >= n || q == 0) break;
         }
+        qf = u64_to_f32_rz(q);
     }
     *hs = h;
     return d;
@@ -267,7 +298,7 @@ __device__ __noinline__ void resolve_and_emit(bool fail, uint64_t B, uint64_t A,
     if (!all_hits) emit_warp(have && my_min < Tm, job, sub, arg_base + my_x, my_min, cand, cap, count);
 }
 
-__device__ __forceinline__ void flush_stats(uint64_t* stats, uint64_t lines, uint64_t fail, uint64_t half) {
+__device__ __forceinline__ void flush_stats(uint64_t* stats, uint32_t lines, uint32_t fail, uint32_t half) {
 #pragma unroll
     for (int off = 16; off; off >>= 1) {
         lines += __shfl_xor_sync(FULLMASK, lines, off);
@@ -292,8 +323,8 @@ struct Packet {
 };
 
 template <int L, int D>
-__device__ __forceinline__ void packet_init(Packet<L, D>& P, const DevTask& t, const DevJob& job,
-                                            const LaunchArgs& a) {
+__device__ __forceinline__ uint32_t packet_init(Packet<L, D>& P, const DevTask& t, const DevJob& job,
+                                                const LaunchArgs& a) {
     const int lane = threadIdx.x & 31;
     P.active = (uint32_t)lane < t.count;
     const uint64_t g = t.g0 + (P.active ? (uint64_t)lane : 0ull);
@@ -310,30 +341,28 @@ __device__ __forceinline__ void packet_init(Packet<L, D>& P, const DevTask& t, c
     P.i0 = (uint32_t)(pk * job.nu);
     P.i1 = min(P.i0 + job.nu, P.blk.n_sub);
     const uint64_t* tw = a.tables + P.blk.table_off;
-    Word<L> t0[D + 1], t1[D];
 #pragma unroll
     for (int w = 0; w <= D; w++)
 #pragma unroll
-        for (int l = 0; l < L; l++) t0[w].l[l] = __ldg(tw + w * L + l);
+        for (int l = 0; l < L; l++) P.d0[w].l[l] = __ldg(tw + w * L + l);
 #pragma unroll
     for (int w = 0; w < D; w++)
 #pragma unroll
-        for (int l = 0; l < L; l++) t1[w].l[l] = __ldg(tw + (D + 1 + w) * L + l);
-    // straightforward shift to sub-interval i0: Delta^l(i0) = sum_{k>=l} binom(i0, k-l) Delta^k(0)
+        for (int l = 0; l < L; l++) P.d1[w].l[l] = __ldg(tw + (D + 1 + w) * L + l);
+    // straightforward shift to sub-interval i0, in place (ascending l only
+    // reads the still-unshifted higher orders):
+    // Delta^l(i0) = sum_{k>=l} binom(i0, k-l) Delta^k(0)
     uint64_t c[5];
     binomials(P.i0, c);
 #pragma unroll
-    for (int l = 0; l <= D; l++) {
-        P.d0[l] = t0[l];
+    for (int l = 0; l < D; l++)
 #pragma unroll
-        for (int k = l + 1; k <= D; k++) w_add<L>(P.d0[l], w_mul_u64<L>(t0[k], c[k - l]));
-    }
+        for (int k = l + 1; k <= D; k++) w_add<L>(P.d0[l], w_mul_u64<L>(P.d0[k], c[k - l]));
 #pragma unroll
-    for (int l = 0; l < D; l++) {
-        P.d1[l] = t1[l];
+    for (int l = 0; l + 1 < D; l++)
 #pragma unroll
-        for (int k = l + 1; k < D; k++) w_add<L>(P.d1[l], w_mul_u64<L>(t1[k], c[k - l]));
-    }
+        for (int k = l + 1; k < D; k++) w_add<L>(P.d1[l], w_mul_u64<L>(P.d1[k], c[k - l]));
+    return lo;
 }
 
 // one tabulated-difference step: Delta^l(i+1) = Delta^l(i) + Delta^(l+1)(i), l ascending
@@ -355,34 +384,70 @@ __device__ __forceinline__ void packet_words(const Packet<L, D>& P, uint32_t m, 
     A = ~P.d1[0].l[L - 1] + (low == 0 ? 1ull : 0ull);
 }
 
+// Lines per packet held in shared memory between the two phases of a task.
+constexpr int NU_MAX = 8;
+constexpr int WARPS_PER_CTA = 8;
+
+struct LineStage {
+    uint64_t B[NU_MAX][32];
+    uint64_t A[NU_MAX][32];
+    uint32_t n[NU_MAX][32];   // arguments of the line; 0 = no line
+};
+
+// Phase 1 steps the packet's tabulated differences and parks the search words
+// and lengths of its nu lines in shared memory; phase 2 runs the search on
+// them with only the continued-fraction state live (the W-bit packet state
+// and the block record are dead by then), so the search loop is not starved
+// of registers.  Block fields are reloaded only on the rare resolve path.
 template <int L, int D>
-__device__ __forceinline__ void fused_task(const DevTask& t, const LaunchArgs& a, uint64_t& st_lines,
-                                           uint64_t& st_fail, uint64_t& st_half) {
-    const DevJob job = a.jobs[t.job];
-    Packet<L, D> P;
-    packet_init<L, D>(P, t, job, a);
-    const uint32_t N = 1u << job.log2_N;
-    const bool all_hits = (job.flags & TMD_ALL_HITS) != 0;
+__device__ __forceinline__ void fused_task(const DevTask& t, const LaunchArgs& a, LineStage& st,
+                                           uint32_t& st_lines, uint32_t& st_fail, uint32_t& st_half) {
+    const int lane = threadIdx.x & 31;
+    const uint32_t nu = a.jobs[t.job].nu;
+    uint32_t b, i0;
+    {
+        const DevJob job = a.jobs[t.job];
+        Packet<L, D> P;
+        const uint32_t bi = packet_init<L, D>(P, t, job, a);
+        b = bi;
+        i0 = P.i0;
+        const uint32_t N = 1u << job.log2_N;
 #pragma unroll 1
-    for (uint32_t it = 0; it < job.nu; it++) {
-        const uint32_t i = P.i0 + it;
-        const bool valid = P.active && i < P.i1;
-        uint64_t B, A;
-        packet_words<L, D>(P, job.m, B, A);
-        const uint64_t off = (uint64_t)i * N;
-        const uint32_t n = valid ? (uint32_t)min((uint64_t)N, P.blk.length - off) : 1u;
+        for (uint32_t it = 0; it < nu; it++) {
+            uint64_t B, A;
+            packet_words<L, D>(P, job.m, B, A);
+            const uint32_t i = P.i0 + it;
+            const bool valid = P.active && i < P.i1;
+            st.B[it][lane] = B;
+            st.A[it][lane] = A;
+            st.n[it][lane] = valid ? (uint32_t)min((uint64_t)N, P.blk.length - (uint64_t)i * N) : 0u;
+            packet_step<L, D>(P);
+        }
+    }
+    __syncwarp();
+    const uint64_t Tm = a.jobs[t.job].Tm;
+#pragma unroll 1
+    for (uint32_t it = 0; it < nu; it++) {
+        const uint32_t n = st.n[it][lane];
+        const uint64_t B = st.B[it][lane];
+        const uint64_t A = st.A[it][lane];
         uint32_t hs = 0;
         uint64_t lb = ~0ull;
-        if (valid) lb = cf_lower_bound(B, A, n, &hs);
-        const bool fail = valid && lb < job.Tm;
-        st_lines += valid ? 1 : 0;
-        st_fail += fail ? 1 : 0;
+        if (n) lb = cf_lower_bound(B, A, n, &hs);
+        const bool fail = n && lb < Tm;
+        st_lines += n ? 1u : 0u;
+        st_fail += fail ? 1u : 0u;
         st_half += hs;
-        if (__any_sync(FULLMASK, fail))
-            resolve_and_emit(fail, B, A, n, job.Tm, all_hits, t.job, (uint32_t)(P.blk.first_sub + i),
-                             P.blk.start + off, a.cand, a.cap, a.count);
-        packet_step<L, D>(P);
+        if (__any_sync(FULLMASK, fail)) {
+            const DevBlock& bk = a.blocks[b];
+            const DevJob& jb = a.jobs[t.job];
+            const uint32_t i = i0 + it;
+            resolve_and_emit(fail, B, A, n ? n : 1u, Tm, (jb.flags & TMD_ALL_HITS) != 0, t.job,
+                             (uint32_t)(bk.first_sub + i), bk.start + ((uint64_t)i << jb.log2_N),
+                             a.cand, a.cap, a.count);
+        }
     }
+    __syncwarp();
 }
 
 template <int L, int D>
@@ -407,11 +472,12 @@ __device__ __forceinline__ void generate_task(const DevTask& t, const LaunchArgs
 // ------------------------------------------------------------------- kernels
 template <int L, int D>
 __global__ void __launch_bounds__(256) k_fused(LaunchArgs a) {
+    __shared__ LineStage stage[WARPS_PER_CTA];
     const uint64_t w = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     if (w >= a.n_tasks) return;  // whole warp
-    uint64_t sl = 0, sf = 0, sh = 0;
+    uint32_t sl = 0, sf = 0, sh = 0;
     const DevTask t = a.tasks[w];
-    fused_task<L, D>(t, a, sl, sf, sh);
+    fused_task<L, D>(t, a, stage[threadIdx.x >> 5], sl, sf, sh);
     flush_stats(a.stats, sl, sf, sh);
 }
 
@@ -427,8 +493,10 @@ __global__ void __launch_bounds__(256) k_generate(LaunchArgs a) {
 // from a device counter until the list is exhausted (no waiting on other
 // warps: a single atomicAdd per task).
 __global__ void __launch_bounds__(256) k_persistent(LaunchArgs a) {
+    __shared__ LineStage stage[WARPS_PER_CTA];
+    LineStage& stg = stage[threadIdx.x >> 5];
     const int lane = threadIdx.x & 31;
-    uint64_t sl = 0, sf = 0, sh = 0;
+    uint32_t sl = 0, sf = 0, sh = 0;
     for (;;) {
         uint32_t t = 0;
         if (lane == 0) t = atomicAdd(a.queue_head, 1u);
@@ -437,18 +505,18 @@ __global__ void __launch_bounds__(256) k_persistent(LaunchArgs a) {
         const DevTask task = a.tasks[t];
         const uint32_t key = a.jobs[task.job].L * 8u + a.jobs[task.job].d;
         switch (key) {
-            case 9: fused_task<1, 1>(task, a, sl, sf, sh); break;
-            case 10: fused_task<1, 2>(task, a, sl, sf, sh); break;
-            case 11: fused_task<1, 3>(task, a, sl, sf, sh); break;
-            case 12: fused_task<1, 4>(task, a, sl, sf, sh); break;
-            case 17: fused_task<2, 1>(task, a, sl, sf, sh); break;
-            case 18: fused_task<2, 2>(task, a, sl, sf, sh); break;
-            case 19: fused_task<2, 3>(task, a, sl, sf, sh); break;
-            case 20: fused_task<2, 4>(task, a, sl, sf, sh); break;
-            case 25: fused_task<3, 1>(task, a, sl, sf, sh); break;
-            case 26: fused_task<3, 2>(task, a, sl, sf, sh); break;
-            case 27: fused_task<3, 3>(task, a, sl, sf, sh); break;
-            case 28: fused_task<3, 4>(task, a, sl, sf, sh); break;
+            case 9: fused_task<1, 1>(task, a, stg, sl, sf, sh); break;
+            case 10: fused_task<1, 2>(task, a, stg, sl, sf, sh); break;
+            case 11: fused_task<1, 3>(task, a, stg, sl, sf, sh); break;
+            case 12: fused_task<1, 4>(task, a, stg, sl, sf, sh); break;
+            case 17: fused_task<2, 1>(task, a, stg, sl, sf, sh); break;
+            case 18: fused_task<2, 2>(task, a, stg, sl, sf, sh); break;
+            case 19: fused_task<2, 3>(task, a, stg, sl, sf, sh); break;
+            case 20: fused_task<2, 4>(task, a, stg, sl, sf, sh); break;
+            case 25: fused_task<3, 1>(task, a, stg, sl, sf, sh); break;
+            case 26: fused_task<3, 2>(task, a, stg, sl, sf, sh); break;
+            case 27: fused_task<3, 3>(task, a, stg, sl, sf, sh); break;
+            case 28: fused_task<3, 4>(task, a, stg, sl, sf, sh); break;
             default: break;
         }
     }
@@ -510,7 +578,7 @@ __global__ void __launch_bounds__(256) k_search_lines(LineArgs a) {
     const bool all_hits = __any_sync(FULLMASK, valid && (flags & TMD_ALL_HITS));
     if (__any_sync(FULLMASK, fail))
         resolve_and_emit(fail, B, A, n, Tm, all_hits, job, sub, arg_base, a.cand, a.cap, a.count);
-    flush_stats(a.stats, valid ? 1 : 0, fail ? 1 : 0, hs);
+    flush_stats(a.stats, valid ? 1u : 0u, fail ? 1u : 0u, hs);
 }
 
 __global__ void __launch_bounds__(256) k_lower_bounds(const uint64_t* B, const uint64_t* A,

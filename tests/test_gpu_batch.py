@@ -1,0 +1,67 @@
+"""GPU parity of the batched form: one persistent, graph-captured launch over
+uneven mixed jobs gives the oracle's candidate list, replay after replay, and
+the same records as the per-job plain launches."""
+import pytest
+
+import workloads as wl
+from oracle import candidates as oc
+
+torch = pytest.importorskip("torch")
+tmd = pytest.importorskip("paper_1211_3056_gb300")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    c = tmd.Context(0)
+    yield c
+    c.close()
+
+
+MIXED = [
+    wl.Job(wl.FUNC_EXP2, 1, 24, 16, 8, 2, 12, 1, 0, 1 << 16),
+    wl.Job(wl.FUNC_LOG, 2, 30, 14, 8, 3, 14, 2, 12345, 1 << 20),
+    wl.Job(wl.FUNC_EXP, 0, 53, 20, 14, 3, 24, 3, wl.plain_start(), 1 << 26),
+    wl.Job(wl.FUNC_EXP, 1, 53, 18, 12, 4, 20, 3, 7 << 40, (1 << 24) + 777),
+    wl.Job(wl.FUNC_LOG, 3, 28, 14, 6, 2, 10, 1, 1 << 25, 1 << 21, wl.FLAG_BP_DIRECTED),
+    wl.Job(wl.FUNC_EXP2, 0, 53, 22, 16, 1, 18, 2, 5 << 30, 1 << 24),
+    wl.toy_job(),
+]
+
+
+def batch_records(b, d_cand, d_count):
+    recs, n = tmd.tmd_candidates(b.ctx, d_cand, d_count)
+    return recs, n
+
+
+def test_batch_matches_oracle_over_replays(ctx):
+    want = oc.candidates(MIXED)
+    d_cand, d_count = tmd.alloc_candidates(1 << 16)
+    b = tmd.Batch(ctx, MIXED, d_cand, d_count)
+    for _ in range(3):
+        b.launch()
+        got, n = batch_records(b, d_cand, d_count)
+        assert n == len(want)
+        assert got == want
+    st = b.stats()
+    assert st["lines"] == sum(__import__("oracle").plan.n_subintervals(j) for j in MIXED)
+    b.close()
+
+
+def test_batch_equals_plain_per_job(ctx):
+    jobs = wl.batched_jobs(njobs=6, m=24, size_log2_range=(24.0, 27.0))
+    d_cand, d_count = tmd.alloc_candidates(1 << 18)
+    b = tmd.Batch(ctx, jobs, d_cand, d_count)
+    b.launch()
+    got, n = batch_records(b, d_cand, d_count)
+    b.close()
+    plain = []
+    for j, job in enumerate(jobs):
+        recs, _ = tmd.run([job], ctx=ctx, fused=True, cap=1 << 18)
+        plain.extend((j,) + r[1:] for r in recs)
+    plain.sort(key=lambda r: (r[0], r[2], r[3]))
+    assert got == plain and n == len(plain)
+    # and one job of the batch against the oracle in full
+    k = min(range(len(jobs)), key=lambda i: jobs[i].count)
+    want = oc.job_candidates(jobs[k], k)
+    assert [r for r in got if r[0] == k] == sorted(want, key=lambda r: (r[0], r[2], r[3]))

@@ -251,6 +251,39 @@ tmd_status tmd_batch_stats(tmd_batch* batch, tmd_stats* out, void* stream);
 /* Free the batch's device memory and graph (after its replays finished). */
 tmd_status tmd_batch_destroy(tmd_batch* batch);
 
+/* ---- search without any device allocation --------------------------------- */
+
+/* Size of the device scratch array behind tmd_search_static (bytes): room for
+ * the plan of about 7000 Taylor blocks of a 192-bit, degree-3 job, e.g. one
+ * 2^36-argument binary64 slice with blocks of 2^24 arguments. */
+#define TMD_STATIC_SCRATCH_BYTES (2u << 20)
+
+/* The paper has no counterpart to this entry point: it is for callers that
+ * cannot allocate device memory when they search -- a host application whose
+ * own allocator has reserved the device memory pool, a plugin that its host
+ * forbids to allocate, or a real-time loop that allows no allocation after
+ * start-up.  It runs the same fused search as tmd_search with
+ * d_lin == NULL, but needs no context and calls no cudaMalloc, cudaFree or
+ * other allocating routine (the host-side plan uses ordinary heap memory):
+ * the plan (jobs, blocks, tables, work list) and the counters live in one
+ * file-scope device array of TMD_STATIC_SCRATCH_BYTES (+ 256) bytes that
+ * every GPU loading the library holds until the process exits.
+ *
+ * Runs on the current CUDA device and `stream`; the caller still owns the
+ * outputs d_cand[cand_cap] and d_count (results exactly as tmd_search).  The
+ * first call on a device looks up the array's device address
+ * (cudaGetSymbolAddress) and caches it; make that first call before any
+ * stream capture.  TMD_ENOMEM when the jobs' plan exceeds
+ * TMD_STATIC_SCRATCH_BYTES (nothing is launched); TMD_EINVAL on bad
+ * arguments; TMD_ECUDA on a failed runtime call.  Every call uses the same
+ * array and leaves its contents behind (the counters are cleared at the
+ * start of each call): calls whose work overlaps on the GPU -- on different
+ * streams or host threads -- race and corrupt each other.  The results are
+ * read like any caller buffer (cudaMemcpy of *d_count and the records); the
+ * counters of tmd_stats are not exposed for these calls. */
+tmd_status tmd_search_static(const tmd_job* jobs, uint32_t njobs, tmd_candidate* d_cand,
+                             uint64_t cand_cap, uint64_t* d_count, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

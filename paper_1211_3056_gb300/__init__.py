@@ -212,6 +212,19 @@ def tmd_batch_destroy(batch: Batch) -> None:
     batch.close()
 
 
+def tmd_search_static(jobs: Sequence, d_cand, d_count, stream=None) -> None:
+    """Fused search of `jobs` on the current device without any device
+    allocation: the plan goes into the library's fixed device array
+    (include/tmd.h, TMD_STATIC_SCRATCH_BYTES).  For callers that may not
+    allocate device memory while they search; calls that overlap on the GPU
+    share that array and race.  Raises TmdError(TMD_ENOMEM) when the plan does
+    not fit."""
+    arr = job_array(jobs)
+    cap = 0 if d_cand is None else (d_cand.numel() * d_cand.element_size()) // CANDIDATE_BYTES
+    check(lib().tmd_search_static(arr, len(jobs), _ptr(d_cand), cap, _ptr(d_count),
+                                  _stream_ptr(stream)), "tmd_search_static")
+
+
 # ------------------------------------------------------------- conveniences
 def alloc_candidates(cap: int, device: int = 0):
     """Device buffers for cap records and the count (torch tensors)."""

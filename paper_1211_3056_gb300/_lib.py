@@ -78,6 +78,7 @@ SIGNATURES = {
     "tmd_batch_launch": (ctypes.c_int, [_vp, _vp]),
     "tmd_batch_stats": (ctypes.c_int, [_vp, ctypes.POINTER(tmd_stats), _vp]),
     "tmd_batch_destroy": (ctypes.c_int, [_vp]),
+    "tmd_search_static": (ctypes.c_int, [ctypes.POINTER(tmd_job), _u32, _vp, _u64, _vp, _vp]),
 }
 
 _LIB = None

@@ -6,6 +6,7 @@
 #include <atomic>
 #include <cstdlib>
 #include <cstring>
+#include <mutex>
 #include <thread>
 #include <vector>
 
@@ -651,3 +652,89 @@ tmd_status tmd_batch_destroy(tmd_batch* b) {
 
 }  // extern "C"
 
+// ------------------------------------------------- no-allocation entry point
+// tmd_search_static keeps everything the search needs besides the caller's
+// inputs and outputs -- the plan arena (jobs, blocks, tables, work list) and
+// the counters -- in one file-scope device array instead of memory from
+// cudaMalloc.  The array exists on every device that loads the library until
+// the process exits.  Host code must not pass `g_static_scratch` itself to a
+// kernel (in host code that name is a host-side stand-in); its device address
+// is taken once per device with cudaGetSymbolAddress and cached below.
+
+namespace {
+
+constexpr size_t STATIC_MISC_BYTES = 256;  // stats[4], error word, queue head
+__device__ __align__(256) unsigned char g_static_scratch[STATIC_MISC_BYTES + TMD_STATIC_SCRATCH_BYTES];
+
+constexpr int STATIC_MAX_DEVICES = 64;
+std::mutex g_static_mutex;
+char* g_static_base[STATIC_MAX_DEVICES] = {};
+
+// Device address of the scratch array on the current device (set-up on the
+// first call per device).
+tmd_status static_scratch_base(int device, char** out) {
+    if (device < 0 || device >= STATIC_MAX_DEVICES) return TMD_EUNSUPPORTED;
+    std::lock_guard<std::mutex> lock(g_static_mutex);
+    if (!g_static_base[device]) {
+        void* p = nullptr;
+        cudaError_t e = cudaGetSymbolAddress(&p, g_static_scratch);
+        if (e != cudaSuccess || p == nullptr) return TMD_ECUDA;
+        g_static_base[device] = (char*)p;
+    }
+    *out = g_static_base[device];
+    return TMD_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+tmd_status tmd_search_static(const tmd_job* jobs, uint32_t njobs, tmd_candidate* d_cand,
+                             uint64_t cand_cap, uint64_t* d_count, void* stream) {
+    if (!jobs || njobs == 0 || !d_count || (cand_cap && !d_cand)) return TMD_EINVAL;
+    int device = 0;
+    CK(cudaGetDevice(&device));
+    char* base = nullptr;
+    tmd_status st = static_scratch_base(device, &base);
+    if (st != TMD_OK) return st;
+    Plan P;
+    st = build_plan(jobs, njobs, P);
+    if (st != TMD_OK) return st;
+    const size_t o_blocks = align256(P.jobs.size() * sizeof(DevJob));
+    const size_t o_tables = align256(o_blocks + P.blocks.size() * sizeof(DevBlock));
+    const size_t o_tasks = align256(o_tables + P.tables.size() * sizeof(uint64_t));
+    const size_t total = align256(o_tasks + P.tasks.size() * sizeof(DevTask));
+    if (total > TMD_STATIC_SCRATCH_BYTES) return TMD_ENOMEM;
+    std::vector<char> host(total, 0);
+    memcpy(host.data(), P.jobs.data(), P.jobs.size() * sizeof(DevJob));
+    memcpy(host.data() + o_blocks, P.blocks.data(), P.blocks.size() * sizeof(DevBlock));
+    memcpy(host.data() + o_tables, P.tables.data(), P.tables.size() * sizeof(uint64_t));
+    memcpy(host.data() + o_tasks, P.tasks.data(), P.tasks.size() * sizeof(DevTask));
+    cudaStream_t s = (cudaStream_t)stream;
+    char* arena = base + STATIC_MISC_BYTES;
+    // pageable source: the call returns once the bytes are staged, so the
+    // vector may go out of scope afterwards
+    CK(cudaMemcpyAsync(arena, host.data(), total, cudaMemcpyHostToDevice, s));
+    CK(cudaMemsetAsync(base, 0, STATIC_MISC_BYTES, s));
+    CK(cudaMemsetAsync(d_count, 0, sizeof(uint64_t), s));
+    LaunchArgs a;
+    memset(&a, 0, sizeof a);
+    a.jobs = (const DevJob*)arena;
+    a.blocks = (const DevBlock*)(arena + o_blocks);
+    a.tables = (const uint64_t*)(arena + o_tables);
+    a.tasks = (const DevTask*)(arena + o_tasks);
+    a.cand = d_cand;
+    a.cap = cand_cap;
+    a.count = d_count;
+    a.stats = (uint64_t*)base;
+    a.queue_head = (uint32_t*)(base + sizeof(uint64_t) * ST_COUNT) + 1;
+    for (const ClassRange& cr : P.classes) {
+        LaunchArgs la = a;
+        la.tasks = a.tasks + cr.first;
+        la.n_tasks = cr.count;
+        CK(launch_tasks(true, cr.L, cr.D, la, s));
+    }
+    return TMD_OK;
+}
+
+}  // extern "C"

@@ -207,6 +207,42 @@ def run_reference(args):
         dist.barrier()
 
 
+# ----------------------------------------------------------- served form
+def run_serving(tmd, ctx, jobs, rate_per_s, seed=2012):
+    """Submit `jobs` with exponential gaps (rate_per_s; inf = all at once)
+    to a server on ctx and collect every result.  Returns (wall seconds,
+    latencies in s, total args, total records)."""
+    import math
+    gaps = ([0.0] * len(jobs) if math.isinf(rate_per_s)
+            else [g2 - g1 for g1, g2 in zip([0.0] + wl.arrival_times(len(jobs), rate_per_s, seed)[:-1],
+                                            wl.arrival_times(len(jobs), rate_per_s, seed))])
+    lat, recs = [], 0
+    with tmd.Server(ctx, max_inflight=16, chunk_tasks=4096, cand_cap=1 << 14) as srv:
+        t0 = time.perf_counter()
+        next_t = t0
+        done = 0
+        for tag, (job, gap) in enumerate(zip(jobs, gaps)):
+            next_t += gap
+            while True:
+                now = time.perf_counter()
+                if now >= next_t:
+                    break
+                for r, rr in srv.poll(wait_ms=0):
+                    lat.append(r["t_done"] - r["t_submit"]); recs += r["count"]; done += 1
+                time.sleep(min(1e-4, next_t - now))
+            srv.submit(job, tag)
+        while done < len(jobs):
+            for r, rr in srv.poll(wait_ms=50):
+                lat.append(r["t_done"] - r["t_submit"]); recs += r["count"]; done += 1
+        wall = time.perf_counter() - t0
+    return wall, lat, sum(j.count for j in jobs), recs
+
+
+def percentile(xs, q):
+    ys = sorted(xs)
+    return ys[min(len(ys) - 1, int(q * (len(ys) - 1) + 0.5))]
+
+
 # ------------------------------------------------------------- native arm
 def main():
     ap = argparse.ArgumentParser()
@@ -218,6 +254,8 @@ def main():
     ap.add_argument("--ref-seconds", type=float, default=12.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--m", type=int, default=40)
+    ap.add_argument("--serve-jobs", type=int, default=400,
+                    help="jobs of the seeded serving stream to serve (0 = skip)")
     ap.add_argument("--count-log2", type=int, default=36,
                     help="slice size (smaller only for profiling captures)")
     args = ap.parse_args()
@@ -340,6 +378,19 @@ def main():
                 "half_steps_per_line": stats["half_steps"] / max(1, stats["lines"]),
                 "filter_fail_per_line": stats["filter_fail"] / max(1, stats["lines"])}
 
+    serving = None
+    if rank == 0 and args.serve_jobs > 0:
+        sjobs = wl.serving_jobs()[: args.serve_jobs]
+        mean_size = sum(j.count for j in sjobs) / len(sjobs)
+        w_sat, lat_sat, a_sat, _ = run_serving(tmd, ctx, sjobs, float("inf"))
+        sat = a_sat / w_sat
+        rate = 0.8 * sat / mean_size
+        w, lat, a, nrec = run_serving(tmd, ctx, sjobs, rate)
+        serving = {"jobs": len(sjobs), "arrival_rate_jobs_per_s": rate, "mean_job_args": mean_size,
+                   "p50_ms": 1e3 * percentile(lat, 0.50), "p99_ms": 1e3 * percentile(lat, 0.99),
+                   "args_per_s": a / w, "saturated_args_per_s": sat, "records": nrec,
+                   "form": "continuous batching, 16 slots, Poisson arrivals at 0.8 x saturated rate"}
+
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
         a, dt, nb, th = oracle_sample(job, seconds_target=args.ref_seconds)
@@ -363,7 +414,7 @@ def main():
             "e2e": {"value": total_args / e2e_s, "unit": UNIT, "h2d_bytes_per_step": h2d,
                     "d2h_bytes_per_step": d2h, "ms_per_step": e2e_s * 1e3},
             "gpu_launches": args.steps * 1,
-            "roofline": roofline, "cpu_baseline": cpu, "clocks": clocks,
+            "roofline": roofline, "cpu_baseline": cpu, "clocks": clocks, "serving": serving,
         }
         print(json.dumps(line), flush=True)
     batch.close()

@@ -251,6 +251,61 @@ tmd_status tmd_batch_stats(tmd_batch* batch, tmd_stats* out, void* stream);
 /* Free the batch's device memory and graph (after its replays finished). */
 tmd_status tmd_batch_destroy(tmd_batch* batch);
 
+/* ---- served form: continuous batching of arriving jobs ---------------------- */
+
+typedef struct tmd_server tmd_server;
+
+typedef struct {
+    uint64_t device_budget;  /* bytes of device memory for the plans of resident jobs
+                                (0 = 1 GiB); a job waits until its plan fits      */
+    uint32_t max_inflight;   /* jobs resident on the device at once, one stream each
+                                (1..64; 0 = 8)                                     */
+    uint32_t chunk_tasks;    /* warp tasks per launch; a job runs as consecutive
+                                launches over its resident tables (0 = 2048)       */
+    uint64_t cand_cap;       /* records kept per job; the count stays exact (0 = 65536) */
+} tmd_server_config;
+
+typedef struct {
+    uint64_t id;             /* the caller's tag from tmd_server_submit            */
+    int32_t  status;         /* tmd_status of this job (TMD_EOVERFLOW: records cut) */
+    uint32_t reserved;
+    uint64_t count;          /* exact number of records of the job                 */
+    uint64_t n_records;      /* records returned for it by tmd_server_poll         */
+    double   t_submit, t_start, t_done;  /* seconds on the server's clock          */
+} tmd_job_result;
+
+/* Start the serving loop on ctx's device: a host thread admits submitted jobs
+ * in arrival order whenever a slot is free and the job's plan fits the
+ * device budget, plans it (host), uploads it and computes its block tables
+ * on the device, and runs the fused search in chunks on the slot's stream,
+ * so that jobs admitted while others run overlap on the GPU.  Finished jobs
+ * are read back (count and sorted records) and queued for tmd_server_poll.
+ * Each job's result is the one tmd_search gives it alone.  The server uses
+ * ctx only for its device; ctx must outlive it. */
+tmd_status tmd_server_create(tmd_ctx* ctx, const tmd_server_config* cfg, tmd_server** server);
+
+/* Queue one job under the caller's tag (thread-safe, never blocks on the GPU).
+ * TMD_EINVAL for a job that fails validation (nothing is queued). */
+tmd_status tmd_server_submit(tmd_server* server, const tmd_job* job, uint64_t id);
+
+/* Move up to `cap` finished jobs into out[] (completion order) and their
+ * records, concatenated in the same order, into h_records[0 .. rec_cap)
+ * (records that do not fit are dropped and the job's n_records says so).
+ * Waits up to wait_ms milliseconds for the first result (0 = do not wait).
+ * *n_out = results returned, *rec_out = records written. */
+tmd_status tmd_server_poll(tmd_server* server, tmd_job_result* out, uint32_t cap, uint32_t* n_out,
+                           tmd_candidate* h_records, uint64_t rec_cap, uint64_t* rec_out,
+                           int32_t wait_ms);
+
+/* Jobs submitted but not yet returned by tmd_server_poll. */
+tmd_status tmd_server_pending(tmd_server* server, uint64_t* n);
+
+/* Seconds on the server's clock (the clock of tmd_job_result). */
+double tmd_server_clock(tmd_server* server);
+
+/* Stop: wait for the jobs on the device, drop queued ones, free everything. */
+tmd_status tmd_server_destroy(tmd_server* server);
+
 /* ---- search without any device allocation --------------------------------- */
 
 /* Size of the device scratch array behind tmd_search_static (bytes): room for

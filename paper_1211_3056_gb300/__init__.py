@@ -212,6 +212,68 @@ def tmd_batch_destroy(batch: Batch) -> None:
     batch.close()
 
 
+class Server:
+    """A tmd_server: continuous batching of submitted jobs on ctx's device."""
+
+    def __init__(self, ctx: Context, device_budget: int = 0, max_inflight: int = 0,
+                 chunk_tasks: int = 0, cand_cap: int = 0):
+        cfg = _lib.tmd_server_config(device_budget, max_inflight, chunk_tasks, cand_cap)
+        h = ctypes.c_void_p()
+        check(lib().tmd_server_create(ctx.handle, ctypes.byref(cfg), ctypes.byref(h)), "tmd_server_create")
+        self.handle = h
+        self.ctx = ctx
+
+    def submit(self, job, tag: int) -> None:
+        check(lib().tmd_server_submit(self.handle, ctypes.byref(make_job(job)), int(tag)), "tmd_server_submit")
+
+    def poll(self, cap: int = 256, rec_cap: int = 1 << 16, wait_ms: int = 0):
+        """[(result dict, [(job, subint, arg_index, value), ...]), ...]"""
+        res = (_lib.tmd_job_result * cap)()
+        recs = (_lib.tmd_candidate * max(1, rec_cap))()
+        n = ctypes.c_uint32(0)
+        nr = ctypes.c_uint64(0)
+        check(lib().tmd_server_poll(self.handle, res, cap, ctypes.byref(n), recs, rec_cap, ctypes.byref(nr),
+                                    int(wait_ms)), "tmd_server_poll")
+        out, pos = [], 0
+        for i in range(n.value):
+            r = res[i]
+            k = r.n_records
+            rr = [(recs[j].job, recs[j].subint, recs[j].arg_index, recs[j].value) for j in range(pos, pos + k)]
+            pos += k
+            out.append(({"id": r.id, "status": r.status, "count": r.count, "n_records": k,
+                         "t_submit": r.t_submit, "t_start": r.t_start, "t_done": r.t_done}, rr))
+        return out
+
+    def pending(self) -> int:
+        n = ctypes.c_uint64(0)
+        check(lib().tmd_server_pending(self.handle, ctypes.byref(n)), "tmd_server_pending")
+        return n.value
+
+    def clock(self) -> float:
+        return lib().tmd_server_clock(self.handle)
+
+    def close(self):
+        if getattr(self, "handle", None):
+            lib().tmd_server_destroy(self.handle)
+            self.handle = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def tmd_server_create(ctx: Context, **cfg) -> Server:
+    return Server(ctx, **cfg)
+
+
 def tmd_search_static(jobs: Sequence, d_cand, d_count, stream=None) -> None:
     """Fused search of `jobs` on the current device without any device
     allocation: the plan goes into the library's fixed device array

@@ -44,6 +44,17 @@ class tmd_block_info(ctypes.Structure):
                 ("scale_log2", ctypes.c_int32)]
 
 
+class tmd_server_config(ctypes.Structure):
+    _fields_ = [("device_budget", ctypes.c_uint64), ("max_inflight", ctypes.c_uint32),
+                ("chunk_tasks", ctypes.c_uint32), ("cand_cap", ctypes.c_uint64)]
+
+
+class tmd_job_result(ctypes.Structure):
+    _fields_ = [("id", ctypes.c_uint64), ("status", ctypes.c_int32), ("reserved", ctypes.c_uint32),
+                ("count", ctypes.c_uint64), ("n_records", ctypes.c_uint64),
+                ("t_submit", ctypes.c_double), ("t_start", ctypes.c_double), ("t_done", ctypes.c_double)]
+
+
 class tmd_stats(ctypes.Structure):
     _fields_ = [("lines", ctypes.c_uint64), ("filter_fail", ctypes.c_uint64),
                 ("candidates", ctypes.c_uint64), ("half_steps", ctypes.c_uint64),
@@ -79,6 +90,13 @@ SIGNATURES = {
     "tmd_batch_stats": (ctypes.c_int, [_vp, ctypes.POINTER(tmd_stats), _vp]),
     "tmd_batch_destroy": (ctypes.c_int, [_vp]),
     "tmd_search_static": (ctypes.c_int, [ctypes.POINTER(tmd_job), _u32, _vp, _u64, _vp, _vp]),
+    "tmd_server_create": (ctypes.c_int, [_vp, ctypes.POINTER(tmd_server_config), ctypes.POINTER(_vp)]),
+    "tmd_server_submit": (ctypes.c_int, [_vp, ctypes.POINTER(tmd_job), _u64]),
+    "tmd_server_poll": (ctypes.c_int, [_vp, ctypes.POINTER(tmd_job_result), _u32, ctypes.POINTER(_u32),
+                                       _vp, _u64, ctypes.POINTER(_u64), ctypes.c_int32]),
+    "tmd_server_pending": (ctypes.c_int, [_vp, ctypes.POINTER(_u64)]),
+    "tmd_server_clock": (ctypes.c_double, [_vp]),
+    "tmd_server_destroy": (ctypes.c_int, [_vp]),
 }
 
 _LIB = None

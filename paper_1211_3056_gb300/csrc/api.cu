@@ -5,11 +5,15 @@
 #include <algorithm>
 #include <atomic>
 #include <cstdlib>
+#include <chrono>
+#include <condition_variable>
 #include <cstring>
+#include <deque>
 #include <mutex>
 #include <thread>
 #include <vector>
 
+#include "coeffs.cuh"
 #include "dev.hpp"
 #include "host.hpp"
 
@@ -17,6 +21,9 @@ namespace tmd {
 cudaError_t launch_tasks(bool fused, uint32_t L, uint32_t D, const LaunchArgs& a, cudaStream_t s);
 cudaError_t launch_persistent(const LaunchArgs& a, int ctas, cudaStream_t s);
 cudaError_t persistent_occupancy(int* blocks_per_sm);
+cudaError_t upload_coeff_consts(const CoeffConsts& C);
+cudaError_t launch_block_tables(const DevJob* jobs, const DevBlock* blocks, uint64_t n_blocks,
+                                uint64_t* tables, uint32_t* status, uint32_t* err, cudaStream_t s);
 }  // namespace tmd
 
 namespace tmd {
@@ -44,6 +51,8 @@ struct Plan {
     std::vector<ClassRange> classes;
     uint64_t total_lines = 0;
     uint64_t total_args = 0;
+    uint64_t table_words = 0;
+    bool host_tables = true;
 };
 
 size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
@@ -75,6 +84,7 @@ namespace {
 uint64_t* stats_ptr(tmd_ctx* c) { return c->d_misc; }
 uint32_t* err_ptr(tmd_ctx* c) { return (uint32_t*)(c->d_misc + ST_COUNT); }
 uint32_t* queue_ptr(tmd_ctx* c) { return (uint32_t*)(c->d_misc + ST_COUNT) + 1; }
+uint32_t* plan_err_ptr(tmd_ctx* c) { return (uint32_t*)(c->d_misc + ST_COUNT) + 2; }
 
 #define CK(x)                                  \
     do {                                       \
@@ -100,10 +110,12 @@ uint32_t choose_nu(const tmd_job& job, uint64_t n_sub_block) {
     return nu;
 }
 
-// Plan every job, compute all block tables (threads over blocks).
-tmd_status build_plan(const tmd_job* jobs, uint32_t njobs, Plan& P) {
+// Plan every job; with host_tables, also compute all block tables (threads
+// over blocks), otherwise the table kernel computes them on the device.
+tmd_status build_plan(const tmd_job* jobs, uint32_t njobs, Plan& P, bool host_tables = true) {
     P = Plan();
     if (njobs == 0 || !jobs) return TMD_EINVAL;
+    P.host_tables = host_tables;
     P.key.assign(jobs, jobs + njobs);
     std::vector<std::vector<Segment>> segs(njobs);
     std::vector<BlockPlan> bplan;
@@ -130,6 +142,9 @@ tmd_status build_plan(const tmd_job* jobs, uint32_t njobs, Plan& P) {
         dj.L = jb.limbs;
         dj.m = (uint32_t)jb.m;
         dj.flags = jb.flags;
+        dj.func = jb.func;
+        dj.e_in = jb.e_in;
+        dj.p = jb.p;
         const uint64_t nsub_full = 1ull << (jb.log2_T - jb.log2_N);
         dj.nu = choose_nu(jb, nsub_full);
         const uint64_t words = (uint64_t)(2 * jb.d + 1) * jb.limbs;
@@ -145,6 +160,8 @@ tmd_status build_plan(const tmd_job* jobs, uint32_t njobs, Plan& P) {
             db.table_off = toff;
             db.job = j;
             db.n_sub = (uint32_t)((bp.length + (1ull << jb.log2_N) - 1) >> jb.log2_N);
+            db.e_out = bp.e_out;
+            db.pad = 0;
             packet += (db.n_sub + dj.nu - 1) / dj.nu;
             toff += words;
             P.blocks.push_back(db);
@@ -163,7 +180,8 @@ tmd_status build_plan(const tmd_job* jobs, uint32_t njobs, Plan& P) {
         P.total_args += jb.count;
     }
     P.total_lines = line;
-    P.tables.assign(toff, 0);
+    P.table_words = toff;
+    if (host_tables) P.tables.assign(toff, 0);
     // correctly rounded tables, blocks spread over host threads
     std::atomic<uint64_t> next(0);
     std::atomic<int> bad(0);
@@ -181,7 +199,9 @@ tmd_status build_plan(const tmd_job* jobs, uint32_t njobs, Plan& P) {
         }
     };
     unsigned nt = std::min<uint64_t>(host_threads(), (nblk + 15) / 16);
-    if (nt <= 1) {
+    if (!host_tables) {
+        // tables come from the device kernel
+    } else if (nt <= 1) {
         worker();
     } else {
         std::vector<std::thread> th;
@@ -203,21 +223,26 @@ tmd_status build_plan(const tmd_job* jobs, uint32_t njobs, Plan& P) {
     return TMD_OK;
 }
 
+// Arena layout: jobs | blocks | tasks | table status | tables.  The first
+// three sections are uploaded; the tables are uploaded when they were made
+// on the host, else written by the table kernel on the device.
 tmd_status upload_plan(tmd_ctx* c, cudaStream_t s) {
     Plan& P = c->plan;
     size_t o_jobs = 0;
     size_t o_blocks = align256(o_jobs + P.jobs.size() * sizeof(DevJob));
-    size_t o_tables = align256(o_blocks + P.blocks.size() * sizeof(DevBlock));
-    size_t o_tasks = align256(o_tables + P.tables.size() * sizeof(uint64_t));
-    size_t total = align256(o_tasks + P.tasks.size() * sizeof(DevTask));
+    size_t o_tasks = align256(o_blocks + P.blocks.size() * sizeof(DevBlock));
+    size_t o_status = align256(o_tasks + P.tasks.size() * sizeof(DevTask));
+    size_t o_tables = align256(o_status + P.blocks.size() * sizeof(uint32_t));
+    size_t total = align256(o_tables + P.table_words * sizeof(uint64_t));
+    size_t upload = P.host_tables ? total : o_status;
     if (c->stage_pending) {
         CK(cudaEventSynchronize(c->stage_done));
         c->stage_pending = false;
     }
-    if (total > c->stage_cap) {
+    if (upload > c->stage_cap) {
         if (c->h_stage) CK(cudaFreeHost(c->h_stage));
         c->h_stage = nullptr;
-        size_t cap = std::max(total, c->stage_cap * 2);
+        size_t cap = std::max(upload, c->stage_cap * 2);
         CK(cudaHostAlloc((void**)&c->h_stage, cap, cudaHostAllocDefault));
         c->stage_cap = cap;
     }
@@ -229,18 +254,24 @@ tmd_status upload_plan(tmd_ctx* c, cudaStream_t s) {
         CK(cudaMalloc((void**)&c->d_arena, cap));
         c->arena_cap = cap;
     }
+    memset(c->h_stage, 0, upload);
     memcpy(c->h_stage + o_jobs, P.jobs.data(), P.jobs.size() * sizeof(DevJob));
     memcpy(c->h_stage + o_blocks, P.blocks.data(), P.blocks.size() * sizeof(DevBlock));
-    memcpy(c->h_stage + o_tables, P.tables.data(), P.tables.size() * sizeof(uint64_t));
     memcpy(c->h_stage + o_tasks, P.tasks.data(), P.tasks.size() * sizeof(DevTask));
-    CK(cudaMemcpyAsync(c->d_arena, c->h_stage, total, cudaMemcpyHostToDevice, s));
+    if (P.host_tables) memcpy(c->h_stage + o_tables, P.tables.data(), P.tables.size() * sizeof(uint64_t));
+    CK(cudaMemcpyAsync(c->d_arena, c->h_stage, upload, cudaMemcpyHostToDevice, s));
     CK(cudaEventRecord(c->stage_done, s));
-    c->upload_bytes = total;
     c->stage_pending = true;
+    c->upload_bytes = upload;
     c->off_jobs = o_jobs;
     c->off_blocks = o_blocks;
     c->off_tables = o_tables;
     c->off_tasks = o_tasks;
+    CK(cudaMemsetAsync(plan_err_ptr(c), 0, sizeof(uint32_t), s));
+    if (!P.host_tables)
+        CK(launch_block_tables((const DevJob*)(c->d_arena + o_jobs), (const DevBlock*)(c->d_arena + o_blocks),
+                               P.blocks.size(), (uint64_t*)(c->d_arena + o_tables),
+                               (uint32_t*)(c->d_arena + o_status), plan_err_ptr(c), s));
     return TMD_OK;
 }
 
@@ -252,7 +283,7 @@ bool same_jobs(const tmd_ctx* c, const tmd_job* jobs, uint32_t njobs) {
 tmd_status make_resident(tmd_ctx* c, const tmd_job* jobs, uint32_t njobs, cudaStream_t s) {
     if (same_jobs(c, jobs, njobs)) return TMD_OK;
     c->resident = false;
-    tmd_status st = build_plan(jobs, njobs, c->plan);
+    tmd_status st = build_plan(jobs, njobs, c->plan, /*host_tables=*/false);
     if (st != TMD_OK) return st;
     st = upload_plan(c, s);
     if (st != TMD_OK) return st;
@@ -313,6 +344,10 @@ tmd_status tmd_create(tmd_ctx** out, int device) {
         return TMD_ECUDA;
     }
     cudaMemset(c->d_misc, 0, 64);
+    if (upload_coeff_consts(coeff_consts()) != cudaSuccess) {
+        tmd_destroy(c);
+        return TMD_ECUDA;
+    }
     *out = c;
     return TMD_OK;
 }
@@ -441,10 +476,12 @@ tmd_status tmd_candidates(tmd_ctx* c, const tmd_candidate* d_cand, const uint64_
     cudaStream_t s = (cudaStream_t)stream;
     CK(cudaSetDevice(c->device));
     uint64_t count = 0;
-    uint32_t err = 0;
+    uint32_t err = 0, perr = 0;
     CK(cudaMemcpyAsync(&count, d_count, sizeof count, cudaMemcpyDeviceToHost, s));
     CK(cudaMemcpyAsync(&err, err_ptr(c), sizeof err, cudaMemcpyDeviceToHost, s));
+    CK(cudaMemcpyAsync(&perr, plan_err_ptr(c), sizeof perr, cudaMemcpyDeviceToHost, s));
     CK(cudaStreamSynchronize(s));
+    if (perr) return TMD_EUNSUPPORTED;
     *n_out = count;
     uint64_t n = std::min(count, std::min(cand_cap, h_cap));
     if (n) {
@@ -559,30 +596,46 @@ tmd_status tmd_batch_create(tmd_ctx* c, const tmd_job* jobs, uint32_t njobs, tmd
     tmd_batch* b = new tmd_batch();
     b->ctx = c;
     b->d_count = d_count;
-    tmd_status st = build_plan(jobs, njobs, b->plan);
+    tmd_status st = build_plan(jobs, njobs, b->plan, /*host_tables=*/false);
     if (st != TMD_OK) {
         batch_free(b);
         return st;
     }
     Plan& P = b->plan;
+    // arena: jobs | blocks | tasks | table status | tables (device-written)
     size_t o_blocks = align256(P.jobs.size() * sizeof(DevJob));
-    size_t o_tables = align256(o_blocks + P.blocks.size() * sizeof(DevBlock));
-    size_t o_tasks = align256(o_tables + P.tables.size() * sizeof(uint64_t));
-    size_t total = align256(o_tasks + P.tasks.size() * sizeof(DevTask));
-    std::vector<char> host(total, 0);
+    size_t o_tasks = align256(o_blocks + P.blocks.size() * sizeof(DevBlock));
+    size_t o_status = align256(o_tasks + P.tasks.size() * sizeof(DevTask));
+    size_t o_tables = align256(o_status + P.blocks.size() * sizeof(uint32_t));
+    size_t total = align256(o_tables + P.table_words * sizeof(uint64_t));
+    std::vector<char> host(o_status, 0);
     memcpy(host.data(), P.jobs.data(), P.jobs.size() * sizeof(DevJob));
     memcpy(host.data() + o_blocks, P.blocks.data(), P.blocks.size() * sizeof(DevBlock));
-    memcpy(host.data() + o_tables, P.tables.data(), P.tables.size() * sizeof(uint64_t));
     memcpy(host.data() + o_tasks, P.tasks.data(), P.tasks.size() * sizeof(DevTask));
+    uint32_t* plan_err = nullptr;
+    uint32_t perr = 0;
     if (cudaMalloc((void**)&b->d_arena, total) != cudaSuccess ||
         cudaMalloc((void**)&b->d_misc, 64) != cudaSuccess ||
-        cudaMemcpyAsync(b->d_arena, host.data(), total, cudaMemcpyHostToDevice, s) != cudaSuccess ||
+        cudaMemsetAsync(b->d_misc, 0, 64, s) != cudaSuccess ||
+        cudaMemcpyAsync(b->d_arena, host.data(), o_status, cudaMemcpyHostToDevice, s) != cudaSuccess) {
+        batch_free(b);
+        return TMD_ECUDA;
+    }
+    plan_err = (uint32_t*)(b->d_misc + ST_COUNT) + 2;
+    if (launch_block_tables((const DevJob*)b->d_arena, (const DevBlock*)(b->d_arena + o_blocks), P.blocks.size(),
+                            (uint64_t*)(b->d_arena + o_tables), (uint32_t*)(b->d_arena + o_status), plan_err,
+                            s) != cudaSuccess ||
+        cudaMemcpyAsync(&perr, plan_err, sizeof perr, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
         cudaStreamSynchronize(s) != cudaSuccess) {
         batch_free(b);
         return TMD_ECUDA;
     }
-    b->upload_bytes = total;
-    if (upload_bytes) *upload_bytes = total;
+    if (perr) {
+        batch_free(b);
+        return TMD_EUNSUPPORTED;
+    }
+    b->upload_bytes = o_status;
+    if (upload_bytes) *upload_bytes = o_status;
     b->off_blocks = o_blocks;
     b->off_tables = o_tables;
     b->off_tasks = o_tasks;
@@ -647,6 +700,371 @@ tmd_status tmd_batch_destroy(tmd_batch* b) {
     if (!b) return TMD_EINVAL;
     cudaSetDevice(b->ctx->device);
     batch_free(b);
+    return TMD_OK;
+}
+
+}  // extern "C"
+
+// ------------------------------------------------------------ serving loop
+
+namespace {
+
+struct ServerJob {
+    tmd_job job;
+    uint64_t id;
+    double t_submit;
+};
+
+struct ServerResult {
+    tmd_job_result r;
+    std::vector<tmd_candidate> recs;
+};
+
+// One resident job: its stream, plan arena, records and counters.
+struct Slot {
+    cudaStream_t stream = nullptr;
+    cudaEvent_t done = nullptr;
+    char* d_arena = nullptr;
+    size_t arena_cap = 0;
+    tmd_candidate* d_cand = nullptr;
+    uint64_t* d_count = nullptr;
+    uint64_t* d_misc = nullptr;   // stats[4], err, queue, plan error
+    char* h_stage = nullptr;
+    size_t stage_cap = 0;
+    bool busy = false;
+    bool all_launched = false;
+    ServerJob sj;
+    double t_start = 0;
+    Plan plan;
+    size_t plan_bytes = 0;
+    size_t off_jobs = 0, off_blocks = 0, off_tasks = 0, off_tables = 0;
+    size_t class_idx = 0;
+    uint64_t class_pos = 0;
+};
+
+}  // namespace
+
+struct tmd_server {
+    tmd_ctx* ctx = nullptr;
+    tmd_server_config cfg;
+    std::thread worker;
+    std::mutex mu;
+    std::condition_variable cv_work, cv_done;
+    std::deque<ServerJob> pending;
+    std::deque<ServerResult> finished;
+    std::vector<Slot> slots;
+    size_t budget_used = 0;
+    uint64_t outstanding = 0;
+    bool stop = false;
+    std::chrono::steady_clock::time_point t0;
+};
+
+namespace {
+
+double server_now(const tmd_server* S) {
+    return std::chrono::duration<double>(std::chrono::steady_clock::now() - S->t0).count();
+}
+
+// plan, upload and table kernel of a job on its slot (worker thread)
+tmd_status slot_start(tmd_server* S, Slot& sl, const ServerJob& sj) {
+    sl.sj = sj;
+    sl.t_start = server_now(S);
+    tmd_status st = build_plan(&sj.job, 1, sl.plan, /*host_tables=*/false);
+    if (st != TMD_OK) return st;
+    Plan& P = sl.plan;
+    const size_t o_blocks = align256(P.jobs.size() * sizeof(DevJob));
+    const size_t o_tasks = align256(o_blocks + P.blocks.size() * sizeof(DevBlock));
+    const size_t o_status = align256(o_tasks + P.tasks.size() * sizeof(DevTask));
+    const size_t o_tables = align256(o_status + P.blocks.size() * sizeof(uint32_t));
+    const size_t total = align256(o_tables + P.table_words * sizeof(uint64_t));
+    if (total > sl.arena_cap) {
+        if (sl.d_arena) CK(cudaFreeAsync(sl.d_arena, sl.stream));
+        sl.d_arena = nullptr;
+        CK(cudaMallocAsync((void**)&sl.d_arena, total, sl.stream));
+        sl.arena_cap = total;
+    }
+    if (o_status > sl.stage_cap) {
+        CK(cudaStreamSynchronize(sl.stream));
+        if (sl.h_stage) CK(cudaFreeHost(sl.h_stage));
+        sl.h_stage = nullptr;
+        CK(cudaHostAlloc((void**)&sl.h_stage, o_status, cudaHostAllocDefault));
+        sl.stage_cap = o_status;
+    }
+    memset(sl.h_stage, 0, o_status);
+    memcpy(sl.h_stage, P.jobs.data(), P.jobs.size() * sizeof(DevJob));
+    memcpy(sl.h_stage + o_blocks, P.blocks.data(), P.blocks.size() * sizeof(DevBlock));
+    memcpy(sl.h_stage + o_tasks, P.tasks.data(), P.tasks.size() * sizeof(DevTask));
+    CK(cudaMemcpyAsync(sl.d_arena, sl.h_stage, o_status, cudaMemcpyHostToDevice, sl.stream));
+    CK(cudaMemsetAsync(sl.d_misc, 0, 64, sl.stream));
+    CK(cudaMemsetAsync(sl.d_count, 0, sizeof(uint64_t), sl.stream));
+    uint32_t* perr = (uint32_t*)(sl.d_misc + ST_COUNT) + 2;
+    CK(launch_block_tables((const DevJob*)sl.d_arena, (const DevBlock*)(sl.d_arena + o_blocks), P.blocks.size(),
+                           (uint64_t*)(sl.d_arena + o_tables), (uint32_t*)(sl.d_arena + o_status), perr,
+                           sl.stream));
+    sl.off_jobs = 0;
+    sl.off_blocks = o_blocks;
+    sl.off_tasks = o_tasks;
+    sl.off_tables = o_tables;
+    sl.plan_bytes = total;
+    sl.class_idx = 0;
+    sl.class_pos = 0;
+    sl.all_launched = false;
+    return TMD_OK;
+}
+
+// launch the next chunk of warp tasks of a slot; records the done event after the last
+tmd_status slot_launch_chunk(tmd_server* S, Slot& sl) {
+    Plan& P = sl.plan;
+    const uint64_t chunk = S->cfg.chunk_tasks;
+    if (sl.class_idx < P.classes.size()) {
+        const ClassRange& cr = P.classes[sl.class_idx];
+        const uint64_t n = std::min<uint64_t>(chunk, cr.count - sl.class_pos);
+        LaunchArgs a;
+        memset(&a, 0, sizeof a);
+        a.jobs = (const DevJob*)sl.d_arena;
+        a.blocks = (const DevBlock*)(sl.d_arena + sl.off_blocks);
+        a.tables = (const uint64_t*)(sl.d_arena + sl.off_tables);
+        a.tasks = (const DevTask*)(sl.d_arena + sl.off_tasks) + cr.first + sl.class_pos;
+        a.n_tasks = n;
+        a.cand = sl.d_cand;
+        a.cap = S->cfg.cand_cap;
+        a.count = sl.d_count;
+        a.stats = sl.d_misc;
+        a.queue_head = (uint32_t*)(sl.d_misc + ST_COUNT) + 1;
+        CK(launch_tasks(true, cr.L, cr.D, a, sl.stream));
+        sl.class_pos += n;
+        if (sl.class_pos >= cr.count) {
+            sl.class_idx++;
+            sl.class_pos = 0;
+        }
+    }
+    if (sl.class_idx >= P.classes.size()) {
+        CK(cudaEventRecord(sl.done, sl.stream));
+        sl.all_launched = true;
+    }
+    return TMD_OK;
+}
+
+void slot_finish(tmd_server* S, Slot& sl, tmd_status st) {
+    ServerResult R;
+    memset(&R.r, 0, sizeof R.r);
+    R.r.id = sl.sj.id;
+    R.r.t_submit = sl.sj.t_submit;
+    R.r.t_start = sl.t_start;
+    if (st == TMD_OK) {
+        uint64_t count = 0;
+        uint32_t err[3] = {0, 0, 0};
+        if (cudaMemcpyAsync(&count, sl.d_count, sizeof count, cudaMemcpyDeviceToHost, sl.stream) != cudaSuccess ||
+            cudaMemcpyAsync(err, sl.d_misc + ST_COUNT, sizeof err, cudaMemcpyDeviceToHost, sl.stream) != cudaSuccess ||
+            cudaStreamSynchronize(sl.stream) != cudaSuccess) {
+            st = TMD_ECUDA;
+        } else if (err[2]) {
+            st = TMD_EUNSUPPORTED;
+        } else {
+            const uint64_t n = std::min<uint64_t>(count, S->cfg.cand_cap);
+            R.recs.resize(n);
+            if (n && (cudaMemcpyAsync(R.recs.data(), sl.d_cand, n * sizeof(tmd_candidate), cudaMemcpyDeviceToHost,
+                                      sl.stream) != cudaSuccess ||
+                      cudaStreamSynchronize(sl.stream) != cudaSuccess)) {
+                st = TMD_ECUDA;
+                R.recs.clear();
+            }
+            std::sort(R.recs.begin(), R.recs.end(), [](const tmd_candidate& a, const tmd_candidate& b) {
+                if (a.arg_index != b.arg_index) return a.arg_index < b.arg_index;
+                return a.value < b.value;
+            });
+            R.r.count = count;
+            if (st == TMD_OK && count > n) st = TMD_EOVERFLOW;
+        }
+    }
+    R.r.status = st;
+    R.r.n_records = R.recs.size();
+    R.r.t_done = server_now(S);
+    {
+        std::lock_guard<std::mutex> lk(S->mu);
+        S->finished.push_back(std::move(R));
+        S->budget_used -= sl.plan_bytes;
+    }
+    S->cv_done.notify_all();
+    sl.busy = false;
+    sl.plan = Plan();
+    sl.plan_bytes = 0;
+}
+
+void server_loop(tmd_server* S) {
+    cudaSetDevice(S->ctx->device);
+    for (;;) {
+        bool progress = false;
+        // completions
+        for (Slot& sl : S->slots) {
+            if (sl.busy && sl.all_launched && cudaEventQuery(sl.done) == cudaSuccess) {
+                slot_finish(S, sl, TMD_OK);
+                progress = true;
+            }
+        }
+        // next chunk of every running job (they overlap across streams)
+        for (Slot& sl : S->slots) {
+            if (sl.busy && !sl.all_launched) {
+                if (slot_launch_chunk(S, sl) != TMD_OK) {
+                    cudaStreamSynchronize(sl.stream);
+                    slot_finish(S, sl, TMD_ECUDA);
+                }
+                progress = true;
+            }
+        }
+        // admission in arrival order while a slot is free and the budget allows
+        for (Slot& sl : S->slots) {
+            if (sl.busy) continue;
+            ServerJob sj;
+            {
+                std::unique_lock<std::mutex> lk(S->mu);
+                if (S->pending.empty()) break;
+                sj = S->pending.front();
+                // plan size estimate: blocks x (record + table) + tasks, checked against the budget
+                uint64_t nb = 0, ns = 0;
+                std::vector<Segment> segs;
+                if (plan_segments(sj.job, segs) == TMD_OK) plan_counts(sj.job, segs, &nb, &ns);
+                const size_t est = (size_t)nb * (sizeof(DevBlock) + 4 + (2 * sj.job.d + 1) * sj.job.limbs * 8) +
+                                   (size_t)(ns / 8 / 32 + nb + 1) * sizeof(DevTask) + 4096;
+                if (S->budget_used > 0 && S->budget_used + est > S->cfg.device_budget) break;
+                S->pending.pop_front();
+                S->budget_used += est;
+                sl.plan_bytes = est;
+            }
+            sl.busy = true;
+            const size_t est = sl.plan_bytes;
+            tmd_status st = slot_start(S, sl, sj);
+            {
+                std::lock_guard<std::mutex> lk(S->mu);
+                S->budget_used += sl.plan_bytes;
+                S->budget_used -= est;
+            }
+            if (st != TMD_OK) {
+                cudaStreamSynchronize(sl.stream);
+                slot_finish(S, sl, st);
+            }
+            progress = true;
+        }
+        bool any_busy = false;
+        for (Slot& sl : S->slots) any_busy |= sl.busy;
+        std::unique_lock<std::mutex> lk(S->mu);
+        if (S->stop && !any_busy) break;
+        if (!progress) {
+            if (!any_busy && S->pending.empty())
+                S->cv_work.wait_for(lk, std::chrono::milliseconds(50));
+            else
+                S->cv_work.wait_for(lk, std::chrono::microseconds(20));
+        }
+        if (S->stop) S->pending.clear();
+    }
+}
+
+}  // namespace
+
+extern "C" {
+
+tmd_status tmd_server_create(tmd_ctx* c, const tmd_server_config* cfg, tmd_server** out) {
+    if (!c || !out) return TMD_EINVAL;
+    *out = nullptr;
+    tmd_server_config k;
+    memset(&k, 0, sizeof k);
+    if (cfg) k = *cfg;
+    if (k.device_budget == 0) k.device_budget = 1ull << 30;
+    if (k.max_inflight == 0) k.max_inflight = 8;
+    if (k.chunk_tasks == 0) k.chunk_tasks = 2048;
+    if (k.cand_cap == 0) k.cand_cap = 65536;
+    if (k.max_inflight > 64) return TMD_EINVAL;
+    CK(cudaSetDevice(c->device));
+    tmd_server* S = new tmd_server();
+    S->ctx = c;
+    S->cfg = k;
+    S->t0 = std::chrono::steady_clock::now();
+    S->slots.resize(k.max_inflight);
+    for (Slot& sl : S->slots) {
+        if (cudaStreamCreateWithFlags(&sl.stream, cudaStreamNonBlocking) != cudaSuccess ||
+            cudaEventCreateWithFlags(&sl.done, cudaEventDisableTiming) != cudaSuccess ||
+            cudaMalloc((void**)&sl.d_cand, k.cand_cap * sizeof(tmd_candidate)) != cudaSuccess ||
+            cudaMalloc((void**)&sl.d_count, sizeof(uint64_t)) != cudaSuccess ||
+            cudaMalloc((void**)&sl.d_misc, 64) != cudaSuccess) {
+            tmd_server_destroy(S);
+            return TMD_ECUDA;
+        }
+    }
+    S->worker = std::thread(server_loop, S);
+    *out = S;
+    return TMD_OK;
+}
+
+tmd_status tmd_server_submit(tmd_server* S, const tmd_job* job, uint64_t id) {
+    if (!S || !job) return TMD_EINVAL;
+    tmd_status st = validate_job(*job);
+    if (st != TMD_OK) return st;
+    {
+        std::lock_guard<std::mutex> lk(S->mu);
+        if (S->stop) return TMD_EINVAL;
+        S->pending.push_back(ServerJob{*job, id, server_now(S)});
+        S->outstanding++;
+    }
+    S->cv_work.notify_one();
+    return TMD_OK;
+}
+
+tmd_status tmd_server_poll(tmd_server* S, tmd_job_result* out, uint32_t cap, uint32_t* n_out,
+                           tmd_candidate* h_records, uint64_t rec_cap, uint64_t* rec_out, int32_t wait_ms) {
+    if (!S || !n_out || (cap && !out) || (rec_cap && !h_records)) return TMD_EINVAL;
+    *n_out = 0;
+    if (rec_out) *rec_out = 0;
+    std::unique_lock<std::mutex> lk(S->mu);
+    if (S->finished.empty() && wait_ms > 0)
+        S->cv_done.wait_for(lk, std::chrono::milliseconds(wait_ms), [&] { return !S->finished.empty(); });
+    uint64_t used = 0;
+    uint32_t n = 0;
+    while (n < cap && !S->finished.empty()) {
+        ServerResult& R = S->finished.front();
+        const uint64_t take = std::min<uint64_t>(R.recs.size(), rec_cap - used);
+        if (take) memcpy(h_records + used, R.recs.data(), take * sizeof(tmd_candidate));
+        used += take;
+        out[n] = R.r;
+        out[n].n_records = take;
+        n++;
+        S->finished.pop_front();
+        S->outstanding--;
+    }
+    *n_out = n;
+    if (rec_out) *rec_out = used;
+    return TMD_OK;
+}
+
+tmd_status tmd_server_pending(tmd_server* S, uint64_t* n) {
+    if (!S || !n) return TMD_EINVAL;
+    std::lock_guard<std::mutex> lk(S->mu);
+    *n = S->outstanding;
+    return TMD_OK;
+}
+
+double tmd_server_clock(tmd_server* S) { return S ? server_now(S) : 0.0; }
+
+tmd_status tmd_server_destroy(tmd_server* S) {
+    if (!S) return TMD_EINVAL;
+    {
+        std::lock_guard<std::mutex> lk(S->mu);
+        S->stop = true;
+    }
+    S->cv_work.notify_all();
+    if (S->worker.joinable()) S->worker.join();
+    cudaSetDevice(S->ctx->device);
+    for (Slot& sl : S->slots) {
+        if (sl.stream) cudaStreamSynchronize(sl.stream);
+        if (sl.d_arena) cudaFreeAsync(sl.d_arena, sl.stream);
+        if (sl.stream) cudaStreamSynchronize(sl.stream);
+        if (sl.d_cand) cudaFree(sl.d_cand);
+        if (sl.d_count) cudaFree(sl.d_count);
+        if (sl.d_misc) cudaFree(sl.d_misc);
+        if (sl.h_stage) cudaFreeHost(sl.h_stage);
+        if (sl.done) cudaEventDestroy(sl.done);
+        if (sl.stream) cudaStreamDestroy(sl.stream);
+    }
+    delete S;
     return TMD_OK;
 }
 

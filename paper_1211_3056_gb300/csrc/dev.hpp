@@ -20,6 +20,10 @@ struct DevJob {
     uint32_t m;
     uint32_t flags;
     uint32_t nu;           // sub-intervals per packet (lane)
+    int32_t func;          // tmd_func
+    int32_t e_in;
+    int32_t p;
+    uint32_t pad;
 };
 
 // One Taylor block.
@@ -31,6 +35,8 @@ struct DevBlock {
     uint64_t table_off;    // offset (in 64-bit words) of the block's 2d+1 table words
     uint32_t job;
     uint32_t n_sub;        // sub-intervals in the block
+    int32_t e_out;         // output exponent on the block
+    uint32_t pad;
 };
 
 // A warp's unit of work: up to 32 consecutive packets of one job.
@@ -39,6 +45,9 @@ struct DevTask {
     uint32_t count;        // packets (1..32)
     uint32_t job;
 };
+
+// Error bits of the context's error word.
+enum { ERR_BAD_LENGTH = 1, ERR_ROUNDING = 2 };
 
 // Counters (device uint64 each) in the order of tmd_stats.
 enum { ST_LINES = 0, ST_FAIL = 1, ST_CAND = 2, ST_HALF = 3, ST_COUNT = 4 };

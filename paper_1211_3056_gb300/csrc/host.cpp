@@ -11,6 +11,7 @@
 #include <cstring>
 
 #include "bigint.hpp"
+#include "coeffs.cuh"
 
 namespace tmd {
 
@@ -476,49 +477,42 @@ int scale_log2(const tmd_job& job, int e_out) {
     return (job.flags & TMD_BP_DIRECTED) ? job.p - e_out : job.p + 1 - e_out;
 }
 
+const CoeffConsts& coeff_consts() {
+    static const CoeffConsts* C = [] {
+        CoeffConsts* c = new CoeffConsts();
+        c->div.r[0] = fx::make_recip(1);
+        for (int n = 1; n <= fx::SMALL_DIV_MAX; n++) c->div.r[n] = fx::make_recip((uint64_t)n);
+        fx::Enc<LN2_LIMBS> e;
+        fx::ln2_enc<LN2_LIMBS>(LN2_BITS, c->div, e);
+        c->ln2_lo = e.lo;
+        c->ln2_hi = e.hi;
+        return c;
+    }();
+    return *C;
+}
+
+CoeffJob coeff_job(const tmd_job& job, int e_out) {
+    CoeffJob J;
+    J.func = job.func;
+    J.e_in = job.e_in;
+    J.p = job.p;
+    J.d = job.d;
+    J.L = (int)job.limbs;
+    J.scale_log2 = scale_log2(job, e_out);
+    J.log2_N = (int)job.log2_N;
+    return J;
+}
+
 tmd_status block_table(const tmd_job& job, const BlockPlan& blk, uint64_t* coeffs, uint64_t* table) {
-    const unsigned L = job.limbs;
-    const int W = 64 * (int)L;
-    const int d = job.d;
-    const uint64_t N = 1ull << job.log2_N;
-    uint64_t M = arg_mantissa(job, blk.start);
-    int sl = scale_log2(job, blk.e_out);
-    Word c[MAX_DEG + 1];
-    // one enclosure of f(X_t) serves every order (exp, 2^x): the order-0
-    // scale is the largest, so its precision covers the others
-    Enc base;
-    const Enc* basep = nullptr;
-    if (job.func != TMD_LOG) {
-        int E0 = W + sl;
-        unsigned P0 = (unsigned)((E0 > 0 ? E0 : 0) + 64) + 8 + 2 * (unsigned)d;
-        base = job.func == TMD_EXP ? exp_fixed(Big(M), (unsigned)(job.p - job.e_in), P0)
-                                   : exp2_fixed(M, (unsigned)(job.p - job.e_in), P0);
-        basep = &base;
-    }
-    for (int k = 0; k <= d; k++) {
-        c[k] = w_zero();
-        int E = W + sl + k * (job.e_in - job.p);
-        if (!scaled_coeff(job.func, M, job.p, job.e_in, k, E, L, c[k].l, basep)) return TMD_EUNSUPPORTED;
-        if (coeffs)
-            for (unsigned l = 0; l < L; l++) coeffs[k * L + l] = c[k].l[l];
-    }
-    if (!table) return TMD_OK;
-    // g0(i) = R(iN) for i = 0..d, g1(i) = R(iN+1) - R(iN) for i = 0..d-1,
-    // then forward differences at 0 (Sect. IV-A hierarchical method)
-    Word g0[MAX_DEG + 1], g1[MAX_DEG];
-    for (int i = 0; i <= d; i++) {
-        Word r0 = horner(c, d, (uint64_t)i * N, L);
-        g0[i] = r0;
-        if (i < d) g1[i] = w_sub(horner(c, d, (uint64_t)i * N + 1, L), r0, L);
-    }
-    for (int lev = 0; lev <= d; lev++) {
-        for (unsigned l = 0; l < L; l++) table[lev * L + l] = g0[0].l[l];
-        for (int i = 0; i + lev < d; i++) g0[i] = w_sub(g0[i + 1], g0[i], L);
-    }
-    for (int lev = 0; lev < d; lev++) {
-        for (unsigned l = 0; l < L; l++) table[(d + 1 + lev) * L + l] = g1[0].l[l];
-        for (int i = 0; i + lev + 1 < d; i++) g1[i] = w_sub(g1[i + 1], g1[i], L);
-    }
+    const CoeffJob J = coeff_job(job, blk.e_out);
+    const uint64_t M = arg_mantissa(job, blk.start);
+    uint64_t c[(MAX_DEG + 1) * MAX_LIMBS];
+    // Ziv: 512-bit words with 64 guard bits, then 768-bit words with 320
+    if (!block_coeffs<8>(J, M, 64, coeff_consts(), c) && !block_coeffs<12>(J, M, 320, coeff_consts(), c))
+        return TMD_EUNSUPPORTED;
+    if (coeffs)
+        for (int i = 0; i < (job.d + 1) * (int)job.limbs; i++) coeffs[i] = c[i];
+    if (table) block_table_words(J, c, table);
     return TMD_OK;
 }
 

@@ -45,4 +45,9 @@ int scale_log2(const tmd_job& job, int e_out);
 tmd_status block_table(const tmd_job& job, const BlockPlan& blk, uint64_t* coeffs,
                        uint64_t* table);
 
+struct CoeffConsts;
+// Constants of the coefficient routine (divisor reciprocals, ln 2), computed
+// once per process.
+const CoeffConsts& coeff_consts();
+
 }  // namespace tmd

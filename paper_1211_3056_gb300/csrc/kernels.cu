@@ -24,6 +24,7 @@
 // quotients (rare: Gauss-Kuzmin tail) take an exact shift-subtract division.
 #include <cuda_runtime.h>
 
+#include "coeffs.cuh"
 #include "dev.hpp"
 
 namespace tmd {
@@ -137,12 +138,58 @@ __device__ __forceinline__ uint32_t sat_madd(uint32_t u, uint32_t k, uint32_t v,
     return min(s, n);
 }
 
+// General half-step by FP32 estimates: k = floor(a/b) (a > b > 0),
+// a' = a mod b, and the reduction of x modulo b whose quotient is at most k.
+__device__ __forceinline__ void half_step_div(uint64_t a, uint64_t b, uint64_t x, uint64_t& a_out,
+                                              uint32_t& k_out, uint64_t& x_out) {
+    const float rbs = scaled_rcp(u64_to_f32_rz(b));
+    bool ok1, ok2;
+    uint32_t k = quot_estimate(u64_to_f32_rz(a), rbs, ok1);
+    uint32_t kx = quot_estimate(u64_to_f32_rz(x), rbs, ok2);
+    uint64_t an = rem_fix(a, b, k);
+    uint64_t xn = rem_fix(x, b, kx);
+    if (!(ok1 && ok2)) {
+        an = divmod_slow(a, b, k);
+        xn = divmod_slow(x, b, kx);
+    }
+    a_out = an;
+    k_out = k;
+    x_out = xn;
+}
+
+// Second half-step by FP32 estimates: k = floor(p/q), p' = p mod q, then
+// d <- (d - p') mod q when d >= p' (the quotient of d - p' < k q is < k).
+__device__ __forceinline__ void second_half_div(uint64_t& p, uint64_t q, uint64_t& d, uint32_t& k) {
+    const float rqs = scaled_rcp(u64_to_f32_rz(q));
+    bool ok1, ok2;
+    uint32_t kk = quot_estimate(u64_to_f32_rz(p), rqs, ok1);
+    uint64_t pn = rem_fix(p, q, kk);
+    bool ge = d >= pn;
+    uint64_t e = ge ? d - pn : 0ull;
+    uint32_t ke = quot_estimate(u64_to_f32_rz(e), rqs, ok2);
+    uint64_t en = rem_fix(e, q, ke);
+    if (!(ok1 && ok2)) {
+        pn = divmod_slow(p, q, kk);
+        ge = d >= pn;
+        en = divmod_slow(ge ? d - pn : 0ull, q, ke);
+    }
+    d = ge ? en : d;
+    p = pn;
+    k = kk;
+}
+
 // Algorithm 4 lower bound of min_{0<=x<n} (B - A x) mod 2^64 on integers
 // scaled by 2^64: p <- A, q <- 2^64, d <- B, u <- 1, v <- 0; returns d when
 // u + v >= n.  Endings of a rational expansion: p = 0 -> d mod q (already
-// reduced), q = 0 -> d.  *hs counts half-steps.  Each half-step converts its
-// new divisor and d to FP32; the dividend's conversion is the divisor's of
-// the half-step before.
+// reduced), q = 0 -> d.  *hs counts half-steps.
+//
+// The dividend of every half-step exceeds its divisor (q mod p < p and
+// p mod q < q), so the partial quotient is k >= 1, and k = 1 exactly when
+// a - b < b.  That case -- 41.5 % of partial quotients (Gauss-Kuzmin) -- is
+// done by subtraction alone: the reduced value is below 2b there, so one
+// compare-and-subtract reduces it (the hybrid subtractive/division scheme of
+// Sect. III-A).  Neighbouring lines share their partial quotients, so the
+// branch is nearly always uniform across a warp.
 __device__ __forceinline__ uint64_t cf_lower_bound(uint64_t B, uint64_t A, uint32_t n, uint32_t* hs) {
     if (A == 0) {
         *hs = 0;
@@ -150,72 +197,49 @@ __device__ __forceinline__ uint64_t cf_lower_bound(uint64_t B, uint64_t A, uint3
     }
     uint64_t p = A, q, d = B;
     uint32_t u = 1, v = 0, h = 1;
-    float pf = u64_to_f32_rz(p), qf;
     // first half-step with q = 2^64: floor(2^64/p) = floor((2^64 - p)/p) + 1,
     // and u = 1 + k * 0 stays 1
     {
-        const float rps = scaled_rcp(pf);
-        bool ok1, ok2;
-        uint32_t k = quot_estimate(u64_to_f32_rz(0ull - p), rps, ok1);
-        uint32_t kd = quot_estimate(u64_to_f32_rz(d), rps, ok2);
-        uint64_t qn = rem_fix(0ull - p, p, k);
-        uint64_t dn = rem_fix(d, p, kd);
-        if (!(ok1 && ok2)) {
-            qn = divmod_slow(0ull - p, p, k);
-            dn = divmod_slow(d, p, kd);
-        }
-        q = qn;
-        d = dn;
+        uint32_t k;
+        half_step_div(0ull - p, p, d, q, k, d);
     }
     if (1u >= n || q == 0) {
         *hs = h;
         return d;
     }
-    qf = u64_to_f32_rz(q);
 #pragma unroll 1
     for (int guard = 0; guard < 64; guard++) {
         // second half: k = floor(p/q); p -= k q; v += k u; if d >= p: d = (d - p) mod q
         {
-            const float rqs = scaled_rcp(qf);
-            bool ok1, ok2;
-            uint32_t k = quot_estimate(pf, rqs, ok1);
-            uint64_t pn = rem_fix(p, q, k);
-            const bool ge = d >= pn;
-            const uint64_t e = ge ? d - pn : 0ull;  // < k q: the quotient is at most k
-            uint32_t ke = quot_estimate(u64_to_f32_rz(e), rqs, ok2);
-            uint64_t en = rem_fix(e, q, ke);
-            if (!(ok1 && ok2)) {
-                pn = divmod_slow(p, q, k);
-                const bool ge2 = d >= pn;
-                en = divmod_slow(ge2 ? d - pn : 0ull, q, ke);
+            const uint64_t r = p - q;
+            if (r < q) {
+                p = r;
+                v = min(v + u, n);
+                d = d >= p ? d - p : d;  // d - p < k q = q
+            } else {
+                uint32_t k;
+                second_half_div(p, q, d, k);
+                v = sat_madd(v, k, u, n);
             }
-            d = (d >= pn) ? en : d;
-            p = pn;
-            v = sat_madd(v, k, u, n);
             h++;
             if (u + v >= n) break;
         }
         if (p == 0) break;  // d was reduced mod q just above
-        pf = u64_to_f32_rz(p);
         // first half: k = floor(q/p); q -= k p; u += k v; d = d mod p
         {
-            const float rps = scaled_rcp(pf);
-            bool ok1, ok2;
-            uint32_t k = quot_estimate(qf, rps, ok1);
-            uint32_t kd = quot_estimate(u64_to_f32_rz(d), rps, ok2);
-            uint64_t qn = rem_fix(q, p, k);
-            uint64_t dn = rem_fix(d, p, kd);
-            if (!(ok1 && ok2)) {
-                qn = divmod_slow(q, p, k);
-                dn = divmod_slow(d, p, kd);
+            const uint64_t r = q - p;
+            if (r < p) {
+                q = r;
+                u = min(u + v, n);
+                d = d >= p ? d - p : d;  // d < q < 2p
+            } else {
+                uint32_t k;
+                half_step_div(q, p, d, q, k, d);
+                u = sat_madd(u, k, v, n);
             }
-            q = qn;
-            d = dn;
-            u = sat_madd(u, k, v, n);
             h++;
             if (u + v >= n || q == 0) break;
         }
-        qf = u64_to_f32_rz(q);
     }
     *hs = h;
     return d;
@@ -594,6 +618,59 @@ __global__ void __launch_bounds__(256) k_lower_bounds(const uint64_t* B, const u
     uint32_t hs = 0;
     lb[s] = cf_lower_bound(B[s], A[s], ln, &hs);
     if (hs_out) hs_out[s] = hs;
+}
+
+// ---------------------------------------------------------- block tables
+// One thread per Taylor block: correctly rounded coefficients of R_t and the
+// 2d+1 step-N difference words (the host path runs the same routine).  Pass
+// 0 works with 512-bit words and 64 guard bits; pass 1 redoes only the blocks
+// left undecided with 768-bit words and 320 guard bits (Ziv); a block still
+// undecided raises ERR_ROUNDING in the error word.
+__constant__ CoeffConsts c_coeff;
+
+__global__ void __launch_bounds__(128) k_block_tables(const DevJob* jobs, const DevBlock* blocks,
+                                                      uint64_t n_blocks, uint64_t* tables,
+                                                      uint32_t* status, int pass, uint32_t* err) {
+    const uint64_t b = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (b >= n_blocks) return;
+    if (pass == 1 && status[b] == 0) return;
+    const DevBlock bk = blocks[b];
+    const DevJob jb = jobs[bk.job];
+    CoeffJob J;
+    J.func = jb.func;
+    J.e_in = jb.e_in;
+    J.p = jb.p;
+    J.d = (int)jb.d;
+    J.L = (int)jb.L;
+    J.scale_log2 = (jb.flags & TMD_BP_DIRECTED) ? jb.p - bk.e_out : jb.p + 1 - bk.e_out;
+    J.log2_N = (int)jb.log2_N;
+    const uint64_t M = (1ull << (jb.p - 1)) + bk.start;
+    uint64_t c[(COEFF_MAX_DEG + 1) * COEFF_MAX_LIMBS];
+    const bool ok = pass == 0 ? block_coeffs<8>(J, M, 64, c_coeff, c)
+                              : block_coeffs<12>(J, M, 320, c_coeff, c);
+    if (ok) {
+        block_table_words(J, c, tables + bk.table_off);
+        status[b] = 0;
+    } else {
+        status[b] = 1;
+        if (pass == 1) atomicOr(err, (uint32_t)ERR_ROUNDING);
+    }
+}
+
+cudaError_t upload_coeff_consts(const CoeffConsts& C) {
+    return cudaMemcpyToSymbol(c_coeff, &C, sizeof C);
+}
+
+cudaError_t launch_block_tables(const DevJob* jobs, const DevBlock* blocks, uint64_t n_blocks,
+                                uint64_t* tables, uint32_t* status, uint32_t* err, cudaStream_t s) {
+    if (n_blocks == 0) return cudaSuccess;
+    const unsigned grid = (unsigned)((n_blocks + 127) / 128);
+    for (int pass = 0; pass < 2; pass++) {
+        k_block_tables<<<grid, 128, 0, s>>>(jobs, blocks, n_blocks, tables, status, pass, err);
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
 }
 
 // --------------------------------------------------------------- launchers

@@ -254,6 +254,8 @@ def main():
     ap.add_argument("--ref-seconds", type=float, default=12.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--m", type=int, default=40)
+    ap.add_argument("--mixed-jobs", type=int, default=64,
+                    help="jobs of the seeded mixed batch for batched vs per-job launches (0 = skip)")
     ap.add_argument("--serve-jobs", type=int, default=400,
                     help="jobs of the seeded serving stream to serve (0 = skip)")
     ap.add_argument("--count-log2", type=int, default=36,
@@ -378,6 +380,32 @@ def main():
                 "half_steps_per_line": stats["half_steps"] / max(1, stats["lines"]),
                 "filter_fail_per_line": stats["filter_fail"] / max(1, stats["lines"])}
 
+    mixed = None
+    if args.mixed_jobs > 0:
+        mjobs = wl.batched_jobs(njobs=args.mixed_jobs)
+        margs = sum(j.count for j in mjobs)
+        dmc, dmn = tmd.alloc_candidates(cap, local_rank)
+        t0 = time.perf_counter()
+        mb = tmd.Batch(ctx, mjobs, dmc, dmn)
+        t_plan = time.perf_counter() - t0
+        singles = [tmd.Batch(ctx, [j], dmc, dmn) for j in mjobs]
+        ms_b = statistics.mean(timed(mb.launch, 10, 3))
+        st_b = mb.stats()
+
+        def per_job():
+            for sb in singles:
+                sb.launch()
+        ms_p = statistics.mean(timed(per_job, 5, 2))
+        mixed = {"jobs": len(mjobs), "args": margs, "lines": st_b["lines"],
+                 "batched": {"value": margs / (ms_b / 1e3), "ms_per_step": ms_b,
+                             "form": "one persistent graph launch over all jobs"},
+                 "plain": {"value": margs / (ms_p / 1e3), "ms_per_step": ms_p,
+                           "form": "one launch per job, plans resident"},
+                 "plan_and_tables_s": t_plan}
+        for sb in singles:
+            sb.close()
+        mb.close()
+
     serving = None
     if rank == 0 and args.serve_jobs > 0:
         sjobs = wl.serving_jobs()[: args.serve_jobs]
@@ -414,7 +442,8 @@ def main():
             "e2e": {"value": total_args / e2e_s, "unit": UNIT, "h2d_bytes_per_step": h2d,
                     "d2h_bytes_per_step": d2h, "ms_per_step": e2e_s * 1e3},
             "gpu_launches": args.steps * 1,
-            "roofline": roofline, "cpu_baseline": cpu, "clocks": clocks, "serving": serving,
+            "roofline": roofline, "cpu_baseline": cpu, "clocks": clocks, "mixed_batch": mixed,
+            "serving": serving,
         }
         print(json.dumps(line), flush=True)
     batch.close()

@@ -113,7 +113,14 @@ uint32_t choose_nu(const tmd_job& job, uint64_t n_sub_block) {
 // Plan every job; with host_tables, also compute all block tables (threads
 // over blocks), otherwise the table kernel computes them on the device.
 tmd_status build_plan(const tmd_job* jobs, uint32_t njobs, Plan& P, bool host_tables = true) {
-    P = Plan();
+    // reuse the vectors' storage of a previous plan (no new pages per call)
+    P.key.clear();
+    P.jobs.clear();
+    P.blocks.clear();
+    P.tables.clear();
+    P.tasks.clear();
+    P.classes.clear();
+    P.total_lines = P.total_args = P.table_words = 0;
     if (njobs == 0 || !jobs) return TMD_EINVAL;
     P.host_tables = host_tables;
     P.key.assign(jobs, jobs + njobs);
@@ -130,6 +137,8 @@ tmd_status build_plan(const tmd_job* jobs, uint32_t njobs, Plan& P, bool host_ta
         uint64_t nb, ns;
         plan_counts(jb, segs[j], &nb, &ns);
         if (P.blocks.size() + nb >= (1ull << 31)) return TMD_EUNSUPPORTED;
+        P.blocks.reserve(P.blocks.size() + nb);
+        P.tasks.reserve(P.tasks.size() + ns / 8 / 32 + nb + 1);
         DevJob dj;
         memset(&dj, 0, sizeof dj);
         dj.line_off = line;
@@ -149,9 +158,24 @@ tmd_status build_plan(const tmd_job* jobs, uint32_t njobs, Plan& P, bool host_ta
         dj.nu = choose_nu(jb, nsub_full);
         const uint64_t words = (uint64_t)(2 * jb.d + 1) * jb.limbs;
         const uint64_t job_pk0 = packet;
+        // blocks of T arguments from each segment start, walked incrementally
+        const uint64_t T = 1ull << jb.log2_T;
+        size_t seg_i = 0;
+        uint64_t seg_pos = segs[j].empty() ? 0 : segs[j][0].j0;
+        uint64_t sub_next = 0;
         for (uint64_t b = 0; b < nb; b++) {
+            while (seg_pos >= segs[j][seg_i].j1) {
+                seg_i++;
+                seg_pos = segs[j][seg_i].j0;
+            }
+            const Segment& sg = segs[j][seg_i];
             BlockPlan bp;
-            plan_block(jb, segs[j], b, &bp);
+            bp.start = seg_pos;
+            bp.length = std::min<uint64_t>(T, sg.j1 - seg_pos);
+            bp.first_sub = sub_next;
+            bp.e_out = sg.e_out;
+            seg_pos += bp.length;
+            sub_next += (bp.length + (1ull << jb.log2_N) - 1) >> jb.log2_N;
             DevBlock db;
             db.start = bp.start;
             db.length = bp.length;
@@ -165,14 +189,20 @@ tmd_status build_plan(const tmd_job* jobs, uint32_t njobs, Plan& P, bool host_ta
             packet += (db.n_sub + dj.nu - 1) / dj.nu;
             toff += words;
             P.blocks.push_back(db);
-            bplan.push_back(bp);
-            bjob.push_back(j);
+            if (host_tables) {
+                bplan.push_back(bp);
+                bjob.push_back(j);
+            }
         }
+        uint32_t bcur = dj.block_off;
         for (uint64_t g = job_pk0; g < packet; g += 32) {
+            while (bcur + 1 < dj.block_off + dj.n_blocks && P.blocks[bcur + 1].packet_off <= g) bcur++;
             DevTask t;
             t.g0 = g;
             t.count = (uint32_t)std::min<uint64_t>(32, packet - g);
             t.job = j;
+            t.block0 = bcur;
+            t.pad = 0;
             P.tasks.push_back(t);
         }
         P.jobs.push_back(dj);
@@ -209,11 +239,19 @@ tmd_status build_plan(const tmd_job* jobs, uint32_t njobs, Plan& P, bool host_ta
         for (auto& t : th) t.join();
     }
     if (bad.load()) return TMD_EUNSUPPORTED;
-    // group tasks by (L, D) so that the plain form launches one kernel per class
-    std::stable_sort(P.tasks.begin(), P.tasks.end(), [&](const DevTask& a, const DevTask& b) {
-        uint32_t ka = P.jobs[a.job].L * 8 + P.jobs[a.job].d, kb = P.jobs[b.job].L * 8 + P.jobs[b.job].d;
-        return ka < kb;
-    });
+    // group tasks by (L, D) so that the plain form launches one kernel per
+    // class (tasks are contiguous per job: reorder whole jobs, stably)
+    bool one_class = true;
+    for (uint32_t j = 1; j < njobs; j++)
+        one_class &= P.jobs[j].L == P.jobs[0].L && P.jobs[j].d == P.jobs[0].d;
+    if (!one_class) {
+        std::vector<DevTask> sorted;
+        sorted.reserve(P.tasks.size());
+        for (uint32_t key = 0; key < 8 * (MAX_LIMBS + 1); key++)
+            for (const DevTask& t : P.tasks)
+                if (P.jobs[t.job].L * 8 + P.jobs[t.job].d == key) sorted.push_back(t);
+        P.tasks.swap(sorted);
+    }
     for (uint64_t i = 0; i < P.tasks.size(); i++) {
         const DevJob& dj = P.jobs[P.tasks[i].job];
         if (P.classes.empty() || P.classes.back().L != dj.L || P.classes.back().D != dj.d)
@@ -367,7 +405,7 @@ tmd_status tmd_destroy(tmd_ctx* c) {
 tmd_status tmd_evict(tmd_ctx* c) {
     if (!c) return TMD_EINVAL;
     c->resident = false;
-    c->plan = Plan();
+    c->plan.key.clear();
     return TMD_OK;
 }
 

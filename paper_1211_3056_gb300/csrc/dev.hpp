@@ -44,6 +44,8 @@ struct DevTask {
     uint64_t g0;           // first global packet index
     uint32_t count;        // packets (1..32)
     uint32_t job;
+    uint32_t block0;       // global index of the block holding packet g0
+    uint32_t pad;
 };
 
 // Error bits of the context's error word.

@@ -352,7 +352,9 @@ __device__ __forceinline__ uint32_t packet_init(Packet<L, D>& P, const DevTask& 
     const int lane = threadIdx.x & 31;
     P.active = (uint32_t)lane < t.count;
     const uint64_t g = t.g0 + (P.active ? (uint64_t)lane : 0ull);
-    uint32_t lo = job.block_off, hi = job.block_off + job.n_blocks - 1;
+    // the task's packets lie in its first block and at most count - 1 more
+    uint32_t lo = t.block0;
+    uint32_t hi = min(t.block0 + t.count - 1, job.block_off + job.n_blocks - 1);
     while (lo < hi) {
         uint32_t mid = (lo + hi + 1) >> 1;
         if (a.blocks[mid].packet_off <= g)

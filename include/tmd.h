@@ -262,7 +262,12 @@ typedef struct {
                                 (1..64; 0 = 8)                                     */
     uint32_t chunk_tasks;    /* warp tasks per launch; a job runs as consecutive
                                 launches over its resident tables (0 = 2048)       */
-    uint64_t cand_cap;       /* records kept per job; the count stays exact (0 = 65536) */
+    uint64_t cand_cap;       /* records kept per admitted group (0 = 65536); a group that
+                                overflows is re-run job by job, so every job's count
+                                stays exact                                         */
+    uint32_t max_batch;      /* jobs admitted together into one slot as one plan
+                                (continuous batching of arrivals; 0 = 32)          */
+    uint32_t reserved;       /* must be 0                                           */
 } tmd_server_config;
 
 typedef struct {
@@ -274,14 +279,15 @@ typedef struct {
     double   t_submit, t_start, t_done;  /* seconds on the server's clock          */
 } tmd_job_result;
 
-/* Start the serving loop on ctx's device: a host thread admits submitted jobs
- * in arrival order whenever a slot is free and the job's plan fits the
- * device budget, plans it (host), uploads it and computes its block tables
- * on the device, and runs the fused search in chunks on the slot's stream,
- * so that jobs admitted while others run overlap on the GPU.  Finished jobs
- * are read back (count and sorted records) and queued for tmd_server_poll.
- * Each job's result is the one tmd_search gives it alone.  The server uses
- * ctx only for its device; ctx must outlive it. */
+/* Start the serving loop on ctx's device: a host thread admits the jobs
+ * waiting in arrival order, up to max_batch at a time, into a free slot
+ * whenever their plans fit the device budget; plans them as one group
+ * (host), uploads the plan and computes its block tables on the device, and
+ * runs the fused search in chunks on the slot's stream, so that groups
+ * admitted while others run overlap on the GPU.  Finished groups are read
+ * back (count and sorted records, split per job) and queued for
+ * tmd_server_poll.  Each job's result is the one tmd_search gives it alone.
+ * The server uses ctx only for its device; ctx must outlive it. */
 tmd_status tmd_server_create(tmd_ctx* ctx, const tmd_server_config* cfg, tmd_server** server);
 
 /* Queue one job under the caller's tag (thread-safe, never blocks on the GPU).

@@ -216,8 +216,8 @@ class Server:
     """A tmd_server: continuous batching of submitted jobs on ctx's device."""
 
     def __init__(self, ctx: Context, device_budget: int = 0, max_inflight: int = 0,
-                 chunk_tasks: int = 0, cand_cap: int = 0):
-        cfg = _lib.tmd_server_config(device_budget, max_inflight, chunk_tasks, cand_cap)
+                 chunk_tasks: int = 0, cand_cap: int = 0, max_batch: int = 0):
+        cfg = _lib.tmd_server_config(device_budget, max_inflight, chunk_tasks, cand_cap, max_batch, 0)
         h = ctypes.c_void_p()
         check(lib().tmd_server_create(ctx.handle, ctypes.byref(cfg), ctypes.byref(h)), "tmd_server_create")
         self.handle = h

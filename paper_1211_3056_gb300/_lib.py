@@ -46,7 +46,8 @@ class tmd_block_info(ctypes.Structure):
 
 class tmd_server_config(ctypes.Structure):
     _fields_ = [("device_budget", ctypes.c_uint64), ("max_inflight", ctypes.c_uint32),
-                ("chunk_tasks", ctypes.c_uint32), ("cand_cap", ctypes.c_uint64)]
+                ("chunk_tasks", ctypes.c_uint32), ("cand_cap", ctypes.c_uint64),
+                ("max_batch", ctypes.c_uint32), ("reserved", ctypes.c_uint32)]
 
 
 class tmd_job_result(ctypes.Structure):

@@ -19,8 +19,8 @@
 
 namespace tmd {
 cudaError_t launch_tasks(bool fused, uint32_t L, uint32_t D, const LaunchArgs& a, cudaStream_t s);
-cudaError_t launch_persistent(const LaunchArgs& a, int ctas, cudaStream_t s);
-cudaError_t persistent_occupancy(int* blocks_per_sm);
+cudaError_t launch_persistent(uint32_t L, uint32_t D, const LaunchArgs& a, int ctas, cudaStream_t s);
+cudaError_t persistent_occupancy(uint32_t L, uint32_t D, int* blocks_per_sm);
 cudaError_t upload_coeff_consts(const CoeffConsts& C);
 cudaError_t launch_block_tables(const DevJob* jobs, const DevBlock* blocks, uint64_t n_blocks,
                                 uint64_t* tables, uint32_t* status, uint32_t* err, cudaStream_t s);
@@ -595,6 +595,9 @@ tmd_status tmd_stats_read(tmd_ctx* c, tmd_stats* out, void* stream) {
 // ---------------------------------------------------------------- batches
 }  // extern "C"
 
+// batch counters: stats[4] | error | unused | plan error | pad | queue heads (one per class)
+enum { BATCH_MISC_BYTES = 128, BATCH_QUEUE_OFF = 64 };
+
 struct tmd_batch {
     tmd_ctx* ctx = nullptr;
     Plan plan;
@@ -653,8 +656,8 @@ tmd_status tmd_batch_create(tmd_ctx* c, const tmd_job* jobs, uint32_t njobs, tmd
     uint32_t* plan_err = nullptr;
     uint32_t perr = 0;
     if (cudaMalloc((void**)&b->d_arena, total) != cudaSuccess ||
-        cudaMalloc((void**)&b->d_misc, 64) != cudaSuccess ||
-        cudaMemsetAsync(b->d_misc, 0, 64, s) != cudaSuccess ||
+        cudaMalloc((void**)&b->d_misc, BATCH_MISC_BYTES) != cudaSuccess ||
+        cudaMemsetAsync(b->d_misc, 0, BATCH_MISC_BYTES, s) != cudaSuccess ||
         cudaMemcpyAsync(b->d_arena, host.data(), o_status, cudaMemcpyHostToDevice, s) != cudaSuccess) {
         batch_free(b);
         return TMD_ECUDA;
@@ -677,31 +680,43 @@ tmd_status tmd_batch_create(tmd_ctx* c, const tmd_job* jobs, uint32_t njobs, tmd
     b->off_blocks = o_blocks;
     b->off_tables = o_tables;
     b->off_tasks = o_tasks;
-    // persistent grid: every SM filled to its occupancy, no more CTAs than tasks need
-    int per_sm = 0;
-    if (persistent_occupancy(&per_sm) != cudaSuccess || per_sm < 1) per_sm = 1;
-    uint64_t want = (P.tasks.size() + 7) / 8;
-    int ctas = (int)std::min<uint64_t>((uint64_t)c->sms * (uint64_t)per_sm, std::max<uint64_t>(want, 1));
+    // one persistent launch per (limbs, degree) class, each over its own task
+    // range with its own queue head; grid = every SM filled to the kernel's
+    // occupancy, no more CTAs than the class's tasks need
     LaunchArgs a;
     memset(&a, 0, sizeof a);
     a.jobs = (const DevJob*)b->d_arena;
     a.blocks = (const DevBlock*)(b->d_arena + o_blocks);
     a.tables = (const uint64_t*)(b->d_arena + o_tables);
-    a.tasks = (const DevTask*)(b->d_arena + o_tasks);
-    a.n_tasks = P.tasks.size();
     a.cand = d_cand;
     a.cap = cand_cap;
     a.count = d_count;
     a.stats = b->d_misc;
-    a.queue_head = (uint32_t*)(b->d_misc + ST_COUNT) + 1;
     if (cudaStreamCreateWithFlags(&b->cap_stream, cudaStreamNonBlocking) != cudaSuccess ||
         cudaStreamBeginCapture(b->cap_stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
         batch_free(b);
         return TMD_ECUDA;
     }
-    cudaMemsetAsync(b->d_misc, 0, sizeof(uint64_t) * (ST_COUNT + 1), b->cap_stream);
+    cudaMemsetAsync(b->d_misc, 0, BATCH_MISC_BYTES, b->cap_stream);
     cudaMemsetAsync(d_count, 0, sizeof(uint64_t), b->cap_stream);
-    launch_persistent(a, ctas, b->cap_stream);
+    static_assert(BATCH_QUEUE_OFF + 4 * 3 * 4 <= BATCH_MISC_BYTES, "one queue head per class");
+    if (P.classes.size() > 12) {
+        cudaStreamEndCapture(b->cap_stream, &b->graph);
+        batch_free(b);
+        return TMD_EUNSUPPORTED;
+    }
+    for (size_t ci = 0; ci < P.classes.size(); ci++) {
+        const ClassRange& cr = P.classes[ci];
+        int per_sm = 0;
+        if (persistent_occupancy(cr.L, cr.D, &per_sm) != cudaSuccess || per_sm < 1) per_sm = 1;
+        const uint64_t want = (cr.count + 7) / 8;
+        const int ctas = (int)std::min<uint64_t>((uint64_t)c->sms * (uint64_t)per_sm, std::max<uint64_t>(want, 1));
+        LaunchArgs ac = a;
+        ac.tasks = (const DevTask*)(b->d_arena + o_tasks) + cr.first;
+        ac.n_tasks = cr.count;
+        ac.queue_head = (uint32_t*)((char*)b->d_misc + BATCH_QUEUE_OFF) + ci;  // ci < 12: inside the 128 B
+        launch_persistent(cr.L, cr.D, ac, ctas, b->cap_stream);
+    }
     if (cudaStreamEndCapture(b->cap_stream, &b->graph) != cudaSuccess ||
         cudaGraphInstantiate(&b->exec, b->graph, 0) != cudaSuccess) {
         batch_free(b);
@@ -751,6 +766,8 @@ struct ServerJob {
     tmd_job job;
     uint64_t id;
     double t_submit;
+    size_t est;      // plan bytes estimate (for the device budget)
+    bool solo;       // re-run alone after its group overflowed the records
 };
 
 struct ServerResult {
@@ -758,24 +775,28 @@ struct ServerResult {
     std::vector<tmd_candidate> recs;
 };
 
-// One resident job: its stream, plan arena, records and counters.
+// Slot meta block on the device: stats[4] | error | queue head | plan error | pad | count.
+enum { META_BYTES = 128, META_COUNT_OFF = 64 };
+
+// One resident group of jobs: its stream, plan arena, records and counters.
 struct Slot {
     cudaStream_t stream = nullptr;
     cudaEvent_t done = nullptr;
     char* d_arena = nullptr;
     size_t arena_cap = 0;
     tmd_candidate* d_cand = nullptr;
-    uint64_t* d_count = nullptr;
-    uint64_t* d_misc = nullptr;   // stats[4], err, queue, plan error
+    char* d_meta = nullptr;
     char* h_stage = nullptr;
     size_t stage_cap = 0;
+    char* h_meta = nullptr;       // pinned copy of the meta block
     bool busy = false;
     bool all_launched = false;
-    ServerJob sj;
+    std::vector<ServerJob> sjs;
+    std::vector<tmd_job> jobs;
     double t_start = 0;
     Plan plan;
     size_t plan_bytes = 0;
-    size_t off_jobs = 0, off_blocks = 0, off_tasks = 0, off_tables = 0;
+    size_t off_blocks = 0, off_tasks = 0, off_tables = 0;
     size_t class_idx = 0;
     uint64_t class_pos = 0;
 };
@@ -803,11 +824,20 @@ double server_now(const tmd_server* S) {
     return std::chrono::duration<double>(std::chrono::steady_clock::now() - S->t0).count();
 }
 
-// plan, upload and table kernel of a job on its slot (worker thread)
-tmd_status slot_start(tmd_server* S, Slot& sl, const ServerJob& sj) {
-    sl.sj = sj;
+size_t plan_estimate(const tmd_job& job) {
+    uint64_t nb = 0, ns = 0;
+    std::vector<Segment> segs;
+    if (plan_segments(job, segs) == TMD_OK) plan_counts(job, segs, &nb, &ns);
+    return (size_t)nb * (sizeof(DevBlock) + 4 + (size_t)(2 * job.d + 1) * job.limbs * 8) +
+           (size_t)(ns / 8 / 32 + nb + 1) * sizeof(DevTask) + 4096;
+}
+
+// plan, upload (plan records and zeroed counters) and table kernel of a group
+tmd_status slot_start(tmd_server* S, Slot& sl) {
     sl.t_start = server_now(S);
-    tmd_status st = build_plan(&sj.job, 1, sl.plan, /*host_tables=*/false);
+    sl.jobs.clear();
+    for (const ServerJob& sj : sl.sjs) sl.jobs.push_back(sj.job);
+    tmd_status st = build_plan(sl.jobs.data(), (uint32_t)sl.jobs.size(), sl.plan, /*host_tables=*/false);
     if (st != TMD_OK) return st;
     Plan& P = sl.plan;
     const size_t o_blocks = align256(P.jobs.size() * sizeof(DevJob));
@@ -833,13 +863,11 @@ tmd_status slot_start(tmd_server* S, Slot& sl, const ServerJob& sj) {
     memcpy(sl.h_stage + o_blocks, P.blocks.data(), P.blocks.size() * sizeof(DevBlock));
     memcpy(sl.h_stage + o_tasks, P.tasks.data(), P.tasks.size() * sizeof(DevTask));
     CK(cudaMemcpyAsync(sl.d_arena, sl.h_stage, o_status, cudaMemcpyHostToDevice, sl.stream));
-    CK(cudaMemsetAsync(sl.d_misc, 0, 64, sl.stream));
-    CK(cudaMemsetAsync(sl.d_count, 0, sizeof(uint64_t), sl.stream));
-    uint32_t* perr = (uint32_t*)(sl.d_misc + ST_COUNT) + 2;
+    CK(cudaMemsetAsync(sl.d_meta, 0, META_BYTES, sl.stream));
+    uint32_t* perr = (uint32_t*)(sl.d_meta + sizeof(uint64_t) * ST_COUNT) + 2;
     CK(launch_block_tables((const DevJob*)sl.d_arena, (const DevBlock*)(sl.d_arena + o_blocks), P.blocks.size(),
                            (uint64_t*)(sl.d_arena + o_tables), (uint32_t*)(sl.d_arena + o_status), perr,
                            sl.stream));
-    sl.off_jobs = 0;
     sl.off_blocks = o_blocks;
     sl.off_tasks = o_tasks;
     sl.off_tables = o_tables;
@@ -850,7 +878,8 @@ tmd_status slot_start(tmd_server* S, Slot& sl, const ServerJob& sj) {
     return TMD_OK;
 }
 
-// launch the next chunk of warp tasks of a slot; records the done event after the last
+// launch the next chunk of warp tasks of a slot; after the last one, queue
+// the read-back of the meta block and record the done event
 tmd_status slot_launch_chunk(tmd_server* S, Slot& sl) {
     Plan& P = sl.plan;
     const uint64_t chunk = S->cfg.chunk_tasks;
@@ -866,9 +895,9 @@ tmd_status slot_launch_chunk(tmd_server* S, Slot& sl) {
         a.n_tasks = n;
         a.cand = sl.d_cand;
         a.cap = S->cfg.cand_cap;
-        a.count = sl.d_count;
-        a.stats = sl.d_misc;
-        a.queue_head = (uint32_t*)(sl.d_misc + ST_COUNT) + 1;
+        a.count = (uint64_t*)(sl.d_meta + META_COUNT_OFF);
+        a.stats = (uint64_t*)sl.d_meta;
+        a.queue_head = (uint32_t*)(sl.d_meta + sizeof(uint64_t) * ST_COUNT) + 1;
         CK(launch_tasks(true, cr.L, cr.D, a, sl.stream));
         sl.class_pos += n;
         if (sl.class_pos >= cr.count) {
@@ -877,70 +906,95 @@ tmd_status slot_launch_chunk(tmd_server* S, Slot& sl) {
         }
     }
     if (sl.class_idx >= P.classes.size()) {
+        CK(cudaMemcpyAsync(sl.h_meta, sl.d_meta, META_BYTES, cudaMemcpyDeviceToHost, sl.stream));
         CK(cudaEventRecord(sl.done, sl.stream));
         sl.all_launched = true;
     }
     return TMD_OK;
 }
 
+void slot_release(tmd_server* S, Slot& sl) {
+    {
+        std::lock_guard<std::mutex> lk(S->mu);
+        S->budget_used -= sl.plan_bytes;
+    }
+    sl.busy = false;
+    sl.sjs.clear();
+    sl.plan_bytes = 0;
+}
+
+// read back a finished group and split it into per-job results; a group
+// whose records overflowed goes back to the queue front job by job
 void slot_finish(tmd_server* S, Slot& sl, tmd_status st) {
-    ServerResult R;
-    memset(&R.r, 0, sizeof R.r);
-    R.r.id = sl.sj.id;
-    R.r.t_submit = sl.sj.t_submit;
-    R.r.t_start = sl.t_start;
+    const double t_done = server_now(S);
+    uint64_t count = 0;
+    std::vector<tmd_candidate> recs;
     if (st == TMD_OK) {
-        uint64_t count = 0;
-        uint32_t err[3] = {0, 0, 0};
-        if (cudaMemcpyAsync(&count, sl.d_count, sizeof count, cudaMemcpyDeviceToHost, sl.stream) != cudaSuccess ||
-            cudaMemcpyAsync(err, sl.d_misc + ST_COUNT, sizeof err, cudaMemcpyDeviceToHost, sl.stream) != cudaSuccess ||
-            cudaStreamSynchronize(sl.stream) != cudaSuccess) {
-            st = TMD_ECUDA;
-        } else if (err[2]) {
+        const uint32_t* err = (const uint32_t*)(sl.h_meta + sizeof(uint64_t) * ST_COUNT);
+        count = *(const uint64_t*)(sl.h_meta + META_COUNT_OFF);
+        if (err[2]) {
             st = TMD_EUNSUPPORTED;
         } else {
             const uint64_t n = std::min<uint64_t>(count, S->cfg.cand_cap);
-            R.recs.resize(n);
-            if (n && (cudaMemcpyAsync(R.recs.data(), sl.d_cand, n * sizeof(tmd_candidate), cudaMemcpyDeviceToHost,
+            recs.resize(n);
+            if (n && (cudaMemcpyAsync(recs.data(), sl.d_cand, n * sizeof(tmd_candidate), cudaMemcpyDeviceToHost,
                                       sl.stream) != cudaSuccess ||
-                      cudaStreamSynchronize(sl.stream) != cudaSuccess)) {
+                      cudaStreamSynchronize(sl.stream) != cudaSuccess))
                 st = TMD_ECUDA;
-                R.recs.clear();
-            }
-            std::sort(R.recs.begin(), R.recs.end(), [](const tmd_candidate& a, const tmd_candidate& b) {
-                if (a.arg_index != b.arg_index) return a.arg_index < b.arg_index;
-                return a.value < b.value;
-            });
-            R.r.count = count;
-            if (st == TMD_OK && count > n) st = TMD_EOVERFLOW;
         }
     }
-    R.r.status = st;
-    R.r.n_records = R.recs.size();
-    R.r.t_done = server_now(S);
+    const bool overflow = st == TMD_OK && count > S->cfg.cand_cap;
+    if (overflow && sl.sjs.size() > 1) {
+        std::vector<ServerJob> again = sl.sjs;
+        slot_release(S, sl);
+        std::lock_guard<std::mutex> lk(S->mu);
+        for (size_t k = again.size(); k-- > 0;) {
+            again[k].solo = true;
+            S->pending.push_front(again[k]);
+        }
+        return;
+    }
+    std::sort(recs.begin(), recs.end(), [](const tmd_candidate& a, const tmd_candidate& b) {
+        if (a.job != b.job) return a.job < b.job;
+        if (a.arg_index != b.arg_index) return a.arg_index < b.arg_index;
+        return a.value < b.value;
+    });
+    std::vector<ServerResult> out(sl.sjs.size());
+    size_t pos = 0;
+    for (size_t k = 0; k < sl.sjs.size(); k++) {
+        ServerResult& R = out[k];
+        memset(&R.r, 0, sizeof R.r);
+        R.r.id = sl.sjs[k].id;
+        R.r.t_submit = sl.sjs[k].t_submit;
+        R.r.t_start = sl.t_start;
+        R.r.t_done = t_done;
+        while (pos < recs.size() && recs[pos].job == k) {
+            tmd_candidate c = recs[pos++];
+            c.job = 0;  // as the job's own run reports it
+            R.recs.push_back(c);
+        }
+        R.r.count = overflow ? count : R.recs.size();
+        R.r.n_records = R.recs.size();
+        R.r.status = st == TMD_OK ? (overflow ? TMD_EOVERFLOW : TMD_OK) : st;
+    }
+    slot_release(S, sl);
     {
         std::lock_guard<std::mutex> lk(S->mu);
-        S->finished.push_back(std::move(R));
-        S->budget_used -= sl.plan_bytes;
+        for (ServerResult& R : out) S->finished.push_back(std::move(R));
     }
     S->cv_done.notify_all();
-    sl.busy = false;
-    sl.plan = Plan();
-    sl.plan_bytes = 0;
 }
 
 void server_loop(tmd_server* S) {
     cudaSetDevice(S->ctx->device);
     for (;;) {
         bool progress = false;
-        // completions
         for (Slot& sl : S->slots) {
             if (sl.busy && sl.all_launched && cudaEventQuery(sl.done) == cudaSuccess) {
                 slot_finish(S, sl, TMD_OK);
                 progress = true;
             }
         }
-        // next chunk of every running job (they overlap across streams)
         for (Slot& sl : S->slots) {
             if (sl.busy && !sl.all_launched) {
                 if (slot_launch_chunk(S, sl) != TMD_OK) {
@@ -950,28 +1004,31 @@ void server_loop(tmd_server* S) {
                 progress = true;
             }
         }
-        // admission in arrival order while a slot is free and the budget allows
+        // admission: the oldest waiting jobs, up to max_batch, while they fit
         for (Slot& sl : S->slots) {
             if (sl.busy) continue;
-            ServerJob sj;
+            size_t take = 0;
             {
                 std::unique_lock<std::mutex> lk(S->mu);
                 if (S->pending.empty()) break;
-                sj = S->pending.front();
-                // plan size estimate: blocks x (record + table) + tasks, checked against the budget
-                uint64_t nb = 0, ns = 0;
-                std::vector<Segment> segs;
-                if (plan_segments(sj.job, segs) == TMD_OK) plan_counts(sj.job, segs, &nb, &ns);
-                const size_t est = (size_t)nb * (sizeof(DevBlock) + 4 + (2 * sj.job.d + 1) * sj.job.limbs * 8) +
-                                   (size_t)(ns / 8 / 32 + nb + 1) * sizeof(DevTask) + 4096;
-                if (S->budget_used > 0 && S->budget_used + est > S->cfg.device_budget) break;
-                S->pending.pop_front();
-                S->budget_used += est;
-                sl.plan_bytes = est;
+                size_t bytes = 0;
+                while (take < S->pending.size() && take < S->cfg.max_batch) {
+                    const ServerJob& sj = S->pending[take];
+                    if (take > 0 && (sj.solo || S->pending[0].solo)) break;
+                    if ((S->budget_used > 0 || take > 0) && S->budget_used + bytes + sj.est > S->cfg.device_budget)
+                        break;
+                    bytes += sj.est;
+                    take++;
+                }
+                if (take == 0) break;
+                sl.sjs.assign(S->pending.begin(), S->pending.begin() + (long)take);
+                S->pending.erase(S->pending.begin(), S->pending.begin() + (long)take);
+                S->budget_used += bytes;
+                sl.plan_bytes = bytes;
             }
             sl.busy = true;
             const size_t est = sl.plan_bytes;
-            tmd_status st = slot_start(S, sl, sj);
+            tmd_status st = slot_start(S, sl);
             {
                 std::lock_guard<std::mutex> lk(S->mu);
                 S->budget_used += sl.plan_bytes;
@@ -1007,10 +1064,12 @@ tmd_status tmd_server_create(tmd_ctx* c, const tmd_server_config* cfg, tmd_serve
     tmd_server_config k;
     memset(&k, 0, sizeof k);
     if (cfg) k = *cfg;
+    if (k.reserved != 0) return TMD_EINVAL;
     if (k.device_budget == 0) k.device_budget = 1ull << 30;
     if (k.max_inflight == 0) k.max_inflight = 8;
     if (k.chunk_tasks == 0) k.chunk_tasks = 2048;
     if (k.cand_cap == 0) k.cand_cap = 65536;
+    if (k.max_batch == 0) k.max_batch = 32;
     if (k.max_inflight > 64) return TMD_EINVAL;
     CK(cudaSetDevice(c->device));
     tmd_server* S = new tmd_server();
@@ -1022,8 +1081,8 @@ tmd_status tmd_server_create(tmd_ctx* c, const tmd_server_config* cfg, tmd_serve
         if (cudaStreamCreateWithFlags(&sl.stream, cudaStreamNonBlocking) != cudaSuccess ||
             cudaEventCreateWithFlags(&sl.done, cudaEventDisableTiming) != cudaSuccess ||
             cudaMalloc((void**)&sl.d_cand, k.cand_cap * sizeof(tmd_candidate)) != cudaSuccess ||
-            cudaMalloc((void**)&sl.d_count, sizeof(uint64_t)) != cudaSuccess ||
-            cudaMalloc((void**)&sl.d_misc, 64) != cudaSuccess) {
+            cudaMalloc((void**)&sl.d_meta, META_BYTES) != cudaSuccess ||
+            cudaHostAlloc((void**)&sl.h_meta, META_BYTES, cudaHostAllocDefault) != cudaSuccess) {
             tmd_server_destroy(S);
             return TMD_ECUDA;
         }
@@ -1037,10 +1096,11 @@ tmd_status tmd_server_submit(tmd_server* S, const tmd_job* job, uint64_t id) {
     if (!S || !job) return TMD_EINVAL;
     tmd_status st = validate_job(*job);
     if (st != TMD_OK) return st;
+    const size_t est = plan_estimate(*job);
     {
         std::lock_guard<std::mutex> lk(S->mu);
         if (S->stop) return TMD_EINVAL;
-        S->pending.push_back(ServerJob{*job, id, server_now(S)});
+        S->pending.push_back(ServerJob{*job, id, server_now(S), est, false});
         S->outstanding++;
     }
     S->cv_work.notify_one();
@@ -1096,9 +1156,9 @@ tmd_status tmd_server_destroy(tmd_server* S) {
         if (sl.d_arena) cudaFreeAsync(sl.d_arena, sl.stream);
         if (sl.stream) cudaStreamSynchronize(sl.stream);
         if (sl.d_cand) cudaFree(sl.d_cand);
-        if (sl.d_count) cudaFree(sl.d_count);
-        if (sl.d_misc) cudaFree(sl.d_misc);
+        if (sl.d_meta) cudaFree(sl.d_meta);
         if (sl.h_stage) cudaFreeHost(sl.h_stage);
+        if (sl.h_meta) cudaFreeHost(sl.h_meta);
         if (sl.done) cudaEventDestroy(sl.done);
         if (sl.stream) cudaStreamDestroy(sl.stream);
     }

@@ -404,8 +404,69 @@ tmd_status validate_job(const tmd_job& job) {
     return TMD_OK;
 }
 
+// e(f(X)) from a 128-bit enclosure of f(X) (fixed-size routines, no heap);
+// the rare undecided case (f(X) within 2^-100 of a power of two) falls back
+// to wider Big enclosures.
+bool output_exponent_fx(const tmd_job& job, uint64_t M, int* e) {
+    const CoeffConsts& C = coeff_consts();
+    const unsigned P = 128, q = (unsigned)(job.p - job.e_in);
+    fx::Enc<6> f;
+    if (job.func == TMD_EXP) {
+        if (!fx::exp_small<6>(M, q, P, C.div, f)) return false;
+    } else if (job.func == TMD_EXP2) {
+        if (q == 0 || (M & ((1ull << q) - 1)) == 0) {
+            fx::set_pow2(f.lo, P + (unsigned)(q >= 64 ? 0 : (M >> q)));
+            f.hi = f.lo;
+        } else {
+            fx::U<6> llo, lhi;
+            fx::U<LN2_LIMBS> a = C.ln2_lo, b = C.ln2_hi;
+            fx::shr(a, LN2_BITS - (P + 16));
+            fx::shr(b, LN2_BITS - (P + 16));
+            fx::add_u64(b, 1);
+            for (int i = 0; i < 6; i++) {
+                llo.w[i] = a.w[i];
+                lhi.w[i] = b.w[i];
+            }
+            fx::mul_u64(llo, M);
+            fx::shr(llo, q);
+            fx::mul_u64(lhi, M);
+            fx::shr(lhi, q);
+            fx::add_u64(lhi, 1);
+            const uint64_t Xc = (uint64_t)1 << (job.e_in > 0 ? job.e_in : 0);
+            uint64_t elo, ehi;
+            fx::U<6> vlo, vhi;
+            if (!fx::exp_big<6>(llo, P + 16, Xc, C.div, vlo, elo)) return false;
+            if (!fx::exp_big<6>(lhi, P + 16, Xc, C.div, vhi, ehi)) return false;
+            fx::add_u64(vhi, ehi);
+            fx::shr(vlo, 16);
+            fx::shr(vhi, 16);
+            fx::add_u64(vhi, 1);
+            f.lo = vlo;
+            f.hi = vhi;
+        }
+    } else {
+        fx::Enc<6> ln2;
+        fx::U<LN2_LIMBS> a = C.ln2_lo, b = C.ln2_hi;
+        fx::shr(a, LN2_BITS - P);
+        fx::shr(b, LN2_BITS - P);
+        fx::add_u64(b, 1);
+        for (int i = 0; i < 6; i++) {
+            ln2.lo.w[i] = a.w[i];
+            ln2.hi.w[i] = b.w[i];
+        }
+        if (!fx::log_enc<6>(M, job.p, job.e_in, P, ln2, C.div, f)) return false;
+    }
+    const int elo = (int)fx::bit_length(f.lo) - (int)P;
+    const int ehi = (int)fx::bit_length(f.hi) - (int)P;
+    if (elo != ehi) return false;
+    *e = elo;
+    return true;
+}
+
 int output_exponent(const tmd_job& job, uint64_t j) {
     uint64_t M = arg_mantissa(job, j);
+    int e;
+    if (output_exponent_fx(job, M, &e)) return e;
     for (unsigned P = 64; P < 64 * 20; P += 64) {
         Enc f = f_enclosure(job, M, P);
         int elo = (int)f.lo.bits() - (int)P;

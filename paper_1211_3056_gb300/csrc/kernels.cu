@@ -496,9 +496,13 @@ __device__ __forceinline__ void generate_task(const DevTask& t, const LaunchArgs
 }
 
 // ------------------------------------------------------------------- kernels
+// The plain form runs 4-warp CTAs (finer-grained scheduling of the last
+// wave than 8-warp CTAs).
+constexpr int FUSED_WARPS_PER_CTA = 4;
+
 template <int L, int D>
-__global__ void __launch_bounds__(256) k_fused(LaunchArgs a) {
-    __shared__ LineStage stage[WARPS_PER_CTA];
+__global__ void __launch_bounds__(128) k_fused(LaunchArgs a) {
+    __shared__ LineStage stage[FUSED_WARPS_PER_CTA];
     const uint64_t w = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     if (w >= a.n_tasks) return;  // whole warp
     uint32_t sl = 0, sf = 0, sh = 0;
@@ -515,9 +519,11 @@ __global__ void __launch_bounds__(256) k_generate(LaunchArgs a) {
     generate_task<L, D>(t, a);
 }
 
-// Persistent form: a grid of resident CTAs; each warp takes the next task
-// from a device counter until the list is exhausted (no waiting on other
-// warps: a single atomicAdd per task).
+// Persistent form: a grid of resident CTAs per (limbs, degree) class; each
+// warp takes the next task of its class from a device counter until the
+// class's list is exhausted (no waiting on other warps: one atomicAdd per
+// task).
+template <int L, int D>
 __global__ void __launch_bounds__(256) k_persistent(LaunchArgs a) {
     __shared__ LineStage stage[WARPS_PER_CTA];
     LineStage& stg = stage[threadIdx.x >> 5];
@@ -529,22 +535,7 @@ __global__ void __launch_bounds__(256) k_persistent(LaunchArgs a) {
         t = __shfl_sync(FULLMASK, t, 0);
         if ((uint64_t)t >= a.n_tasks) break;
         const DevTask task = a.tasks[t];
-        const uint32_t key = a.jobs[task.job].L * 8u + a.jobs[task.job].d;
-        switch (key) {
-            case 9: fused_task<1, 1>(task, a, stg, sl, sf, sh); break;
-            case 10: fused_task<1, 2>(task, a, stg, sl, sf, sh); break;
-            case 11: fused_task<1, 3>(task, a, stg, sl, sf, sh); break;
-            case 12: fused_task<1, 4>(task, a, stg, sl, sf, sh); break;
-            case 17: fused_task<2, 1>(task, a, stg, sl, sf, sh); break;
-            case 18: fused_task<2, 2>(task, a, stg, sl, sf, sh); break;
-            case 19: fused_task<2, 3>(task, a, stg, sl, sf, sh); break;
-            case 20: fused_task<2, 4>(task, a, stg, sl, sf, sh); break;
-            case 25: fused_task<3, 1>(task, a, stg, sl, sf, sh); break;
-            case 26: fused_task<3, 2>(task, a, stg, sl, sf, sh); break;
-            case 27: fused_task<3, 3>(task, a, stg, sl, sf, sh); break;
-            case 28: fused_task<3, 4>(task, a, stg, sl, sf, sh); break;
-            default: break;
-        }
+        fused_task<L, D>(task, a, stg, sl, sf, sh);
     }
     flush_stats(a.stats, sl, sf, sh);
 }
@@ -696,20 +687,28 @@ static TaskKernel generate_kernel(uint32_t L, uint32_t D) {
 
 cudaError_t launch_tasks(bool fused, uint32_t L, uint32_t D, const LaunchArgs& a, cudaStream_t s) {
     if (a.n_tasks == 0) return cudaSuccess;
-    const uint64_t warps_per_cta = 8;
+    const uint64_t warps_per_cta = fused ? FUSED_WARPS_PER_CTA : 8;
     const uint64_t ctas = (a.n_tasks + warps_per_cta - 1) / warps_per_cta;
     TaskKernel k = fused ? fused_kernel(L, D) : generate_kernel(L, D);
-    k<<<(unsigned)ctas, 256, 0, s>>>(a);
+    k<<<(unsigned)ctas, (unsigned)(32 * warps_per_cta), 0, s>>>(a);
     return cudaGetLastError();
 }
 
-cudaError_t launch_persistent(const LaunchArgs& a, int ctas, cudaStream_t s) {
-    k_persistent<<<ctas, 256, 0, s>>>(a);
+static TaskKernel persistent_kernel(uint32_t L, uint32_t D) {
+    static const TaskKernel tab[3][4] = {
+        {k_persistent<1, 1>, k_persistent<1, 2>, k_persistent<1, 3>, k_persistent<1, 4>},
+        {k_persistent<2, 1>, k_persistent<2, 2>, k_persistent<2, 3>, k_persistent<2, 4>},
+        {k_persistent<3, 1>, k_persistent<3, 2>, k_persistent<3, 3>, k_persistent<3, 4>}};
+    return tab[L - 1][D - 1];
+}
+
+cudaError_t launch_persistent(uint32_t L, uint32_t D, const LaunchArgs& a, int ctas, cudaStream_t s) {
+    persistent_kernel(L, D)<<<ctas, 256, 0, s>>>(a);
     return cudaGetLastError();
 }
 
-cudaError_t persistent_occupancy(int* blocks_per_sm) {
-    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, k_persistent, 256, 0);
+cudaError_t persistent_occupancy(uint32_t L, uint32_t D, int* blocks_per_sm) {
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, persistent_kernel(L, D), 256, 0);
 }
 
 cudaError_t launch_search_lines(bool raw, const LineArgs& a, cudaStream_t s) {

@@ -60,3 +60,30 @@ def test_served_overflow_keeps_exact_count():
         r, recs = res[0]
         assert r["status"] == tmd.TMD_EOVERFLOW and r["count"] == n
         assert len(recs) == 8 and set(recs) <= set(solo)
+
+
+def test_group_overflow_reruns_jobs_alone_with_exact_counts():
+    """Jobs admitted together whose records overflow the group's buffer are
+    re-run one by one: few-candidate jobs come back complete, the others
+    with TMD_EOVERFLOW and their exact count."""
+    many = wl.Job(wl.FUNC_EXP, 0, 53, 18, 14, 3, 24, 3, wl.plain_start(), 1 << 28)
+    few = [wl.Job(wl.FUNC_EXP2, 1, 24, 14, 8, 2, 12, 1, 0, 1 << 14),
+           wl.Job(wl.FUNC_LOG, 2, 53, 40, 14, 2, 18, 3, 5 << 40, 1 << 20)]
+    jobs = [few[0], many, few[1]]
+    with tmd.Context(0) as ctx:
+        solo = [tmd.run([j], ctx=ctx, fused=True, cap=1 << 16) for j in jobs]
+        assert solo[0][1] < 8 and solo[2][1] < 8 and solo[1][1] > 8
+        with tmd.Server(ctx, cand_cap=8, max_batch=8, max_inflight=1) as srv:
+            for tag, j in enumerate(jobs):
+                srv.submit(j, tag)
+            got = {}
+            deadline = time.time() + 60
+            while len(got) < 3 and time.time() < deadline:
+                for r, recs in srv.poll(wait_ms=100):
+                    got[r["id"]] = (r, recs)
+    for tag in (0, 2):
+        r, recs = got[tag]
+        assert r["status"] == 0 and recs == solo[tag][0] and r["count"] == solo[tag][1]
+    r, recs = got[1]
+    assert r["status"] == tmd.TMD_EOVERFLOW and r["count"] == solo[1][1]
+    assert len(recs) == 8 and set(recs) <= set(solo[1][0])

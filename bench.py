@@ -217,7 +217,7 @@ def run_serving(tmd, ctx, jobs, rate_per_s, seed=2012):
             else [g2 - g1 for g1, g2 in zip([0.0] + wl.arrival_times(len(jobs), rate_per_s, seed)[:-1],
                                             wl.arrival_times(len(jobs), rate_per_s, seed))])
     lat, recs = [], 0
-    with tmd.Server(ctx, max_inflight=16, chunk_tasks=4096, cand_cap=1 << 14) as srv:
+    with tmd.Server(ctx, max_inflight=16, chunk_tasks=4096, cand_cap=1 << 14, max_batch=32) as srv:
         t0 = time.perf_counter()
         next_t = t0
         done = 0
@@ -256,6 +256,8 @@ def main():
     ap.add_argument("--m", type=int, default=40)
     ap.add_argument("--mixed-jobs", type=int, default=64,
                     help="jobs of the seeded mixed batch for batched vs per-job launches (0 = skip)")
+    ap.add_argument("--large", type=int, default=1,
+                    help="run the large batch: 2^x, 2^40 args in 2^16 uneven jobs (0 = skip)")
     ap.add_argument("--serve-jobs", type=int, default=400,
                     help="jobs of the seeded serving stream to serve (0 = skip)")
     ap.add_argument("--count-log2", type=int, default=36,
@@ -406,6 +408,23 @@ def main():
             sb.close()
         mb.close()
 
+    large = None
+    if args.large:
+        ljobs = wl.large_jobs()
+        largs = sum(j.count for j in ljobs)
+        dlc, dln = tmd.alloc_candidates(cap, local_rank)
+        t0 = time.perf_counter()
+        lb = tmd.Batch(ctx, ljobs, dlc, dln)
+        t_plan = time.perf_counter() - t0
+        ms_l = statistics.mean(timed(lb.launch, 5, 3))
+        st_l = lb.stats()
+        _, n_l = tmd.tmd_candidates(ctx, dlc, dln)
+        large = {"jobs": len(ljobs), "args": largs, "lines": st_l["lines"], "candidates": n_l,
+                 "batched": {"value": largs / (ms_l / 1e3), "ms_per_step": ms_l,
+                             "form": "one persistent graph launch over all 2^16 jobs"},
+                 "plan_and_tables_s": t_plan, "upload_bytes": lb.upload_bytes}
+        lb.close()
+
     serving = None
     if rank == 0 and args.serve_jobs > 0:
         sjobs = wl.serving_jobs()[: args.serve_jobs]
@@ -417,7 +436,7 @@ def main():
         serving = {"jobs": len(sjobs), "arrival_rate_jobs_per_s": rate, "mean_job_args": mean_size,
                    "p50_ms": 1e3 * percentile(lat, 0.50), "p99_ms": 1e3 * percentile(lat, 0.99),
                    "args_per_s": a / w, "saturated_args_per_s": sat, "records": nrec,
-                   "form": "continuous batching, 16 slots, Poisson arrivals at 0.8 x saturated rate"}
+                   "form": "continuous batching: up to 32 waiting jobs per admitted group, 16 slots, Poisson arrivals at 0.8 x saturated rate"}
 
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
@@ -443,6 +462,7 @@ def main():
                     "d2h_bytes_per_step": d2h, "ms_per_step": e2e_s * 1e3},
             "gpu_launches": args.steps * 1,
             "roofline": roofline, "cpu_baseline": cpu, "clocks": clocks, "mixed_batch": mixed,
+            "large_batch": large,
             "serving": serving,
         }
         print(json.dumps(line), flush=True)

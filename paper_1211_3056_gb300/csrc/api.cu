@@ -16,6 +16,7 @@
 #include "coeffs.cuh"
 #include "dev.hpp"
 #include "host.hpp"
+#include "planrec.cuh"
 
 namespace tmd {
 cudaError_t launch_tasks(bool fused, uint32_t L, uint32_t D, const LaunchArgs& a, cudaStream_t s);
@@ -24,6 +25,9 @@ cudaError_t persistent_occupancy(uint32_t L, uint32_t D, int* blocks_per_sm);
 cudaError_t upload_coeff_consts(const CoeffConsts& C);
 cudaError_t launch_block_tables(const DevJob* jobs, const DevBlock* blocks, uint64_t n_blocks,
                                 uint64_t* tables, uint32_t* status, uint32_t* err, cudaStream_t s);
+cudaError_t launch_plan(const DevJob* jobs, uint32_t n_jobs, DevBlock* blocks, uint64_t n_blocks,
+                        const uint32_t* class_jobs, const uint64_t* class_task0, uint32_t n_entries,
+                        DevTask* tasks, uint64_t n_tasks, cudaStream_t s);
 }  // namespace tmd
 
 namespace tmd {
@@ -41,17 +45,22 @@ struct ClassRange {
     uint64_t first, count;  // task range
 };
 
-// A plan resident on the device: jobs, blocks, tables, tasks.
+// A plan: per-job records with their segment tables, the class grouping of
+// the tasks, and (host mode only) the materialised blocks, tasks and tables.
 struct Plan {
     std::vector<tmd_job> key;
     std::vector<DevJob> jobs;
-    std::vector<DevBlock> blocks;
-    std::vector<uint64_t> tables;
-    std::vector<DevTask> tasks;
+    std::vector<uint32_t> class_jobs;   // job indices grouped by (limbs, degree) class
+    std::vector<uint64_t> class_task0;  // global first task of each class_jobs entry
+    std::vector<DevBlock> blocks;       // host mode
+    std::vector<uint64_t> tables;       // host mode
+    std::vector<DevTask> tasks;         // host mode
     std::vector<ClassRange> classes;
     uint64_t total_lines = 0;
     uint64_t total_args = 0;
     uint64_t table_words = 0;
+    uint64_t n_blocks = 0;
+    uint64_t n_tasks = 0;
     bool host_tables = true;
 };
 
@@ -110,43 +119,39 @@ uint32_t choose_nu(const tmd_job& job, uint64_t n_sub_block) {
     return nu;
 }
 
-// Plan every job; with host_tables, also compute all block tables (threads
-// over blocks), otherwise the table kernel computes them on the device.
+// Plan every job: output-binade segments and, per segment, its blocks,
+// sub-intervals and packets, as counts and offsets in the job record (the
+// device planning kernels expand them).  With host_tables the blocks, tasks
+// and correctly rounded tables are also materialised on the host (threads
+// over blocks).
 tmd_status build_plan(const tmd_job* jobs, uint32_t njobs, Plan& P, bool host_tables = true) {
     // reuse the vectors' storage of a previous plan (no new pages per call)
     P.key.clear();
     P.jobs.clear();
+    P.class_jobs.clear();
+    P.class_task0.clear();
     P.blocks.clear();
     P.tables.clear();
     P.tasks.clear();
     P.classes.clear();
-    P.total_lines = P.total_args = P.table_words = 0;
+    P.total_lines = P.total_args = P.table_words = P.n_blocks = P.n_tasks = 0;
     if (njobs == 0 || !jobs) return TMD_EINVAL;
     P.host_tables = host_tables;
     P.key.assign(jobs, jobs + njobs);
-    std::vector<std::vector<Segment>> segs(njobs);
-    std::vector<BlockPlan> bplan;
-    std::vector<uint32_t> bjob;
-    uint64_t line = 0, packet = 0, toff = 0;
+    std::vector<Segment> segs;
+    uint64_t line = 0, packet = 0, toff = 0, nblk_total = 0;
     for (uint32_t j = 0; j < njobs; j++) {
         const tmd_job& jb = jobs[j];
         tmd_status st = validate_job(jb);
         if (st != TMD_OK) return st;
-        st = plan_segments(jb, segs[j]);
+        st = plan_segments(jb, segs);
         if (st != TMD_OK) return st;
-        uint64_t nb, ns;
-        plan_counts(jb, segs[j], &nb, &ns);
-        if (P.blocks.size() + nb >= (1ull << 31)) return TMD_EUNSUPPORTED;
-        P.blocks.reserve(P.blocks.size() + nb);
-        P.tasks.reserve(P.tasks.size() + ns / 8 / 32 + nb + 1);
+        if (segs.size() > 4) return TMD_EUNSUPPORTED;
         DevJob dj;
         memset(&dj, 0, sizeof dj);
-        dj.line_off = line;
-        dj.n_lines = ns;
         dj.Tm = 1ull << (65 - jb.m);
-        dj.block_off = (uint32_t)P.blocks.size();
-        dj.n_blocks = (uint32_t)nb;
         dj.log2_N = jb.log2_N;
+        dj.log2_T = jb.log2_T;
         dj.d = (uint32_t)jb.d;
         dj.L = jb.limbs;
         dj.m = (uint32_t)jb.m;
@@ -154,111 +159,147 @@ tmd_status build_plan(const tmd_job* jobs, uint32_t njobs, Plan& P, bool host_ta
         dj.func = jb.func;
         dj.e_in = jb.e_in;
         dj.p = jb.p;
-        const uint64_t nsub_full = 1ull << (jb.log2_T - jb.log2_N);
-        dj.nu = choose_nu(jb, nsub_full);
-        const uint64_t words = (uint64_t)(2 * jb.d + 1) * jb.limbs;
-        const uint64_t job_pk0 = packet;
-        // blocks of T arguments from each segment start, walked incrementally
-        const uint64_t T = 1ull << jb.log2_T;
-        size_t seg_i = 0;
-        uint64_t seg_pos = segs[j].empty() ? 0 : segs[j][0].j0;
-        uint64_t sub_next = 0;
-        for (uint64_t b = 0; b < nb; b++) {
-            while (seg_pos >= segs[j][seg_i].j1) {
-                seg_i++;
-                seg_pos = segs[j][seg_i].j0;
-            }
-            const Segment& sg = segs[j][seg_i];
-            BlockPlan bp;
-            bp.start = seg_pos;
-            bp.length = std::min<uint64_t>(T, sg.j1 - seg_pos);
-            bp.first_sub = sub_next;
-            bp.e_out = sg.e_out;
-            seg_pos += bp.length;
-            sub_next += (bp.length + (1ull << jb.log2_N) - 1) >> jb.log2_N;
-            DevBlock db;
-            db.start = bp.start;
-            db.length = bp.length;
-            db.first_sub = bp.first_sub;
-            db.packet_off = packet;
-            db.table_off = toff;
-            db.job = j;
-            db.n_sub = (uint32_t)((bp.length + (1ull << jb.log2_N) - 1) >> jb.log2_N);
-            db.e_out = bp.e_out;
-            db.pad = 0;
-            packet += (db.n_sub + dj.nu - 1) / dj.nu;
-            toff += words;
-            P.blocks.push_back(db);
-            if (host_tables) {
-                bplan.push_back(bp);
-                bjob.push_back(j);
-            }
+        const uint64_t T = 1ull << jb.log2_T, N = 1ull << jb.log2_N;
+        const uint64_t SB = T >> jb.log2_N;  // sub-intervals of a full block
+        dj.nu = choose_nu(jb, SB);
+        dj.ppb = (uint32_t)((SB + dj.nu - 1) / dj.nu);
+        dj.words = (uint32_t)((2 * jb.d + 1) * jb.limbs);
+        dj.n_seg = (uint32_t)segs.size();
+        uint64_t nb = 0, ns = 0, np = 0;
+        for (size_t k = 0; k < segs.size(); k++) {
+            const uint64_t len = segs[k].j1 - segs[k].j0;
+            const uint64_t nfull = len >> jb.log2_T, rest = len & (T - 1);
+            const uint64_t nsub_last = (rest + N - 1) >> jb.log2_N;
+            dj.seg_j0[k] = segs[k].j0;
+            dj.seg_j1[k] = segs[k].j1;
+            dj.seg_e_out[k] = segs[k].e_out;
+            dj.seg_block0[k] = nb;
+            dj.seg_sub0[k] = ns;
+            dj.seg_packet0[k] = np;
+            nb += nfull + (rest ? 1 : 0);
+            ns += nfull * SB + nsub_last;
+            np += nfull * dj.ppb + (nsub_last + dj.nu - 1) / dj.nu;
         }
-        uint32_t bcur = dj.block_off;
-        for (uint64_t g = job_pk0; g < packet; g += 32) {
-            while (bcur + 1 < dj.block_off + dj.n_blocks && P.blocks[bcur + 1].packet_off <= g) bcur++;
-            DevTask t;
-            t.g0 = g;
-            t.count = (uint32_t)std::min<uint64_t>(32, packet - g);
-            t.job = j;
-            t.block0 = bcur;
-            t.pad = 0;
-            P.tasks.push_back(t);
-        }
+        if (nblk_total + nb >= (1ull << 31)) return TMD_EUNSUPPORTED;
+        dj.line_off = line;
+        dj.n_lines = ns;
+        dj.block_off = (uint32_t)nblk_total;
+        dj.n_blocks = (uint32_t)nb;
+        dj.packet_off = packet;
+        dj.n_packets = np;
+        dj.table_off = toff;
         P.jobs.push_back(dj);
         line += ns;
+        packet += np;
+        toff += nb * dj.words;
+        nblk_total += nb;
         P.total_args += jb.count;
     }
     P.total_lines = line;
     P.table_words = toff;
-    if (host_tables) P.tables.assign(toff, 0);
-    // correctly rounded tables, blocks spread over host threads
+    P.n_blocks = nblk_total;
+    // tasks class by class, job by job (stable)
+    uint64_t task = 0;
+    for (uint32_t key = 0; key < 8 * (MAX_LIMBS + 1); key++) {
+        const uint64_t first = task;
+        uint32_t Lk = 0, Dk = 0;
+        for (uint32_t j = 0; j < njobs; j++) {
+            const DevJob& dj = P.jobs[j];
+            if (dj.L * 8 + dj.d != key) continue;
+            P.class_jobs.push_back(j);
+            P.class_task0.push_back(task);
+            task += (dj.n_packets + 31) / 32;
+            Lk = dj.L;
+            Dk = dj.d;
+        }
+        if (task > first) P.classes.push_back(ClassRange{Lk, Dk, first, task - first});
+    }
+    P.n_tasks = task;
+    if (!host_tables) return TMD_OK;
+    // host mode: materialise blocks, tasks and tables with the same formulas
+    P.blocks.resize(P.n_blocks);
+    for (uint32_t j = 0; j < njobs; j++)
+        for (uint64_t rb = 0; rb < P.jobs[j].n_blocks; rb++)
+            P.blocks[P.jobs[j].block_off + rb] = block_record(P.jobs[j], j, rb);
+    P.tasks.resize(P.n_tasks);
+    for (size_t e = 0; e < P.class_jobs.size(); e++) {
+        const uint32_t j = P.class_jobs[e];
+        const uint64_t nt = (P.jobs[j].n_packets + 31) / 32;
+        for (uint64_t k = 0; k < nt; k++) P.tasks[P.class_task0[e] + k] = task_record(P.jobs[j], j, k);
+    }
+    P.tables.assign(toff, 0);
     std::atomic<uint64_t> next(0);
     std::atomic<int> bad(0);
-    const uint64_t nblk = P.blocks.size();
+    const uint64_t nblk = P.n_blocks;
     auto worker = [&]() {
         for (;;) {
             uint64_t b = next.fetch_add(16);
             if (b >= nblk) break;
             uint64_t e = std::min<uint64_t>(b + 16, nblk);
             for (; b < e; b++) {
-                const tmd_job& jb = jobs[bjob[b]];
-                if (block_table(jb, bplan[b], nullptr, &P.tables[P.blocks[b].table_off]) != TMD_OK)
-                    bad.store(1);
+                const DevBlock& db = P.blocks[b];
+                BlockPlan bp;
+                bp.start = db.start;
+                bp.length = db.length;
+                bp.first_sub = db.first_sub;
+                bp.e_out = db.e_out;
+                if (block_table(jobs[db.job], bp, nullptr, &P.tables[db.table_off]) != TMD_OK) bad.store(1);
             }
         }
     };
     unsigned nt = std::min<uint64_t>(host_threads(), (nblk + 15) / 16);
-    if (!host_tables) {
-        // tables come from the device kernel
-    } else if (nt <= 1) {
+    if (nt <= 1) {
         worker();
     } else {
         std::vector<std::thread> th;
         for (unsigned i = 0; i < nt; i++) th.emplace_back(worker);
         for (auto& t : th) t.join();
     }
-    if (bad.load()) return TMD_EUNSUPPORTED;
-    // group tasks by (L, D) so that the plain form launches one kernel per
-    // class (tasks are contiguous per job: reorder whole jobs, stably)
-    bool one_class = true;
-    for (uint32_t j = 1; j < njobs; j++)
-        one_class &= P.jobs[j].L == P.jobs[0].L && P.jobs[j].d == P.jobs[0].d;
-    if (!one_class) {
-        std::vector<DevTask> sorted;
-        sorted.reserve(P.tasks.size());
-        for (uint32_t key = 0; key < 8 * (MAX_LIMBS + 1); key++)
-            for (const DevTask& t : P.tasks)
-                if (P.jobs[t.job].L * 8 + P.jobs[t.job].d == key) sorted.push_back(t);
-        P.tasks.swap(sorted);
+    return bad.load() ? TMD_EUNSUPPORTED : TMD_OK;
+}
+
+// Device layout of a plan: jobs | class jobs | class first tasks | blocks |
+// tasks | table status | tables.  Without host tables only the first three
+// sections are uploaded; the planning and table kernels write the rest.
+struct Layout {
+    size_t o_cjobs, o_ctask, o_blocks, o_tasks, o_status, o_tables, total, upload;
+};
+
+Layout plan_layout(const Plan& P) {
+    Layout L;
+    L.o_cjobs = align256(P.jobs.size() * sizeof(DevJob));
+    L.o_ctask = align256(L.o_cjobs + P.class_jobs.size() * sizeof(uint32_t));
+    L.o_blocks = align256(L.o_ctask + P.class_task0.size() * sizeof(uint64_t));
+    L.o_tasks = align256(L.o_blocks + P.n_blocks * sizeof(DevBlock));
+    L.o_status = align256(L.o_tasks + P.n_tasks * sizeof(DevTask));
+    L.o_tables = align256(L.o_status + P.n_blocks * sizeof(uint32_t));
+    L.total = align256(L.o_tables + P.table_words * sizeof(uint64_t));
+    L.upload = P.host_tables ? L.total : L.o_blocks;
+    return L;
+}
+
+void pack_plan(const Plan& P, const Layout& L, char* dst) {
+    memset(dst, 0, L.upload);
+    memcpy(dst, P.jobs.data(), P.jobs.size() * sizeof(DevJob));
+    memcpy(dst + L.o_cjobs, P.class_jobs.data(), P.class_jobs.size() * sizeof(uint32_t));
+    memcpy(dst + L.o_ctask, P.class_task0.data(), P.class_task0.size() * sizeof(uint64_t));
+    if (P.host_tables) {
+        memcpy(dst + L.o_blocks, P.blocks.data(), P.blocks.size() * sizeof(DevBlock));
+        memcpy(dst + L.o_tasks, P.tasks.data(), P.tasks.size() * sizeof(DevTask));
+        memcpy(dst + L.o_tables, P.tables.data(), P.tables.size() * sizeof(uint64_t));
     }
-    for (uint64_t i = 0; i < P.tasks.size(); i++) {
-        const DevJob& dj = P.jobs[P.tasks[i].job];
-        if (P.classes.empty() || P.classes.back().L != dj.L || P.classes.back().D != dj.d)
-            P.classes.push_back(ClassRange{dj.L, dj.d, i, 0});
-        P.classes.back().count++;
-    }
-    return TMD_OK;
+}
+
+// after the upload: blocks, tasks and tables on the device (unless host mode)
+cudaError_t expand_plan(const Plan& P, const Layout& L, char* d_arena, uint32_t* plan_err, cudaStream_t s) {
+    if (P.host_tables) return cudaSuccess;
+    cudaError_t e = launch_plan((const DevJob*)d_arena, (uint32_t)P.jobs.size(), (DevBlock*)(d_arena + L.o_blocks),
+                                P.n_blocks, (const uint32_t*)(d_arena + L.o_cjobs),
+                                (const uint64_t*)(d_arena + L.o_ctask), (uint32_t)P.class_jobs.size(),
+                                (DevTask*)(d_arena + L.o_tasks), P.n_tasks, s);
+    if (e != cudaSuccess) return e;
+    return launch_block_tables((const DevJob*)d_arena, (const DevBlock*)(d_arena + L.o_blocks), P.n_blocks,
+                               (uint64_t*)(d_arena + L.o_tables), (uint32_t*)(d_arena + L.o_status), plan_err, s);
 }
 
 // Arena layout: jobs | blocks | tasks | table status | tables.  The first
@@ -266,50 +307,37 @@ tmd_status build_plan(const tmd_job* jobs, uint32_t njobs, Plan& P, bool host_ta
 // on the host, else written by the table kernel on the device.
 tmd_status upload_plan(tmd_ctx* c, cudaStream_t s) {
     Plan& P = c->plan;
-    size_t o_jobs = 0;
-    size_t o_blocks = align256(o_jobs + P.jobs.size() * sizeof(DevJob));
-    size_t o_tasks = align256(o_blocks + P.blocks.size() * sizeof(DevBlock));
-    size_t o_status = align256(o_tasks + P.tasks.size() * sizeof(DevTask));
-    size_t o_tables = align256(o_status + P.blocks.size() * sizeof(uint32_t));
-    size_t total = align256(o_tables + P.table_words * sizeof(uint64_t));
-    size_t upload = P.host_tables ? total : o_status;
+    const Layout Lo = plan_layout(P);
     if (c->stage_pending) {
         CK(cudaEventSynchronize(c->stage_done));
         c->stage_pending = false;
     }
-    if (upload > c->stage_cap) {
+    if (Lo.upload > c->stage_cap) {
         if (c->h_stage) CK(cudaFreeHost(c->h_stage));
         c->h_stage = nullptr;
-        size_t cap = std::max(upload, c->stage_cap * 2);
+        size_t cap = std::max(Lo.upload, c->stage_cap * 2);
         CK(cudaHostAlloc((void**)&c->h_stage, cap, cudaHostAllocDefault));
         c->stage_cap = cap;
     }
-    if (total > c->arena_cap) {
+    if (Lo.total > c->arena_cap) {
         CK(cudaStreamSynchronize(s));
         if (c->d_arena) CK(cudaFree(c->d_arena));
         c->d_arena = nullptr;
-        size_t cap = std::max(total, c->arena_cap * 2);
+        size_t cap = std::max(Lo.total, c->arena_cap * 2);
         CK(cudaMalloc((void**)&c->d_arena, cap));
         c->arena_cap = cap;
     }
-    memset(c->h_stage, 0, upload);
-    memcpy(c->h_stage + o_jobs, P.jobs.data(), P.jobs.size() * sizeof(DevJob));
-    memcpy(c->h_stage + o_blocks, P.blocks.data(), P.blocks.size() * sizeof(DevBlock));
-    memcpy(c->h_stage + o_tasks, P.tasks.data(), P.tasks.size() * sizeof(DevTask));
-    if (P.host_tables) memcpy(c->h_stage + o_tables, P.tables.data(), P.tables.size() * sizeof(uint64_t));
-    CK(cudaMemcpyAsync(c->d_arena, c->h_stage, upload, cudaMemcpyHostToDevice, s));
+    pack_plan(P, Lo, c->h_stage);
+    CK(cudaMemcpyAsync(c->d_arena, c->h_stage, Lo.upload, cudaMemcpyHostToDevice, s));
     CK(cudaEventRecord(c->stage_done, s));
     c->stage_pending = true;
-    c->upload_bytes = upload;
-    c->off_jobs = o_jobs;
-    c->off_blocks = o_blocks;
-    c->off_tables = o_tables;
-    c->off_tasks = o_tasks;
+    c->upload_bytes = Lo.upload;
+    c->off_jobs = 0;
+    c->off_blocks = Lo.o_blocks;
+    c->off_tables = Lo.o_tables;
+    c->off_tasks = Lo.o_tasks;
     CK(cudaMemsetAsync(plan_err_ptr(c), 0, sizeof(uint32_t), s));
-    if (!P.host_tables)
-        CK(launch_block_tables((const DevJob*)(c->d_arena + o_jobs), (const DevBlock*)(c->d_arena + o_blocks),
-                               P.blocks.size(), (uint64_t*)(c->d_arena + o_tables),
-                               (uint32_t*)(c->d_arena + o_status), plan_err_ptr(c), s));
+    CK(expand_plan(P, Lo, c->d_arena, plan_err_ptr(c), s));
     return TMD_OK;
 }
 
@@ -336,7 +364,7 @@ LaunchArgs task_args(tmd_ctx* c) {
     a.blocks = (const DevBlock*)(c->d_arena + c->off_blocks);
     a.tables = (const uint64_t*)(c->d_arena + c->off_tables);
     a.tasks = (const DevTask*)(c->d_arena + c->off_tasks);
-    a.n_tasks = c->plan.tasks.size();
+    a.n_tasks = c->plan.n_tasks;
     a.stats = stats_ptr(c);
     a.queue_head = queue_ptr(c);
     return a;
@@ -643,29 +671,21 @@ tmd_status tmd_batch_create(tmd_ctx* c, const tmd_job* jobs, uint32_t njobs, tmd
         return st;
     }
     Plan& P = b->plan;
-    // arena: jobs | blocks | tasks | table status | tables (device-written)
-    size_t o_blocks = align256(P.jobs.size() * sizeof(DevJob));
-    size_t o_tasks = align256(o_blocks + P.blocks.size() * sizeof(DevBlock));
-    size_t o_status = align256(o_tasks + P.tasks.size() * sizeof(DevTask));
-    size_t o_tables = align256(o_status + P.blocks.size() * sizeof(uint32_t));
-    size_t total = align256(o_tables + P.table_words * sizeof(uint64_t));
-    std::vector<char> host(o_status, 0);
-    memcpy(host.data(), P.jobs.data(), P.jobs.size() * sizeof(DevJob));
-    memcpy(host.data() + o_blocks, P.blocks.data(), P.blocks.size() * sizeof(DevBlock));
-    memcpy(host.data() + o_tasks, P.tasks.data(), P.tasks.size() * sizeof(DevTask));
+    const Layout Lo = plan_layout(P);
+    const size_t o_blocks = Lo.o_blocks, o_tasks = Lo.o_tasks, o_tables = Lo.o_tables;
+    std::vector<char> host(Lo.upload, 0);
+    pack_plan(P, Lo, host.data());
     uint32_t* plan_err = nullptr;
     uint32_t perr = 0;
-    if (cudaMalloc((void**)&b->d_arena, total) != cudaSuccess ||
+    if (cudaMalloc((void**)&b->d_arena, Lo.total) != cudaSuccess ||
         cudaMalloc((void**)&b->d_misc, BATCH_MISC_BYTES) != cudaSuccess ||
         cudaMemsetAsync(b->d_misc, 0, BATCH_MISC_BYTES, s) != cudaSuccess ||
-        cudaMemcpyAsync(b->d_arena, host.data(), o_status, cudaMemcpyHostToDevice, s) != cudaSuccess) {
+        cudaMemcpyAsync(b->d_arena, host.data(), Lo.upload, cudaMemcpyHostToDevice, s) != cudaSuccess) {
         batch_free(b);
         return TMD_ECUDA;
     }
     plan_err = (uint32_t*)(b->d_misc + ST_COUNT) + 2;
-    if (launch_block_tables((const DevJob*)b->d_arena, (const DevBlock*)(b->d_arena + o_blocks), P.blocks.size(),
-                            (uint64_t*)(b->d_arena + o_tables), (uint32_t*)(b->d_arena + o_status), plan_err,
-                            s) != cudaSuccess ||
+    if (expand_plan(P, Lo, b->d_arena, plan_err, s) != cudaSuccess ||
         cudaMemcpyAsync(&perr, plan_err, sizeof perr, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
         cudaStreamSynchronize(s) != cudaSuccess) {
         batch_free(b);
@@ -675,8 +695,8 @@ tmd_status tmd_batch_create(tmd_ctx* c, const tmd_job* jobs, uint32_t njobs, tmd
         batch_free(b);
         return TMD_EUNSUPPORTED;
     }
-    b->upload_bytes = o_status;
-    if (upload_bytes) *upload_bytes = o_status;
+    b->upload_bytes = Lo.upload;
+    if (upload_bytes) *upload_bytes = Lo.upload;
     b->off_blocks = o_blocks;
     b->off_tables = o_tables;
     b->off_tasks = o_tasks;
@@ -840,34 +860,26 @@ tmd_status slot_start(tmd_server* S, Slot& sl) {
     tmd_status st = build_plan(sl.jobs.data(), (uint32_t)sl.jobs.size(), sl.plan, /*host_tables=*/false);
     if (st != TMD_OK) return st;
     Plan& P = sl.plan;
-    const size_t o_blocks = align256(P.jobs.size() * sizeof(DevJob));
-    const size_t o_tasks = align256(o_blocks + P.blocks.size() * sizeof(DevBlock));
-    const size_t o_status = align256(o_tasks + P.tasks.size() * sizeof(DevTask));
-    const size_t o_tables = align256(o_status + P.blocks.size() * sizeof(uint32_t));
-    const size_t total = align256(o_tables + P.table_words * sizeof(uint64_t));
+    const Layout Lo = plan_layout(P);
+    const size_t o_blocks = Lo.o_blocks, o_tasks = Lo.o_tasks, o_tables = Lo.o_tables, total = Lo.total;
     if (total > sl.arena_cap) {
         if (sl.d_arena) CK(cudaFreeAsync(sl.d_arena, sl.stream));
         sl.d_arena = nullptr;
         CK(cudaMallocAsync((void**)&sl.d_arena, total, sl.stream));
         sl.arena_cap = total;
     }
-    if (o_status > sl.stage_cap) {
+    if (Lo.upload > sl.stage_cap) {
         CK(cudaStreamSynchronize(sl.stream));
         if (sl.h_stage) CK(cudaFreeHost(sl.h_stage));
         sl.h_stage = nullptr;
-        CK(cudaHostAlloc((void**)&sl.h_stage, o_status, cudaHostAllocDefault));
-        sl.stage_cap = o_status;
+        CK(cudaHostAlloc((void**)&sl.h_stage, Lo.upload, cudaHostAllocDefault));
+        sl.stage_cap = Lo.upload;
     }
-    memset(sl.h_stage, 0, o_status);
-    memcpy(sl.h_stage, P.jobs.data(), P.jobs.size() * sizeof(DevJob));
-    memcpy(sl.h_stage + o_blocks, P.blocks.data(), P.blocks.size() * sizeof(DevBlock));
-    memcpy(sl.h_stage + o_tasks, P.tasks.data(), P.tasks.size() * sizeof(DevTask));
-    CK(cudaMemcpyAsync(sl.d_arena, sl.h_stage, o_status, cudaMemcpyHostToDevice, sl.stream));
+    pack_plan(P, Lo, sl.h_stage);
+    CK(cudaMemcpyAsync(sl.d_arena, sl.h_stage, Lo.upload, cudaMemcpyHostToDevice, sl.stream));
     CK(cudaMemsetAsync(sl.d_meta, 0, META_BYTES, sl.stream));
     uint32_t* perr = (uint32_t*)(sl.d_meta + sizeof(uint64_t) * ST_COUNT) + 2;
-    CK(launch_block_tables((const DevJob*)sl.d_arena, (const DevBlock*)(sl.d_arena + o_blocks), P.blocks.size(),
-                           (uint64_t*)(sl.d_arena + o_tables), (uint32_t*)(sl.d_arena + o_status), perr,
-                           sl.stream));
+    CK(expand_plan(P, Lo, sl.d_arena, perr, sl.stream));
     sl.off_blocks = o_blocks;
     sl.off_tasks = o_tasks;
     sl.off_tables = o_tables;

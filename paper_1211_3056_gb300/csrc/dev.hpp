@@ -23,6 +23,20 @@ struct DevJob {
     int32_t func;          // tmd_func
     int32_t e_in;
     int32_t p;
+    uint32_t n_seg;        // output-binade segments (1..4)
+    // device-side planning: the job's blocks and packets, segment by segment
+    uint64_t packet_off;   // global index of the job's first packet
+    uint64_t n_packets;
+    uint64_t table_off;    // word offset of the job's first block table
+    uint32_t ppb;          // packets of a full block
+    uint32_t words;        // table words of a block ((2d+1) L)
+    uint64_t seg_j0[4];    // first argument of each segment
+    uint64_t seg_j1[4];    // end of each segment
+    uint64_t seg_block0[4];    // job-relative first block of each segment
+    uint64_t seg_sub0[4];      // job-relative first sub-interval of each segment
+    uint64_t seg_packet0[4];   // job-relative first packet of each segment
+    int32_t seg_e_out[4];
+    uint32_t log2_T;
     uint32_t pad;
 };
 

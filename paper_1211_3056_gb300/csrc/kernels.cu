@@ -26,6 +26,7 @@
 
 #include "coeffs.cuh"
 #include "dev.hpp"
+#include "planrec.cuh"
 
 namespace tmd {
 
@@ -611,6 +612,49 @@ __global__ void __launch_bounds__(256) k_lower_bounds(const uint64_t* B, const u
     uint32_t hs = 0;
     lb[s] = cf_lower_bound(B[s], A[s], ln, &hs);
     if (hs_out) hs_out[s] = hs;
+}
+
+// ------------------------------------------------------- device planning
+// Block and task records from the per-job segment table (Sect. III-A split
+// and Sect. IV blocks: blocks of T arguments from each segment start, the
+// last one of a segment shorter; packets of nu sub-intervals per block).
+__global__ void __launch_bounds__(256) k_plan_blocks(const DevJob* jobs, uint32_t n_jobs, DevBlock* blocks,
+                                                     uint64_t n_blocks) {
+    const uint64_t b = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (b >= n_blocks) return;
+    uint32_t lo = 0, hi = n_jobs - 1;
+    while (lo < hi) {  // last job whose first block is <= b
+        const uint32_t mid = (lo + hi + 1) >> 1;
+        if (jobs[mid].block_off <= b) lo = mid; else hi = mid - 1;
+    }
+    blocks[b] = block_record(jobs[lo], lo, b - jobs[lo].block_off);
+}
+
+// Tasks are laid out class by class (class_jobs lists the jobs of each
+// (limbs, degree) class in order; class_task0 their first task), 32 packets
+// per task within a job.
+__global__ void __launch_bounds__(256) k_plan_tasks(const DevJob* jobs, const uint32_t* class_jobs,
+                                                    const uint64_t* class_task0, uint32_t n_entries,
+                                                    DevTask* tasks, uint64_t n_tasks) {
+    const uint64_t t = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= n_tasks) return;
+    uint32_t lo = 0, hi = n_entries - 1;
+    while (lo < hi) {
+        const uint32_t mid = (lo + hi + 1) >> 1;
+        if (class_task0[mid] <= t) lo = mid; else hi = mid - 1;
+    }
+    const uint32_t j = class_jobs[lo];
+    tasks[t] = task_record(jobs[j], j, t - class_task0[lo]);
+}
+
+cudaError_t launch_plan(const DevJob* jobs, uint32_t n_jobs, DevBlock* blocks, uint64_t n_blocks,
+                        const uint32_t* class_jobs, const uint64_t* class_task0, uint32_t n_entries,
+                        DevTask* tasks, uint64_t n_tasks, cudaStream_t s) {
+    if (n_blocks) k_plan_blocks<<<(unsigned)((n_blocks + 255) / 256), 256, 0, s>>>(jobs, n_jobs, blocks, n_blocks);
+    if (n_tasks)
+        k_plan_tasks<<<(unsigned)((n_tasks + 255) / 256), 256, 0, s>>>(jobs, class_jobs, class_task0, n_entries,
+                                                                       tasks, n_tasks);
+    return cudaGetLastError();
 }
 
 // ---------------------------------------------------------- block tables

@@ -65,3 +65,21 @@ def test_batch_equals_plain_per_job(ctx):
     k = min(range(len(jobs)), key=lambda i: jobs[i].count)
     want = oc.job_candidates(jobs[k], k)
     assert [r for r in got if r[0] == k] == sorted(want, key=lambda r: (r[0], r[2], r[3]))
+
+
+def test_large_batch_sample_exact(ctx):
+    """The first 256 jobs of the large 2^x batch (uneven sizes, N = 2^16,
+    192-bit words) at the m = 22 twin in one persistent launch; sampled jobs
+    record by record against the oracle, all counts consistent."""
+    jobs = [j.replace(m=22) for j in wl.large_jobs()[:256]]
+    d_cand, d_count = tmd.alloc_candidates(1 << 16)
+    b = tmd.Batch(ctx, jobs, d_cand, d_count)
+    b.launch()
+    got, n = tmd.tmd_candidates(ctx, d_cand, d_count)
+    b.close()
+    assert n == len(got) > 500
+    import random
+    rng = random.Random(4)
+    for k in sorted(rng.sample(range(len(jobs)), 12)) + [0, 255]:
+        want = oc.job_candidates(jobs[k], k)
+        assert [r for r in got if r[0] == k] == sorted(want, key=lambda r: (r[0], r[2], r[3])), k

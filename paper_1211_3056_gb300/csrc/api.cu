@@ -3,6 +3,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <array>
 #include <atomic>
 #include <cstdlib>
 #include <chrono>
@@ -23,8 +24,8 @@ cudaError_t launch_tasks(bool fused, uint32_t L, uint32_t D, const LaunchArgs& a
 cudaError_t launch_persistent(uint32_t L, uint32_t D, const LaunchArgs& a, int ctas, cudaStream_t s);
 cudaError_t persistent_occupancy(uint32_t L, uint32_t D, int* blocks_per_sm);
 cudaError_t upload_coeff_consts(const CoeffConsts& C);
-cudaError_t launch_block_tables(const DevJob* jobs, const DevBlock* blocks, uint64_t n_blocks,
-                                uint64_t* tables, uint32_t* status, uint32_t* err, cudaStream_t s);
+cudaError_t launch_block_tables(const DevJob* jobs, const DevBlock* blocks, uint64_t n_blocks, uint64_t* tables,
+                                uint32_t* status, uint32_t* err, cudaStream_t s);
 cudaError_t launch_plan(const DevJob* jobs, uint32_t n_jobs, DevBlock* blocks, uint64_t n_blocks,
                         const uint32_t* class_jobs, const uint64_t* class_task0, uint32_t n_entries,
                         DevTask* tasks, uint64_t n_tasks, cudaStream_t s);
@@ -108,6 +109,18 @@ unsigned host_threads() {
     return n ? n : 1;
 }
 
+// fn() on n threads (the calling thread alone when n <= 1)
+template <class F>
+void run_threads(unsigned n, F&& fn) {
+    if (n <= 1) {
+        fn();
+        return;
+    }
+    std::vector<std::thread> th;
+    for (unsigned i = 0; i < n; i++) th.emplace_back(fn);
+    for (auto& t : th) t.join();
+}
+
 uint32_t choose_nu(const tmd_job& job, uint64_t n_sub_block) {
     const char* env = getenv("TMD_NU");
     uint32_t nu = 8;  // at most the kernels' shared-memory stage (8 lines per lane)
@@ -138,15 +151,38 @@ tmd_status build_plan(const tmd_job* jobs, uint32_t njobs, Plan& P, bool host_ta
     if (njobs == 0 || !jobs) return TMD_EINVAL;
     P.host_tables = host_tables;
     P.key.assign(jobs, jobs + njobs);
+    // validation and output-binade cuts of every job (independent per job:
+    // spread over host threads for large batches)
+    std::vector<std::array<Segment, MAX_SEGMENTS>> seg_of(njobs);
+    std::vector<uint8_t> nseg_of(njobs, 0);
+    std::vector<tmd_status> st_of(njobs, TMD_OK);
+    auto seg_work = [&](uint32_t a, uint32_t b) {
+        std::vector<Segment> sg;
+        for (uint32_t j = a; j < b; j++) {
+            tmd_status st = validate_job(jobs[j]);
+            if (st == TMD_OK) st = plan_segments(jobs[j], sg);
+            if (st == TMD_OK && sg.size() > MAX_SEGMENTS) st = TMD_EUNSUPPORTED;
+            st_of[j] = st;
+            if (st != TMD_OK) continue;
+            nseg_of[j] = (uint8_t)sg.size();
+            for (size_t k = 0; k < sg.size(); k++) seg_of[j][k] = sg[k];
+        }
+    };
+    const unsigned nth = njobs >= 512 ? std::min<unsigned>(host_threads(), 32) : 1;
+    std::atomic<uint32_t> next_chunk(0);
+    run_threads(nth, [&]() {
+        for (;;) {
+            const uint32_t a = next_chunk.fetch_add(64);
+            if (a >= njobs) break;
+            seg_work(a, std::min<uint32_t>(njobs, a + 64));
+        }
+    });
     std::vector<Segment> segs;
     uint64_t line = 0, packet = 0, toff = 0, nblk_total = 0;
     for (uint32_t j = 0; j < njobs; j++) {
         const tmd_job& jb = jobs[j];
-        tmd_status st = validate_job(jb);
-        if (st != TMD_OK) return st;
-        st = plan_segments(jb, segs);
-        if (st != TMD_OK) return st;
-        if (segs.size() > 4) return TMD_EUNSUPPORTED;
+        if (st_of[j] != TMD_OK) return st_of[j];
+        segs.assign(seg_of[j].begin(), seg_of[j].begin() + nseg_of[j]);
         DevJob dj;
         memset(&dj, 0, sizeof dj);
         dj.Tm = 1ull << (65 - jb.m);
@@ -228,6 +264,18 @@ tmd_status build_plan(const tmd_job* jobs, uint32_t njobs, Plan& P, bool host_ta
         for (uint64_t k = 0; k < nt; k++) P.tasks[P.class_task0[e] + k] = task_record(P.jobs[j], j, k);
     }
     P.tables.assign(toff, 0);
+    // the anchors of the jobs, then the tables block by block
+    std::vector<Anchor> anchors(njobs);
+    std::atomic<uint32_t> next_job(0);
+    run_threads(std::min<unsigned>(host_threads(), njobs), [&]() {
+        std::vector<Segment> sg;
+        for (;;) {
+            const uint32_t j = next_job.fetch_add(1);
+            if (j >= njobs) break;
+            sg.assign(seg_of[j].begin(), seg_of[j].begin() + nseg_of[j]);
+            host_anchor(jobs[j], sg, &anchors[j]);
+        }
+    });
     std::atomic<uint64_t> next(0);
     std::atomic<int> bad(0);
     const uint64_t nblk = P.n_blocks;
@@ -243,18 +291,12 @@ tmd_status build_plan(const tmd_job* jobs, uint32_t njobs, Plan& P, bool host_ta
                 bp.length = db.length;
                 bp.first_sub = db.first_sub;
                 bp.e_out = db.e_out;
-                if (block_table(jobs[db.job], bp, nullptr, &P.tables[db.table_off]) != TMD_OK) bad.store(1);
+                if (block_table(jobs[db.job], bp, nullptr, &P.tables[db.table_off], &anchors[db.job]) != TMD_OK)
+                    bad.store(1);
             }
         }
     };
-    unsigned nt = std::min<uint64_t>(host_threads(), (nblk + 15) / 16);
-    if (nt <= 1) {
-        worker();
-    } else {
-        std::vector<std::thread> th;
-        for (unsigned i = 0; i < nt; i++) th.emplace_back(worker);
-        for (auto& t : th) t.join();
-    }
+    run_threads((unsigned)std::min<uint64_t>(host_threads(), (nblk + 15) / 16), worker);
     return bad.load() ? TMD_EUNSUPPORTED : TMD_OK;
 }
 
@@ -469,7 +511,9 @@ tmd_status tmd_block_tables(const tmd_job* job, uint64_t block, uint64_t* coeffs
         info->e_out = bp.e_out;
         info->scale_log2 = scale_log2(*job, bp.e_out);
     }
-    return block_table(*job, bp, coeffs, table);
+    Anchor A;
+    host_anchor(*job, segs, &A);
+    return block_table(*job, bp, coeffs, table, &A);
 }
 
 tmd_status tmd_generate(tmd_ctx* c, const tmd_job* jobs, uint32_t njobs, void* d_lin, size_t lin_bytes,

@@ -98,10 +98,160 @@ TMD_HD bool log_exact(uint64_t M, int k, int sh, const CoeffConsts& C, int L, ui
 
 }  // namespace cf_detail
 
-// c[k*L + l] for k = 0..d.  Returns false when a rounding stays undecided
-// at this width (retry with a wider NL) or a width is exceeded.
+// 2^X for X = M 2^-q (M not a multiple of 2^q) with PB fractional bits:
+// exp of the outward-rounded argument X ln 2 with PB + 16 bits, both ends.
 template <int NL>
-TMD_HD bool block_coeffs(const CoeffJob& J, uint64_t M, int guard, const CoeffConsts& C, uint64_t* c) {
+TMD_HD bool exp2_arg(const CoeffJob& J, uint64_t M, unsigned PB, const CoeffConsts& C, fx::Enc<NL>& f) {
+    using namespace fx;
+    const unsigned q = (unsigned)(J.p - J.e_in);
+    U<NL> llo, lhi;
+    cf_detail::ln2_at<NL>(C, PB + 16, llo, lhi);
+    U<NL> ylo = llo, yhi = lhi;
+    mul_u64(ylo, M);
+    shr(ylo, q);
+    mul_u64(yhi, M);
+    const bool up = low_bits(yhi, q);
+    shr(yhi, q);
+    if (up) add_u64(yhi, 1);
+    // Xc = ceil(M 2^-q) bounds the argument X ln 2 < X
+    const uint64_t Xc = (M >> q) + ((M & ((1ull << q) - 1)) ? 1 : 0);
+    uint64_t e_lo, e_hi;
+    U<NL> vlo, vhi;
+    if (!exp_big<NL>(ylo, PB + 16, Xc, C.div, vlo, e_lo)) return false;
+    if (!exp_big<NL>(yhi, PB + 16, Xc, C.div, vhi, e_hi)) return false;
+    add_u64(vhi, e_hi);
+    shr(vlo, 16);
+    const bool up2 = low_bits(vhi, 16);
+    shr(vhi, 16);
+    if (up2) add_u64(vhi, 1);
+    f.lo = vlo;
+    f.hi = vhi;
+    return true;
+}
+
+// Per-job anchor: an enclosure of f at the job's first block X_a (exp and
+// 2^x: f(X_a) with P2 fractional bits; log: log X_a with P), at the
+// precision of the job's first segment (the largest scale of the job).
+// Blocks then evaluate only the short series of the offset X_t - X_a:
+//   exp(X_t) = exp(X_a) exp(d),  2^X_t = 2^X_a exp(d ln 2),
+//   log X_t = log X_a + 2 atanh((M_t - M_a)/(M_t + M_a)),
+// with d = (M_t - M_a) 2^(e_in - p) small.
+enum { ANCHOR_LIMBS = 8 };
+struct Anchor {
+    uint64_t Ma;
+    uint32_t P;     // fractional bits of lo, hi
+    uint32_t ok;
+    uint64_t lo[ANCHOR_LIMBS], hi[ANCHOR_LIMBS];
+};
+
+namespace cf_detail {
+
+// fractional bits of the base enclosure of f for a block with this scale
+TMD_HD unsigned base_bits(const CoeffJob& J, int guard) {
+    const int E0 = 64 * J.L + J.scale_log2;
+    const unsigned P = (unsigned)((E0 > 0 ? E0 : 0) + guard);
+    return J.func == 2 ? P : P + 16;
+}
+
+// direct enclosure of f(X) (exp, 2^x: P2 = P + 16 bits; log: P bits)
+template <int NL>
+TMD_HD bool f_direct(const CoeffJob& J, uint64_t M, unsigned PB, const CoeffConsts& C, fx::Enc<NL>& f, bool& exact) {
+    using namespace fx;
+    const unsigned q = (unsigned)(J.p - J.e_in);
+    exact = false;
+    if (J.func == 2) {
+        Enc<NL> ln2;
+        ln2_at<NL>(C, PB, ln2.lo, ln2.hi);
+        return log_enc<NL>(M, J.p, J.e_in, PB, ln2, C.div, f);
+    }
+    if (J.func == 0) return exp_small<NL>(M, q, PB, C.div, f);
+    if (q == 0 || (M & ((1ull << q) - 1)) == 0) {  // 2^X at an integer X
+        set_pow2(f.lo, PB + (unsigned)(q >= 64 ? 0 : (M >> q)));
+        f.hi = f.lo;
+        exact = true;
+        return true;
+    }
+    return exp2_arg<NL>(J, M, PB, C, f);
+}
+
+}  // namespace cf_detail
+
+template <int NL>
+TMD_HD bool job_anchor(const CoeffJob& J0, uint64_t Ma, int guard, const CoeffConsts& C, Anchor& A) {
+    static_assert(NL == ANCHOR_LIMBS, "anchors are stored with ANCHOR_LIMBS limbs");
+    A.Ma = Ma;
+    A.P = cf_detail::base_bits(J0, guard);
+    A.ok = 0;
+    if ((int)A.P + 80 > 64 * NL) return false;
+    fx::Enc<NL> f;
+    bool exact;
+    if (!cf_detail::f_direct<NL>(J0, Ma, A.P, C, f, exact)) return false;
+    for (int i = 0; i < NL; i++) {
+        A.lo[i] = f.lo.w[i];
+        A.hi[i] = f.hi.w[i];
+    }
+    A.ok = 1;
+    return true;
+}
+
+namespace cf_detail {
+
+// enclosure of f(X_t) with PB fractional bits from the anchor (false when
+// the anchor does not apply; the anchor's own block is evaluated directly)
+template <int NL>
+TMD_HD bool f_anchored(const CoeffJob& J, uint64_t M, unsigned PB, const CoeffConsts& C, const Anchor& A,
+                       fx::Enc<NL>& f) {
+    using namespace fx;
+    if (!A.ok || M <= A.Ma || A.P < PB) return false;
+    Enc<NL> a;
+    for (int i = 0; i < NL; i++) {
+        a.lo.w[i] = i < ANCHOR_LIMBS ? A.lo[i] : 0;
+        a.hi.w[i] = i < ANCHOR_LIMBS ? A.hi[i] : 0;
+    }
+    const unsigned sh = A.P - PB;
+    if (sh) {
+        const bool up = low_bits(a.hi, sh);
+        shr(a.lo, sh);
+        shr(a.hi, sh);
+        if (up) add_u64(a.hi, 1);
+    }
+    const uint64_t dM = M - A.Ma;
+    const unsigned q = (unsigned)(J.p - J.e_in);
+    if (J.func == 2) {  // log X_t = log X_a + 2 atanh(dM / (M + Ma))
+        U<NL> S;
+        uint64_t E;
+        if (!atanh_ratio<NL>(dM, M + A.Ma, PB, C.div, S, E)) return false;
+        U<NL> two_lo = S, two_hi = S;
+        add_u64(two_hi, E);
+        mul_u64(two_lo, 2);
+        mul_u64(two_hi, 2);
+        f.lo = a.lo;
+        f.hi = a.hi;
+        add(f.lo, two_lo);
+        add(f.hi, two_hi);
+        return true;
+    }
+    Enc<NL> e;  // exp(d) or exp(d ln 2)
+    if (J.func == 0) {
+        if (!exp_small<NL>(dM, q, PB, C.div, e)) return false;
+    } else {
+        const CoeffJob Jd = J;
+        if (!exp2_arg<NL>(Jd, dM, PB, C, e)) return false;
+    }
+    mul_shr(a.lo, e.lo, PB, f.lo);
+    mul_shr(a.hi, e.hi, PB, f.hi);
+    add_u64(f.hi, 1);
+    return true;
+}
+
+}  // namespace cf_detail
+
+// c[k*L + l] for k = 0..d.  Returns false when a rounding stays undecided
+// at this width (retry with a wider NL) or a width is exceeded.  With an
+// anchor of the block's job, f(X_t) comes from the anchored short series.
+template <int NL>
+TMD_HD bool block_coeffs(const CoeffJob& J, uint64_t M, int guard, const CoeffConsts& C, uint64_t* c,
+                         const Anchor* anchor = nullptr) {
     using namespace fx;
     const int W = 64 * J.L;
     const int E0 = W + J.scale_log2;
@@ -109,10 +259,13 @@ TMD_HD bool block_coeffs(const CoeffJob& J, uint64_t M, int guard, const CoeffCo
     const unsigned q = (unsigned)(J.p - J.e_in);
     if ((int)P + 96 > 64 * NL) return false;
     const uint64_t fact[5] = {1, 1, 2, 6, 24};
+    const unsigned PB = cf_detail::base_bits(J, guard);
+    Enc<NL> f;
+    bool exact = false;
+    const bool integer_x = J.func == 1 && (q == 0 || (M & ((1ull << q) - 1)) == 0);
+    if (!(anchor && !integer_x && cf_detail::f_anchored<NL>(J, M, PB, C, *anchor, f)))
+        if (!cf_detail::f_direct<NL>(J, M, PB, C, f, exact)) return false;
     if (J.func == 2) {  // log
-        Enc<NL> ln2, f;
-        cf_detail::ln2_at<NL>(C, P, ln2.lo, ln2.hi);
-        if (!log_enc<NL>(M, J.p, J.e_in, P, ln2, C.div, f)) return false;
         const int s = (int)P - E0;
         if (s < 1) return false;
         cf_detail::rn_shift(f.lo, (unsigned)s);
@@ -125,42 +278,8 @@ TMD_HD bool block_coeffs(const CoeffJob& J, uint64_t M, int guard, const CoeffCo
         }
         return true;
     }
-    // exp or 2^x: one enclosure of f(X_t) with P2 >= P fractional bits
-    const unsigned P2 = P + 16;
-    Enc<NL> f;
-    bool exact = false;
-    if (J.func == 0) {
-        if (!exp_small<NL>(M, q, P2, C.div, f)) return false;
-    } else {
-        if (q == 0 || (M & ((1ull << q) - 1)) == 0) {  // 2^X at an integer X
-            set_pow2(f.lo, P2 + (unsigned)(q >= 64 ? 0 : (M >> q)));
-            f.hi = f.lo;
-            exact = true;
-        } else {
-            U<NL> llo, lhi;
-            cf_detail::ln2_at<NL>(C, P2 + 16, llo, lhi);
-            U<NL> ylo = llo, yhi = lhi;
-            mul_u64(ylo, M);
-            shr(ylo, q);
-            mul_u64(yhi, M);
-            const bool up = low_bits(yhi, q);
-            shr(yhi, q);
-            if (up) add_u64(yhi, 1);
-            // the argument has P2 + 16 fractional bits; Xc bounds X ln 2 < 2^(e_in)
-            const uint64_t Xc = (uint64_t)1 << (J.e_in > 0 ? J.e_in : 0);
-            uint64_t e_lo, e_hi;
-            U<NL> vlo, vhi;
-            if (!exp_big<NL>(ylo, P2 + 16, Xc, C.div, vlo, e_lo)) return false;
-            if (!exp_big<NL>(yhi, P2 + 16, Xc, C.div, vhi, e_hi)) return false;
-            add_u64(vhi, e_hi);
-            shr(vlo, 16);
-            const bool up2 = low_bits(vhi, 16);
-            shr(vhi, 16);
-            if (up2) add_u64(vhi, 1);
-            f.lo = vlo;
-            f.hi = vhi;
-        }
-    }
+    // exp or 2^x: the enclosure of f(X_t) has P2 = PB fractional bits
+    const unsigned P2 = PB;
     U<NL> l2lo, l2hi;
     if (J.func == 1) cf_detail::ln2_at<NL>(C, P2, l2lo, l2hi);
     U<NL> plo = f.lo, phi = f.hi;  // f (ln 2)^k enclosure, updated per order

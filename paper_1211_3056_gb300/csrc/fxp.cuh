@@ -315,19 +315,33 @@ struct DivTable {
 // t_0 = 2^P, t_n = floor(t_{n-1} y / (2^Q n)); the truncation error of t_n
 // satisfies e_n <= e_{n-1} X / n + 1, tracked with Xc = ceil(X); once
 // t_n = 0 and n >= 2 Xc + 2 the true term is at most e_n and the tail after
-// it at most the term.  Needs 64 NL >= P + bits(y) + bits(e^X) + 2.
+// it at most the term.  Needs 64 NL >= P + bits(y) + bits(e^X) + 2.  When
+// X < 1 and Q <= 64, y / 2^Q is applied as the one-limb multiplier
+// y 2^(64-Q) followed by dropping the low limb (the same floor).
 template <int NL>
 TMD_HD bool exp_small(uint64_t y, unsigned Q, unsigned P, const DivTable& T, Enc<NL>& out) {
     const uint64_t Xc = Q >= 64 ? (y ? 1 : 0) : ((y >> Q) + ((y & ((1ull << Q) - 1)) ? 1 : 0));
+    const bool fold = Q >= 1 && (Q == 64 || (Q < 64 && (y >> Q) == 0));
+    const uint64_t yf = Q == 64 ? y : (fold ? y << (64 - Q) : 0);
     U<NL> t, S;
     set_pow2(t, P);
     S = t;
     uint64_t e = 0, E = 0;
     for (uint64_t n = 1; n <= SMALL_DIV_MAX; n++) {
-        mul_u64(t, y);
-        shr(t, Q);
+        if (fold) {
+            const uint64_t top = mul_u64(t, yf);
+#pragma unroll
+            for (int i = 0; i + 1 < NL; i++) t.w[i] = t.w[i + 1];
+            t.w[NL - 1] = top;
+        } else {
+            mul_u64(t, y);
+            shr(t, Q);
+        }
         div_u64(t, T.r[n]);
-        e = (e * Xc + n - 1) / n + 1;
+        U<1> en;
+        en.w[0] = e * Xc + n - 1;
+        div_u64(en, T.r[n]);
+        e = en.w[0] + 1;
         add(S, t);
         E += e;
         if (n >= 2 * Xc + 2 && is_zero(t)) {
@@ -393,22 +407,20 @@ TMD_HD bool ln2_enc(unsigned P, const DivTable& T, Enc<NL>& out) {
     return false;
 }
 
-// log X for X = M 2^(e_in - p), 2^(p-1) <= M < 2^p, e_in >= 1:
-// log X = e_in ln 2 - 2 atanh(z), z = (2^p - M)/(2^p + M) in (0, 1/3];
-// w_0 = floor(2^P num/den) (error <= 1), w_k = w_{k-1} z^2 by two truncating
-// multiply-divides (error <= 3), term_k = floor(w_k/(2k+1)) (error <= 2).
+// atanh(num/den) for 0 <= num < den / 3 (den < 2^62), P fractional bits:
+// S <= 2^P atanh(num/den) <= S + E.  w_0 = floor(2^P num/den) (error <= 1),
+// w_k = w_{k-1} z^2 by two truncating multiply-divides (error <= 3),
+// term_k = floor(w_k/(2k+1)) (error <= 2); the tail after a zero term is
+// below 1.
 template <int NL>
-TMD_HD bool log_enc(uint64_t M, int p, int e_in, unsigned P, const Enc<NL>& ln2, const DivTable& T,
-                    Enc<NL>& out) {
-    const uint64_t num = (1ull << p) - M, den = (1ull << p) + M;
+TMD_HD bool atanh_ratio(uint64_t num, uint64_t den, unsigned P, const DivTable& T, U<NL>& S, uint64_t& E) {
     const Recip Rd = make_recip(den);
-    U<NL> w, S;
+    U<NL> w;
     set_pow2(w, P);
     mul_u64(w, num);
     div_u64(w, Rd);
     S = w;
-    uint64_t E = 1;
-    bool done = false;
+    E = 1;
     for (uint64_t k = 1; 2 * k + 1 <= SMALL_DIV_MAX; k++) {
         mul_u64(w, num);
         div_u64(w, Rd);
@@ -420,11 +432,20 @@ TMD_HD bool log_enc(uint64_t M, int p, int e_in, unsigned P, const Enc<NL>& ln2,
         E += 2;
         if (is_zero(t)) {
             E += 1;
-            done = true;
-            break;
+            return true;
         }
     }
-    if (!done) return false;
+    return false;
+}
+
+// log X for X = M 2^(e_in - p), 2^(p-1) <= M < 2^p, e_in >= 1:
+// log X = e_in ln 2 - 2 atanh(z), z = (2^p - M)/(2^p + M) in (0, 1/3].
+template <int NL>
+TMD_HD bool log_enc(uint64_t M, int p, int e_in, unsigned P, const Enc<NL>& ln2, const DivTable& T,
+                    Enc<NL>& out) {
+    U<NL> S;
+    uint64_t E;
+    if (!atanh_ratio<NL>((1ull << p) - M, (1ull << p) + M, P, T, S, E)) return false;
     U<NL> two_hi = S, two_lo = S;
     add_u64(two_hi, E);
     mul_u64(two_hi, 2);

@@ -564,12 +564,23 @@ CoeffJob coeff_job(const tmd_job& job, int e_out) {
     return J;
 }
 
-tmd_status block_table(const tmd_job& job, const BlockPlan& blk, uint64_t* coeffs, uint64_t* table) {
+void host_anchor(const tmd_job& job, const std::vector<Segment>& segs, Anchor* A) {
+    A->ok = 0;
+    if (segs.empty()) return;
+    uint64_t nb = 0, ns = 0;
+    plan_counts(job, segs, &nb, &ns);
+    if (nb < 2) return;
+    job_anchor<ANCHOR_LIMBS>(coeff_job(job, segs[0].e_out), arg_mantissa(job, segs[0].j0), 64, coeff_consts(), *A);
+}
+
+tmd_status block_table(const tmd_job& job, const BlockPlan& blk, uint64_t* coeffs, uint64_t* table,
+                       const Anchor* anchor) {
     const CoeffJob J = coeff_job(job, blk.e_out);
     const uint64_t M = arg_mantissa(job, blk.start);
     uint64_t c[(MAX_DEG + 1) * MAX_LIMBS];
-    // Ziv: 512-bit words with 64 guard bits, then 768-bit words with 320
-    if (!block_coeffs<8>(J, M, 64, coeff_consts(), c) && !block_coeffs<12>(J, M, 320, coeff_consts(), c))
+    // Ziv: 512-bit words with 64 guard bits (from the anchor when there is
+    // one), then 768-bit words with 320 computed directly
+    if (!block_coeffs<8>(J, M, 64, coeff_consts(), c, anchor) && !block_coeffs<12>(J, M, 320, coeff_consts(), c))
         return TMD_EUNSUPPORTED;
     if (coeffs)
         for (int i = 0; i < (job.d + 1) * (int)job.limbs; i++) coeffs[i] = c[i];

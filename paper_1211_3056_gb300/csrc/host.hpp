@@ -40,10 +40,16 @@ bool plan_block(const tmd_job& job, const std::vector<Segment>& segs, uint64_t b
 // log2 of the breakpoint scale s on a segment with output exponent e_out.
 int scale_log2(const tmd_job& job, int e_out);
 
+struct Anchor;
+// Enclosure of f at the job's first argument, at the precision of its first
+// segment (A->ok = 0 when it cannot be formed or the job has one block).
+void host_anchor(const tmd_job& job, const std::vector<Segment>& segs, Anchor* A);
+
 // Coefficients c_0..c_d (limbs each, little-endian) and the 2d+1 table words
-// of the block.  TMD_EUNSUPPORTED if the rounding could not be decided.
+// of the block, from the job's anchor when given.  TMD_EUNSUPPORTED if the
+// rounding could not be decided.
 tmd_status block_table(const tmd_job& job, const BlockPlan& blk, uint64_t* coeffs,
-                       uint64_t* table);
+                       uint64_t* table, const Anchor* anchor = nullptr);
 
 struct CoeffConsts;
 // Constants of the coefficient routine (divisor reciprocals, ln 2), computed

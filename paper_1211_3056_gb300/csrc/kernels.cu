@@ -660,37 +660,55 @@ cudaError_t launch_plan(const DevJob* jobs, uint32_t n_jobs, DevBlock* blocks, u
 // ---------------------------------------------------------- block tables
 // One thread per Taylor block: correctly rounded coefficients of R_t and the
 // 2d+1 step-N difference words (the host path runs the same routine).  Pass
-// 0 works with 512-bit words and 64 guard bits; pass 1 redoes only the blocks
-// left undecided with 768-bit words and 320 guard bits (Ziv); a block still
-// undecided raises ERR_ROUNDING in the error word.
+// 0 works with 512-bit words and 64 guard bits; pass 1, a kernel of its own
+// (its 768-bit code stays out of pass 0's instruction cache), redoes only
+// the blocks left undecided with 320 guard bits (Ziv); a block still
+// undecided raises ERR_ROUNDING in the error word.  (The per-job anchors of
+// the host path are not used here: on the device the anchor's own
+// evaluation would sit in front of every block's on the critical path.)
 __constant__ CoeffConsts c_coeff;
 
-__global__ void __launch_bounds__(128) k_block_tables(const DevJob* jobs, const DevBlock* blocks,
-                                                      uint64_t n_blocks, uint64_t* tables,
-                                                      uint32_t* status, int pass, uint32_t* err) {
-    const uint64_t b = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (b >= n_blocks) return;
-    if (pass == 1 && status[b] == 0) return;
-    const DevBlock bk = blocks[b];
-    const DevJob jb = jobs[bk.job];
+__device__ __forceinline__ CoeffJob block_coeff_job(const DevJob& jb, int e_out) {
     CoeffJob J;
     J.func = jb.func;
     J.e_in = jb.e_in;
     J.p = jb.p;
     J.d = (int)jb.d;
     J.L = (int)jb.L;
-    J.scale_log2 = (jb.flags & TMD_BP_DIRECTED) ? jb.p - bk.e_out : jb.p + 1 - bk.e_out;
+    J.scale_log2 = (jb.flags & TMD_BP_DIRECTED) ? jb.p - e_out : jb.p + 1 - e_out;
     J.log2_N = (int)jb.log2_N;
+    return J;
+}
+
+__global__ void __launch_bounds__(64) k_block_tables(const DevJob* jobs, const DevBlock* blocks, uint64_t n_blocks,
+                                                     uint64_t* tables, uint32_t* status) {
+    const uint64_t b = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (b >= n_blocks) return;
+    const DevBlock bk = blocks[b];
+    const DevJob jb = jobs[bk.job];
+    const CoeffJob J = block_coeff_job(jb, bk.e_out);
     const uint64_t M = (1ull << (jb.p - 1)) + bk.start;
     uint64_t c[(COEFF_MAX_DEG + 1) * COEFF_MAX_LIMBS];
-    const bool ok = pass == 0 ? block_coeffs<8>(J, M, 64, c_coeff, c)
-                              : block_coeffs<12>(J, M, 320, c_coeff, c);
-    if (ok) {
+    const bool ok = block_coeffs<8>(J, M, 64, c_coeff, c);
+    if (ok) block_table_words(J, c, tables + bk.table_off);
+    status[b] = ok ? 0 : 1;
+}
+
+__global__ void __launch_bounds__(64) k_block_tables_wide(const DevJob* jobs, const DevBlock* blocks,
+                                                          uint64_t n_blocks, uint64_t* tables, uint32_t* status,
+                                                          uint32_t* err) {
+    const uint64_t b = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (b >= n_blocks || status[b] == 0) return;
+    const DevBlock bk = blocks[b];
+    const DevJob jb = jobs[bk.job];
+    const CoeffJob J = block_coeff_job(jb, bk.e_out);
+    const uint64_t M = (1ull << (jb.p - 1)) + bk.start;
+    uint64_t c[(COEFF_MAX_DEG + 1) * COEFF_MAX_LIMBS];
+    if (block_coeffs<12>(J, M, 320, c_coeff, c)) {
         block_table_words(J, c, tables + bk.table_off);
         status[b] = 0;
     } else {
-        status[b] = 1;
-        if (pass == 1) atomicOr(err, (uint32_t)ERR_ROUNDING);
+        atomicOr(err, (uint32_t)ERR_ROUNDING);
     }
 }
 
@@ -698,16 +716,14 @@ cudaError_t upload_coeff_consts(const CoeffConsts& C) {
     return cudaMemcpyToSymbol(c_coeff, &C, sizeof C);
 }
 
-cudaError_t launch_block_tables(const DevJob* jobs, const DevBlock* blocks, uint64_t n_blocks,
-                                uint64_t* tables, uint32_t* status, uint32_t* err, cudaStream_t s) {
+cudaError_t launch_block_tables(const DevJob* jobs, const DevBlock* blocks, uint64_t n_blocks, uint64_t* tables,
+                                uint32_t* status, uint32_t* err, cudaStream_t s) {
     if (n_blocks == 0) return cudaSuccess;
-    const unsigned grid = (unsigned)((n_blocks + 127) / 128);
-    for (int pass = 0; pass < 2; pass++) {
-        k_block_tables<<<grid, 128, 0, s>>>(jobs, blocks, n_blocks, tables, status, pass, err);
-        cudaError_t e = cudaGetLastError();
-        if (e != cudaSuccess) return e;
-    }
-    return cudaSuccess;
+    // 64-thread CTAs spread the (few, long) threads over more SMs
+    const unsigned grid = (unsigned)((n_blocks + 63) / 64);
+    k_block_tables<<<grid, 64, 0, s>>>(jobs, blocks, n_blocks, tables, status);
+    k_block_tables_wide<<<grid, 64, 0, s>>>(jobs, blocks, n_blocks, tables, status, err);
+    return cudaGetLastError();
 }
 
 // --------------------------------------------------------------- launchers

@@ -6,14 +6,18 @@ of 2^24 arguments in 192-bit fixed point, sub-intervals of N = 2^14
 arguments, threshold m = 40: packet starts, tabulated-difference stepping,
 Algorithm 4 filter, exact resolution and compaction over all 2^22 lines.
 
-  value   device throughput of the fused step (tables resident in HBM when
-          the timed region starts), arguments / s, whole job over all ranks.
-  plain   the same work as two launches (generate lines to HBM, then search
-          them), for the batched-vs-plain comparison.
-  e2e     the public C-ABI call from host job descriptors to the sorted host
-          candidate list: host planning and correctly rounded tables, the
-          host->device upload of the tables, the kernel, the device->host
-          read of the count and records, every step.
+  value    device throughput of the batched form: the persistent work-queue
+           kernel replayed as a CUDA graph, plan and tables resident in HBM
+           when the timed region starts; arguments / s, whole job over all
+           ranks.
+  plain    the same work as one fused per-job launch (tmd_search).
+  unfused  the same work as two launches (generate lines to HBM, then search
+           them).
+  e2e      the public C-ABI call from host job descriptors to the sorted
+           host candidate list, every step: host planning (output-binade
+           cuts), the host->device copy of the job records, the device
+           planning and correctly rounded table kernels, the search kernel,
+           the device->host read of the count and records.
 
 Between timed steps a 256 MiB buffer (> the 129 MB L2) is written so that no
 step starts with a warm L2.  `--impl reference` times the CPU oracle instead
@@ -54,6 +58,12 @@ ISSUE_PEAK_OPS = SMS * LANES_PER_SM * SM_MAX_HZ
 #                   quotient estimates, two 64x32 multiply-subtracts, two
 #                   corrections, the u/v update, the exit test).
 OPS_PER_HALF_STEP = 35
+
+# DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of one launch of
+# k_persistent<3,3> on this 2^36 workload, from one single-pass ncu capture of
+# the kernel as it stands (1,347,072 read + 59,136 written); to be reset to
+# None whenever that kernel changes.
+TRAFFIC_BYTES_PER_LAUNCH = 1_406_208
 
 
 def ops_per_line(job) -> int:
@@ -359,6 +369,7 @@ def main():
     h2d = 0
     for k in range(args.e2e_steps + 1):
         tmd.tmd_evict(ctx)
+        flush.fill_(1)
         torch.cuda.synchronize()
         barrier()
         t0 = time.perf_counter()
@@ -377,7 +388,8 @@ def main():
     achieved = alg_ops / (statistics.mean(batched_ms) / 1e3)
     roofline = {"bound": "alu", "achieved": achieved / 1e12, "peak": ISSUE_PEAK_OPS / 1e12,
                 "unit": "Tops/s", "frac": achieved / ISSUE_PEAK_OPS,
-                "traffic": None,
+                "traffic": TRAFFIC_BYTES_PER_LAUNCH if args.count_log2 == 36 else None,
+                "traffic_unit": "bytes per launch (ncu DRAM read + write)",
                 "peak_note": "derived: 152 SMs x 128 lanes x 2.07 GHz (issue ceiling, of derived)",
                 "half_steps_per_line": stats["half_steps"] / max(1, stats["lines"]),
                 "filter_fail_per_line": stats["filter_fail"] / max(1, stats["lines"])}

@@ -414,30 +414,42 @@ __device__ __forceinline__ void packet_words(const Packet<L, D>& P, uint32_t m, 
 // Lines per packet held in shared memory between the two phases of a task.
 constexpr int NU_MAX = 8;
 constexpr int WARPS_PER_CTA = 8;
+constexpr int TASK_LINES = 32 * NU_MAX;
+
+// Line s of a task (packet s / nu, line s % nu of that packet) sits at
+// stage_slot(s): one padding slot per 32 keeps both the packet-major writes
+// of phase 1 (stride nu between lanes) and the line-major reads of phase 2
+// (stride 1) free of shared-memory bank conflicts.
+__device__ __forceinline__ int stage_slot(int s) { return s + (s >> 5); }
 
 struct LineStage {
-    uint64_t B[NU_MAX][32];
-    uint64_t A[NU_MAX][32];
-    uint32_t n[NU_MAX][32];   // arguments of the line; 0 = no line
+    uint64_t B[TASK_LINES + TASK_LINES / 32];
+    uint64_t A[TASK_LINES + TASK_LINES / 32];
+    uint32_t n[TASK_LINES + TASK_LINES / 32];   // arguments of the line; 0 = no line
+    uint32_t blk[32];                            // block of each packet
+    uint32_t i0[32];                             // first sub-interval of each packet in its block
 };
 
-// Phase 1 steps the packet's tabulated differences and parks the search words
-// and lengths of its nu lines in shared memory; phase 2 runs the search on
-// them with only the continued-fraction state live (the W-bit packet state
-// and the block record are dead by then), so the search loop is not starved
-// of registers.  Block fields are reloaded only on the rare resolve path.
+// Phase 1: each lane steps the tabulated differences of its packet and parks
+// the search words and lengths of its nu lines in shared memory.  Phase 2:
+// the warp searches the task's lines 32 at a time in sub-interval order, so
+// that the 32 lines searched together are neighbouring sub-intervals: their
+// slopes differ in the low bits only, their continued fractions share all
+// but the last partial quotients, and the lanes take the same branches of
+// the search loop.  Only the search state is live in phase 2 (the W-bit
+// packet state is dead by then); block fields are reloaded only on the rare
+// resolve path.
 template <int L, int D>
 __device__ __forceinline__ void fused_task(const DevTask& t, const LaunchArgs& a, LineStage& st,
                                            uint32_t& st_lines, uint32_t& st_fail, uint32_t& st_half) {
     const int lane = threadIdx.x & 31;
     const uint32_t nu = a.jobs[t.job].nu;
-    uint32_t b, i0;
     {
         const DevJob job = a.jobs[t.job];
         Packet<L, D> P;
         const uint32_t bi = packet_init<L, D>(P, t, job, a);
-        b = bi;
-        i0 = P.i0;
+        st.blk[lane] = bi;
+        st.i0[lane] = P.i0;
         const uint32_t N = 1u << job.log2_N;
 #pragma unroll 1
         for (uint32_t it = 0; it < nu; it++) {
@@ -445,19 +457,22 @@ __device__ __forceinline__ void fused_task(const DevTask& t, const LaunchArgs& a
             packet_words<L, D>(P, job.m, B, A);
             const uint32_t i = P.i0 + it;
             const bool valid = P.active && i < P.i1;
-            st.B[it][lane] = B;
-            st.A[it][lane] = A;
-            st.n[it][lane] = valid ? (uint32_t)min((uint64_t)N, P.blk.length - (uint64_t)i * N) : 0u;
+            const int s = stage_slot(lane * (int)nu + (int)it);
+            st.B[s] = B;
+            st.A[s] = A;
+            st.n[s] = valid ? (uint32_t)min((uint64_t)N, P.blk.length - (uint64_t)i * N) : 0u;
             packet_step<L, D>(P);
         }
     }
     __syncwarp();
     const uint64_t Tm = a.jobs[t.job].Tm;
 #pragma unroll 1
-    for (uint32_t it = 0; it < nu; it++) {
-        const uint32_t n = st.n[it][lane];
-        const uint64_t B = st.B[it][lane];
-        const uint64_t A = st.A[it][lane];
+    for (uint32_t r = 0; r < nu; r++) {
+        const int s = (int)r * 32 + lane;
+        const int slot = stage_slot(s);
+        const uint32_t n = st.n[slot];
+        const uint64_t B = st.B[slot];
+        const uint64_t A = st.A[slot];
         uint32_t hs = 0;
         uint64_t lb = ~0ull;
         if (n) lb = cf_lower_bound(B, A, n, &hs);
@@ -466,9 +481,10 @@ __device__ __forceinline__ void fused_task(const DevTask& t, const LaunchArgs& a
         st_fail += fail ? 1u : 0u;
         st_half += hs;
         if (__any_sync(FULLMASK, fail)) {
-            const DevBlock& bk = a.blocks[b];
+            const uint32_t pk = (uint32_t)s / nu;
+            const uint32_t i = st.i0[pk] + (uint32_t)s % nu;
+            const DevBlock& bk = a.blocks[st.blk[pk]];
             const DevJob& jb = a.jobs[t.job];
-            const uint32_t i = i0 + it;
             resolve_and_emit(fail, B, A, n ? n : 1u, Tm, (jb.flags & TMD_ALL_HITS) != 0, t.job,
                              (uint32_t)(bk.first_sub + i), bk.start + ((uint64_t)i << jb.log2_N),
                              a.cand, a.cap, a.count);

@@ -8,6 +8,7 @@ import pytest
 from gpu_util import to_u32_list, to_u64_list, u32_tensor, u64_tensor
 from oracle import candidates as oc
 from oracle import search
+import workloads as wl
 
 torch = pytest.importorskip("torch")
 tmd = pytest.importorskip("paper_1211_3056_gb300")
@@ -75,6 +76,76 @@ def test_lower_bound_equals_algorithm4_random(ctx):
     for (B, A, n), g, h in zip(lines, lb, hs):
         want, _, whs = search.regular_lb_unrolled(B, A, n)
         assert (g, h) == (want, whs), (hex(B), hex(A), n)
+
+
+def clustered_lines(n_warps, seed):
+    """Warps of 32 lines whose slopes lie close together, as neighbouring
+    sub-intervals of one job do (their continued fractions share all but
+    the last partial quotients): spreads from 0 to the whole circle, slopes
+    near 0 (huge first quotient) and with trailing zero bits (the expansion
+    ends early), shuffled lanes, equal and mixed lengths, and a zero slope
+    among close ones."""
+    rng = random.Random(seed)
+    out = []
+    for w in range(n_warps):
+        kind = w % 8
+        A0 = rng.getrandbits(64)
+        if kind == 5:
+            A0 = rng.getrandbits(rng.randrange(1, 50))
+        spread = rng.choice([0, 1, 1 << rng.randrange(0, 48), rng.getrandbits(rng.randrange(1, 64))])
+        As = [(A0 + l * spread) & M64 for l in range(32)]
+        if kind == 4:
+            z = rng.randrange(0, 60)
+            As = [a & ~((1 << z) - 1) & M64 for a in As]
+        if kind == 6:
+            rng.shuffle(As)
+        if kind == 7:
+            As[rng.randrange(32)] = 0
+        mode = rng.randrange(4)
+        if mode == 0:
+            ns = [1 << 14] * 32
+        elif mode == 1:
+            ns = [rng.choice([1, 2, 3, 100, 4096, 1 << 14, 1 << 16]) for _ in range(32)]
+        elif mode == 2:
+            ns = [1 << 16] * 31 + [rng.randrange(1, 1 << 16)]
+        else:
+            ns = [rng.choice([1 << 12, 1 << 16])] * 32
+        out += [(rng.getrandbits(64), a, nn) for a, nn in zip(As, ns)]
+    return out
+
+
+def test_lower_bound_equals_algorithm4_clustered(ctx):
+    lines = clustered_lines(1500, 17)
+    lb, hs = run_lower_bounds(ctx, lines)
+    for (B, A, n), g, h in zip(lines, lb, hs):
+        want, _, whs = search.regular_lb_unrolled(B, A, n)
+        assert (g, h) == (want, whs), (hex(B), hex(A), n)
+
+
+@pytest.mark.parametrize("job", [
+    wl.plain_job(m=40, count_log2=30),
+    wl.Job(wl.FUNC_LOG, 3, 53, 40, 16, 2, 18, 3, 1 << 44, 1 << 30),
+    wl.Job(wl.FUNC_EXP2, 1, 53, 40, 12, 3, 24, 3, 3 << 48, 1 << 28),
+], ids=["exp-N14", "log-N16", "exp2-N12"])
+def test_lower_bound_on_generated_lines(ctx, job):
+    """Lines of real jobs, generated on the device: bound and half-step
+    count compared line by line with Algorithm 4 on a sample of warps."""
+    need = tmd.tmd_generate(ctx, [job], None)
+    d_lin = torch.empty(need // 8, dtype=torch.int64, device="cuda:0")
+    tmd.tmd_generate(ctx, [job], d_lin)
+    half = d_lin.numel() // 2
+    B, A = d_lin[:half].contiguous(), d_lin[half:].contiguous()
+    n = torch.full((half,), 1 << job.log2_N, dtype=torch.int32, device="cuda:0")
+    lb = torch.empty_like(B)
+    hs = torch.empty_like(n)
+    tmd.tmd_lower_bounds(ctx, B, A, n, lb, hs)
+    Bh, Ah = to_u64_list(B), to_u64_list(A)
+    lbh, hsh = to_u64_list(lb), to_u32_list(hs)
+    rng = random.Random(job.count)
+    for w in rng.sample(range(half // 32), 300):
+        for s in range(32 * w, 32 * w + 32):
+            want, _, whs = search.regular_lb_unrolled(Bh[s], Ah[s], 1 << job.log2_N)
+            assert (lbh[s], hsh[s]) == (want, whs), s
 
 
 def brute_records(lines, m, all_hits=False):

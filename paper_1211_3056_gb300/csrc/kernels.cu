@@ -270,17 +270,171 @@ __device__ __forceinline__ void emit_warp(bool has, uint32_t job, uint32_t sub, 
     }
 }
 
-// Exact resolution of the flagged lines of a warp, one line at a time by all
-// 32 lanes (x = lane, lane + 32, ...), then compaction.
+// ------------------------------------------------------- exact minimum
+// floor(x / b) for any b > 0: FP32 estimates that never exceed the quotient
+// (round-toward-zero conversions, a reciprocal biased down by 2^-20), each
+// removing ~20 bits of it, then compare-and-subtract; *r = x mod b.
+__device__ __forceinline__ uint64_t udivmod64(uint64_t x, uint64_t b, uint64_t* r) {
+    const float rb = scaled_rcp(u64_to_f32_rz(b));
+    uint64_t q = 0;
+#pragma unroll 1
+    for (int it = 0; it < 6 && x >= b; it++) {
+        const float kf = u64_to_f32_rz(x) * rb;  // <= x / b
+        uint64_t t;
+        if (kf < 4194304.0f)
+            t = (uint64_t)(__float_as_uint(__fadd_rz(kf, 8388608.0f)) - 0x4B000000u);
+        else
+            t = __float2ull_rz(kf);
+        if (t == 0) t = 1;  // x >= b here, so floor(x / b) >= 1
+        x -= t * b;
+        q += t;
+    }
+    if (x >= b) {  // not reached for b >= 1 (each pass leaves x < 2^-19 x + 2b)
+        uint32_t k;
+        x = divmod_slow(x, b, k);
+        q = ~0ull;
+    }
+    *r = x;
+    return q;
+}
+
+// floor((hi 2^64 + lo) / m) for a quotient known to be below 2^16 (m > 0).
+__device__ __forceinline__ uint64_t udiv128_small(uint64_t hi, uint64_t lo, uint64_t m) {
+    const float nf = __fmaf_rz((float)hi, 18446744073709551616.0f, u64_to_f32_rz(lo));  // <= value
+    const float kf = nf * scaled_rcp(u64_to_f32_rz(m));                               // <= quotient
+    uint64_t t = (uint64_t)(__float_as_uint(__fadd_rz(kf, 8388608.0f)) - 0x4B000000u);
+    // remainder (hi:lo) - t m, then at most a few compare-and-subtracts
+    uint64_t plo = t * m, phi = __umul64hi(t, m);
+    uint64_t rlo = lo - plo, rhi = hi - phi - (lo < plo ? 1ull : 0ull);
+#pragma unroll 1
+    for (int it = 0; it < 4 && (rhi != 0 || rlo >= m); it++) {
+        rhi -= rlo < m ? 1ull : 0ull;
+        rlo -= m;
+        t++;
+    }
+    return t;
+}
+
+// Exact min_{0<=x<n} (B - A x) mod 2^64 and its smallest argmin (n >= 1),
+// without visiting the n points.  The sequence y_x = (b - c x) mod m falls
+// by c until it wraps, so only the ends of its runs and its last point can
+// be minima; the value at the end of run w is (b + w m) mod c -- a rising
+// sequence modulo c.  A rising sequence (b + a x) mod m can only have its
+// minimum at x = 0 or just after a wrap, and the value after wrap k is
+// (b - k m) mod a -- a falling sequence modulo a.  Each form hands the next
+// the same candidate values on a smaller modulus (m, c) -> (c, m mod c), the
+// Euclidean algorithm, with fewer points; a running minimum of the direct
+// candidates is the answer.  The smallest argmin then follows from
+// A x = B - min (mod 2^64): with A = 2^t A', x = ((B - min) / 2^t) A'^-1
+// mod 2^(64-t), the least solution, which lies below n.
+__device__ __noinline__ uint64_t exact_min(uint64_t B, uint64_t A, uint32_t n, uint32_t* argmin) {
+    if (A == 0 || n <= 1) {
+        *argmin = 0;
+        return B;
+    }
+    // level 0, falling form with modulus 2^64: runs end where the subtraction wraps
+    uint64_t best;
+    uint64_t m, c, b, cnt;
+    {
+        const uint64_t Tl = A * (uint64_t)(n - 1), Th = __umul64hi(A, (uint64_t)(n - 1));
+        best = B - Tl;  // last point
+        uint64_t W = 0;
+        if (Th != 0 || Tl > B) {  // W = ceil((T - B) / 2^64)
+            const uint64_t dl = Tl - B, dh = Th - (Tl < B ? 1ull : 0ull);
+            W = dh + (dl != 0 ? 1ull : 0ull);
+        }
+        cnt = W;
+        if (cnt) {
+            // rising form: (B mod A + w (2^64 mod A)) mod A, w < W
+            uint64_t bm, mm;
+            udivmod64(B, A, &bm);
+            udivmod64(0ull - A, A, &mm);  // 2^64 mod A = (2^64 - A) mod A
+            m = A;
+            c = mm;
+            b = bm;
+        }
+    }
+    bool rising = true;
+#pragma unroll 1
+    for (int level = 0; level < 200 && cnt != 0; level++) {
+        if (rising) {
+            // (b + a x) mod m, x < cnt, a = c: minimum at x = 0 or after a wrap
+            best = b < best ? b : best;
+            const uint64_t a = c;
+            if (a == 0) break;
+            // K = floor((b + a (cnt - 1)) / m) wraps
+            uint64_t lo = a * (cnt - 1), hi = __umul64hi(a, cnt - 1);
+            lo += b;
+            hi += lo < b ? 1ull : 0ull;
+            const uint64_t K = udiv128_small(hi, lo, m);
+            if (K == 0) break;
+            // after wrap k: (b - k m) mod a = (b mod a - (k mod ...) ) -> falling form
+            uint64_t bm, mm;
+            udivmod64(b, a, &bm);
+            udivmod64(m, a, &mm);
+            const uint64_t b2 = bm >= mm ? bm - mm : bm + (a - mm);  // (b - m) mod a
+            cnt = K;
+            m = a;
+            c = mm;
+            b = b2;
+            rising = false;
+        } else {
+            // (b - c x) mod m, x < cnt: minimum at the end of a run or at the last point
+            if (c == 0) {
+                best = b < best ? b : best;
+                break;
+            }
+            const uint64_t Tl = c * (cnt - 1), Th = __umul64hi(c, cnt - 1);
+            uint64_t W = 0;
+            if (Th != 0 || Tl > b) {  // W = ceil((T - b) / m) = floor((T - b - 1) / m) + 1
+                uint64_t dl = Tl - b, dh = Th - (Tl < b ? 1ull : 0ull);
+                dh -= dl == 0 ? 1ull : 0ull;
+                dl -= 1;
+                W = udiv128_small(dh, dl, m) + 1;
+            }
+            const uint64_t last = b + W * m - Tl;  // exact, below m
+            best = last < best ? last : best;
+            if (W == 0) break;
+            uint64_t bm, mm;
+            udivmod64(b, c, &bm);
+            udivmod64(m, c, &mm);
+            cnt = W;
+            m = c;
+            c = mm;
+            b = bm;
+            rising = true;
+        }
+    }
+    // least x with A x = B - best (mod 2^64)
+    const int t = __ffsll((long long)A) - 1;
+    const uint64_t ao = A >> t;
+    uint64_t inv = ao;  // correct to 3 bits; each Newton step doubles that
+#pragma unroll
+    for (int i = 0; i < 5; i++) inv *= 2ull - ao * inv;
+    uint64_t x = ((B - best) >> t) * inv;
+    if (t > 0) x &= (~0ull) >> t;
+    *argmin = (uint32_t)x;
+    return best;
+}
+
+// Exact resolution of the flagged lines of a warp, then compaction.  Each
+// flagged lane finds its line's minimum and smallest argmin by exact_min;
+// in all-hits mode every argument of each flagged line is visited by the
+// whole warp (x = lane, lane + 32, ...) and every one below the threshold
+// is reported.
 __device__ __noinline__ void resolve_and_emit(bool fail, uint64_t B, uint64_t A, uint32_t n,
                                               uint64_t Tm, bool all_hits, uint32_t job,
                                               uint32_t sub, uint64_t arg_base,
                                               tmd_candidate* cand, uint64_t cap, uint64_t* count) {
+    if (!all_hits) {
+        uint64_t mn = 0;
+        uint32_t x = 0;
+        if (fail) mn = exact_min(B, A, n, &x);
+        emit_warp(fail && mn < Tm, job, sub, arg_base + x, mn, cand, cap, count);
+        return;
+    }
     const int lane = threadIdx.x & 31;
     unsigned fails = __ballot_sync(FULLMASK, fail);
-    bool have = false;
-    uint64_t my_min = 0;
-    uint32_t my_x = 0;
     while (fails) {
         const int src = __ffs(fails) - 1;
         fails &= fails - 1u;
@@ -290,37 +444,15 @@ __device__ __noinline__ void resolve_and_emit(bool fail, uint64_t B, uint64_t A,
         const uint32_t js = __shfl_sync(FULLMASK, job, src);
         const uint32_t ss = __shfl_sync(FULLMASK, sub, src);
         const uint64_t ab = __shfl_sync(FULLMASK, arg_base, src);
-        uint64_t best = ~0ull;
-        uint32_t bx = 0xffffffffu;
         uint64_t val = Bs - As * (uint64_t)lane;
         const uint64_t step = As * 32ull;
         const uint32_t trips = (ns + 31u) >> 5;
         for (uint32_t t = 0; t < trips; t++) {
             const uint32_t x = t * 32u + (uint32_t)lane;
-            const bool ok = x < ns;
-            if (ok && val < best) {
-                best = val;
-                bx = x;
-            }
-            if (all_hits) emit_warp(ok && val < Tm, js, ss, ab + x, val, cand, cap, count);
+            emit_warp(x < ns && val < Tm, js, ss, ab + x, val, cand, cap, count);
             val -= step;
         }
-#pragma unroll
-        for (int off = 16; off; off >>= 1) {
-            uint64_t ob = __shfl_xor_sync(FULLMASK, best, off);
-            uint32_t ox = __shfl_xor_sync(FULLMASK, bx, off);
-            if (ob < best || (ob == best && ox < bx)) {
-                best = ob;
-                bx = ox;
-            }
-        }
-        if (lane == src) {
-            have = true;
-            my_min = best;
-            my_x = bx;
-        }
     }
-    if (!all_hits) emit_warp(have && my_min < Tm, job, sub, arg_base + my_x, my_min, cand, cap, count);
 }
 
 __device__ __forceinline__ void flush_stats(uint64_t* stats, uint32_t lines, uint32_t fail, uint32_t half) {

@@ -166,7 +166,7 @@ def sort_by_line(recs):
     return sorted(recs, key=lambda r: (r[1], r[2], r[3]))
 
 
-@pytest.mark.parametrize("m", [6, 10, 20])
+@pytest.mark.parametrize("m", [2, 6, 10, 20])
 def test_search_lines_match_brute_force(ctx, m):
     lines = random_lines(3000, 100 + m) + edge_lines()
     B = u64_tensor([l[0] for l in lines])
@@ -184,6 +184,37 @@ def test_search_lines_match_brute_force(ctx, m):
     T = 1 << (65 - m)
     flagged = sum(1 for (Bv, Av, nv) in lines if search.regular_lb_unrolled(Bv, Av, nv)[0] < T)
     assert st["filter_fail"] == flagged
+
+
+def exact_min_hard_lines(seed):
+    """Lines for the exact minimum: slopes with every count of trailing zero
+    bits (periodic point sets, tied minima: the smallest argmin is the
+    reported one), tiny slopes (huge quotients in the recursion), slopes
+    next to 2^64, and the extreme offsets, at the longest length."""
+    rng = random.Random(seed)
+    out = []
+    for t in range(64):
+        for _ in range(3):
+            A = ((rng.getrandbits(64 - t) | 1) << t) & M64
+            out.append((rng.getrandbits(64), A, rng.choice([1 << 16, 1 << 14, 777, 2])))
+    for A in list(range(1, 40)) + [M64 - k for k in range(40)] + [1 << 32, (1 << 32) + 1, 3 << 62]:
+        out.append((rng.choice([0, 1, M64, rng.getrandbits(64)]), A, 1 << 16))
+    return out
+
+
+def test_exact_minimum_on_hard_lines(ctx):
+    """m = 2 flags nearly every line, so every line goes through the exact
+    minimum; records must equal brute force (value and smallest argmin)."""
+    lines = exact_min_hard_lines(11)
+    B = u64_tensor([l[0] for l in lines])
+    A = u64_tensor([l[1] for l in lines])
+    n = u32_tensor([l[2] for l in lines])
+    d_cand, d_count = tmd.alloc_candidates(len(lines) + 16)
+    tmd.tmd_search_lines(ctx, B, A, n, 2, 0, d_cand, d_count)
+    got, count = tmd.tmd_candidates(ctx, d_cand, d_count)
+    want = brute_records(lines, 2)
+    assert count == len(want) > 0.8 * len(lines)
+    assert sort_by_line(got) == sort_by_line(want)
 
 
 def test_search_lines_all_hits(ctx):

@@ -61,9 +61,9 @@ OPS_PER_HALF_STEP = 35
 
 # DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of one launch of
 # k_persistent<3,3> on this 2^36 workload, from one single-pass ncu capture of
-# the kernel as it stands (1,347,072 read + 59,136 written); to be reset to
-# None whenever that kernel changes.
-TRAFFIC_BYTES_PER_LAUNCH = 1_406_208
+# the kernel as it stands; None until the kernel's current form is captured,
+# and reset to None whenever that kernel changes.
+TRAFFIC_BYTES_PER_LAUNCH = None
 
 
 def ops_per_line(job) -> int:
@@ -272,6 +272,8 @@ def main():
                     help="jobs of the seeded serving stream to serve (0 = skip)")
     ap.add_argument("--count-log2", type=int, default=36,
                     help="slice size (smaller only for profiling captures)")
+    ap.add_argument("--tiling", default="auto",
+                    help="'auto' (tmd_autotune picks it) or 'nu,ctas_per_sm' for the batched form")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     if args.impl == "reference":
@@ -309,9 +311,17 @@ def main():
     def fused_step():
         tmd.tmd_search(ctx, [job], None, d_cand, d_count)
 
-    # batched form: the persistent work-queue kernel, captured once as a graph
+    # batched form: the persistent work-queue kernel, captured once as a
+    # graph, with the tiling the autotuner picks for this batch (untimed)
+    if args.tiling == "auto":
+        tuned = tmd.tmd_autotune(ctx, [job])
+        tiling = None
+    else:
+        nu, per_sm = (int(v) for v in args.tiling.split(","))
+        tuned = {"nu": nu, "ctas_per_sm": per_sm, "ms": None}
+        tiling = (nu, per_sm)
     d_cand_b, d_count_b = tmd.alloc_candidates(cap, local_rank)
-    batch = tmd.Batch(ctx, [job], d_cand_b, d_count_b)
+    batch = tmd.Batch(ctx, [job], d_cand_b, d_count_b, tiling=tiling)
 
     def batched_step():
         batch.launch()
@@ -337,6 +347,9 @@ def main():
         torch.cuda.synchronize()
         barrier()
         return [e0.elapsed_time(e1) for e0, e1 in evs]
+
+    # measured issue rates of the pipes (lane-operations per SM per clock)
+    pipe_rates = tmd.tmd_pipe_rates(local_rank)
 
     sampler = ClockSampler(cuda_index(local_rank))
     sampler.start()
@@ -390,7 +403,11 @@ def main():
                 "unit": "Tops/s", "frac": achieved / ISSUE_PEAK_OPS,
                 "traffic": TRAFFIC_BYTES_PER_LAUNCH if args.count_log2 == 36 else None,
                 "traffic_unit": "bytes per launch (ncu DRAM read + write)",
-                "peak_note": "derived: 152 SMs x 128 lanes x 2.07 GHz (issue ceiling, of derived)",
+                "peak_note": ("derived: 152 SMs x 128 lanes x 2.07 GHz (one warp instruction per "
+                              "scheduler per clock; issue ceiling, of derived); the measured rates below "
+                              "(lane-ops per SM per clock) reach 128 for 32-bit add and FP32 FMA, 64 for "
+                              "logic and integer multiply-add"),
+                "measured_pipe_rates": pipe_rates,
                 "half_steps_per_line": stats["half_steps"] / max(1, stats["lines"]),
                 "filter_fail_per_line": stats["filter_fail"] / max(1, stats["lines"])}
 
@@ -399,6 +416,7 @@ def main():
         mjobs = wl.batched_jobs(njobs=args.mixed_jobs)
         margs = sum(j.count for j in mjobs)
         dmc, dmn = tmd.alloc_candidates(cap, local_rank)
+        mtuned = tmd.tmd_autotune(ctx, mjobs)
         t0 = time.perf_counter()
         mb = tmd.Batch(ctx, mjobs, dmc, dmn)
         t_plan = time.perf_counter() - t0
@@ -412,7 +430,8 @@ def main():
         ms_p = statistics.mean(timed(per_job, 5, 2))
         mixed = {"jobs": len(mjobs), "args": margs, "lines": st_b["lines"],
                  "batched": {"value": margs / (ms_b / 1e3), "ms_per_step": ms_b,
-                             "form": "one persistent graph launch over all jobs"},
+                             "form": "one persistent graph launch over all jobs",
+                             "tiling": {"nu": mtuned["nu"], "ctas_per_sm": mtuned["ctas_per_sm"]}},
                  "plain": {"value": margs / (ms_p / 1e3), "ms_per_step": ms_p,
                            "form": "one launch per job, plans resident"},
                  "plan_and_tables_s": t_plan}
@@ -425,6 +444,7 @@ def main():
         ljobs = wl.large_jobs()
         largs = sum(j.count for j in ljobs)
         dlc, dln = tmd.alloc_candidates(cap, local_rank)
+        ltuned = tmd.tmd_autotune(ctx, ljobs)
         t0 = time.perf_counter()
         lb = tmd.Batch(ctx, ljobs, dlc, dln)
         t_plan = time.perf_counter() - t0
@@ -433,7 +453,8 @@ def main():
         _, n_l = tmd.tmd_candidates(ctx, dlc, dln)
         large = {"jobs": len(ljobs), "args": largs, "lines": st_l["lines"], "candidates": n_l,
                  "batched": {"value": largs / (ms_l / 1e3), "ms_per_step": ms_l,
-                             "form": "one persistent graph launch over all 2^16 jobs"},
+                             "form": "one persistent graph launch over all 2^16 jobs",
+                             "tiling": {"nu": ltuned["nu"], "ctas_per_sm": ltuned["ctas_per_sm"]}},
                  "plan_and_tables_s": t_plan, "upload_bytes": lb.upload_bytes}
         lb.close()
 
@@ -465,6 +486,9 @@ def main():
                                    f"d=3, W=192, N=2^14, m={args.m}",
                        "l2": "256 MiB flush before every step",
                        "form": "batched: persistent work-queue kernel replayed as a CUDA graph",
+                       "tiling": {"nu": tuned["nu"], "ctas_per_sm": tuned["ctas_per_sm"],
+                                  "picked_by": ("tmd_autotune (mean of 4 replays per candidate)"
+                                                if args.tiling == "auto" else "--tiling")},
                        "candidates": count},
             "plain": {"value": fused_value, "ms_per_step": ms_fused,
                       "form": "per-job fused launch (tmd_search)"},

@@ -226,6 +226,17 @@ tmd_status tmd_lower_bounds(tmd_ctx* ctx, const uint64_t* d_B, const uint64_t* d
  * Synchronises `stream`. */
 tmd_status tmd_stats_read(tmd_ctx* ctx, tmd_stats* out, void* stream);
 
+/* Measured issue rates of the pipes the search runs on (no counterpart in the
+ * paper: the measured denominator of the integer-pipe roofline).  Long
+ * independent chains of one instruction kind per thread, 8 CTAs of 256
+ * threads on every SM of `device`, timed by the SM cycle counter:
+ * out[0..3] = lane-operations per SM per clock of 32-bit add, 3-input
+ * logic, 32-bit multiply-add and FP32 fused multiply-add; out[4] (if
+ * n_out > 4) = the SM clock in MHz during the add run.  Writes
+ * min(n_out, 5) values.  Synchronises the device; allocates and frees
+ * about 1.3 MB of device memory. */
+tmd_status tmd_pipe_rates(int device, double* out, int n_out);
+
 /* ---- batched form: one persistent launch over many jobs, as a CUDA graph ---- */
 
 typedef struct tmd_batch tmd_batch;
@@ -241,6 +252,43 @@ typedef struct tmd_batch tmd_batch;
 tmd_status tmd_batch_create(tmd_ctx* ctx, const tmd_job* jobs, uint32_t njobs,
                             tmd_candidate* d_cand, uint64_t cand_cap, uint64_t* d_count,
                             void* stream, tmd_batch** batch, uint64_t* upload_bytes);
+
+/* Tiling of the batched form: how the work of a batch is cut for the
+ * persistent kernel.  nu = sub-intervals per packet, i.e. lines one lane
+ * steps by tabulated differences before the search (1..8; 0 = 8): longer
+ * packets amortise the straightforward shift to the packet start (Sect.
+ * IV-B), shorter ones give more, smaller tasks of 32 packets.  ctas_per_sm =
+ * resident CTAs of 8 warps per SM (0 = the kernel's occupancy): with the
+ * task count it fixes how evenly the tasks divide among the resident warps.
+ * Lanes per approximation are 1 (one line per lane, Sect. III-C). */
+typedef struct {
+    uint32_t nu;
+    uint32_t ctas_per_sm;
+} tmd_tiling;
+
+/* tmd_batch_create with an explicit tiling (NULL = the default); EINVAL for
+ * nu > 8 or ctas_per_sm > 64.  tmd_batch_create itself takes the tiling that
+ * tmd_autotune chose for a batch of the same signature on this context
+ * (distinct limbs/degree/N classes, SM count, order of magnitude of the
+ * sub-interval count), else the default. */
+tmd_status tmd_batch_create_tiled(tmd_ctx* ctx, const tmd_job* jobs, uint32_t njobs,
+                                  tmd_candidate* d_cand, uint64_t cand_cap, uint64_t* d_count,
+                                  void* stream, const tmd_tiling* tiling, tmd_batch** batch,
+                                  uint64_t* upload_bytes);
+
+/* Autotuner of the batched form (no counterpart in the paper, which tunes
+ * its block sizes by hand, Sect. V-A): builds the batch with every tiling of
+ * nu in {8, 6, 4, 2} x ctas_per_sm in {occupancy .. 1}, times a few graph
+ * replays of each on `stream` (CUDA events; records are counted, not
+ * stored), and keeps the fastest in the context for batches of the same
+ * signature.  *best receives it, *best_ms (may be NULL) its mean replay time.
+ * Synchronises `stream`; allocates and frees 8 bytes of device memory. */
+tmd_status tmd_autotune(tmd_ctx* ctx, const tmd_job* jobs, uint32_t njobs, void* stream,
+                        tmd_tiling* best, float* best_ms);
+
+/* The tiling a batch was built with (nu = its longest packet, ctas_per_sm =
+ * its largest per-SM CTA count over the classes). */
+tmd_status tmd_batch_tiling(const tmd_batch* batch, tmd_tiling* out);
 
 /* Replay the batch's graph on `stream` (asynchronous). */
 tmd_status tmd_batch_launch(tmd_batch* batch, void* stream);

@@ -162,18 +162,32 @@ def tmd_stats_read(ctx: Context, stream=None) -> dict:
 class Batch:
     """A tmd_batch: resident plan of many jobs plus its captured graph."""
 
-    def __init__(self, ctx: Context, jobs: Sequence, d_cand, d_count, stream=None):
+    def __init__(self, ctx: Context, jobs: Sequence, d_cand, d_count, stream=None, tiling=None):
+        """tiling: None = the context's autotuned tiling for this batch
+        signature (else the default); or (nu, ctas_per_sm)."""
         self.ctx = ctx
         self.jobs = list(jobs)
         self.d_cand, self.d_count = d_cand, d_count   # kept alive with the batch
         cap = 0 if d_cand is None else (d_cand.numel() * d_cand.element_size()) // CANDIDATE_BYTES
         h = ctypes.c_void_p()
         up = ctypes.c_uint64(0)
-        check(lib().tmd_batch_create(ctx.handle, job_array(self.jobs), len(self.jobs), _ptr(d_cand),
-                                     cap, _ptr(d_count), _stream_ptr(stream), ctypes.byref(h),
-                                     ctypes.byref(up)), "tmd_batch_create")
+        if tiling is None:
+            check(lib().tmd_batch_create(ctx.handle, job_array(self.jobs), len(self.jobs), _ptr(d_cand),
+                                         cap, _ptr(d_count), _stream_ptr(stream), ctypes.byref(h),
+                                         ctypes.byref(up)), "tmd_batch_create")
+        else:
+            t = _lib.tmd_tiling(int(tiling[0]), int(tiling[1]))
+            check(lib().tmd_batch_create_tiled(ctx.handle, job_array(self.jobs), len(self.jobs), _ptr(d_cand),
+                                               cap, _ptr(d_count), _stream_ptr(stream), ctypes.byref(t),
+                                               ctypes.byref(h), ctypes.byref(up)), "tmd_batch_create_tiled")
         self.handle = h
         self.upload_bytes = up.value
+
+    def tiling(self) -> tuple:
+        """(nu, ctas_per_sm) the batch was built with."""
+        t = _lib.tmd_tiling()
+        check(lib().tmd_batch_tiling(self.handle, ctypes.byref(t)), "tmd_batch_tiling")
+        return (t.nu, t.ctas_per_sm)
 
     def launch(self, stream=None):
         check(lib().tmd_batch_launch(self.handle, _stream_ptr(stream)), "tmd_batch_launch")
@@ -196,8 +210,19 @@ class Batch:
             pass
 
 
-def tmd_batch_create(ctx: Context, jobs: Sequence, d_cand, d_count, stream=None) -> Batch:
-    return Batch(ctx, jobs, d_cand, d_count, stream)
+def tmd_batch_create(ctx: Context, jobs: Sequence, d_cand, d_count, stream=None, tiling=None) -> Batch:
+    return Batch(ctx, jobs, d_cand, d_count, stream, tiling)
+
+
+def tmd_autotune(ctx: Context, jobs: Sequence, stream=None) -> dict:
+    """Time the batch under every candidate tiling; the fastest is kept in the
+    context for batches of the same signature.  Returns {"nu", "ctas_per_sm",
+    "ms"}."""
+    t = _lib.tmd_tiling()
+    ms = ctypes.c_float(0.0)
+    check(lib().tmd_autotune(ctx.handle, job_array(list(jobs)), len(jobs), _stream_ptr(stream),
+                             ctypes.byref(t), ctypes.byref(ms)), "tmd_autotune")
+    return {"nu": t.nu, "ctas_per_sm": t.ctas_per_sm, "ms": ms.value}
 
 
 def tmd_batch_launch(batch: Batch, stream=None) -> None:
@@ -315,3 +340,11 @@ def run(jobs: Sequence, ctx: Optional[Context] = None, fused: bool = True, cap: 
     finally:
         if own:
             ctx.close()
+
+
+def tmd_pipe_rates(device: int = 0) -> dict:
+    """Measured lane-operations per SM per clock of 32-bit add, 3-input logic,
+    32-bit multiply-add and FP32 FMA chains, and the SM clock (MHz)."""
+    out = (ctypes.c_double * 5)()
+    check(lib().tmd_pipe_rates(int(device), out, 5), "tmd_pipe_rates")
+    return {"add_u32": out[0], "lop3": out[1], "mad_u32": out[2], "ffma": out[3], "sm_mhz": out[4]}

@@ -62,6 +62,10 @@ class tmd_stats(ctypes.Structure):
                 ("upload_bytes", ctypes.c_uint64), ("count", ctypes.c_uint64)]
 
 
+class tmd_tiling(ctypes.Structure):
+    _fields_ = [("nu", ctypes.c_uint32), ("ctas_per_sm", ctypes.c_uint32)]
+
+
 _vp = ctypes.c_void_p
 _u64 = ctypes.c_uint64
 _u32 = ctypes.c_uint32
@@ -87,7 +91,14 @@ SIGNATURES = {
     "tmd_stats_read": (ctypes.c_int, [_vp, ctypes.POINTER(tmd_stats), _vp]),
     "tmd_batch_create": (ctypes.c_int, [_vp, ctypes.POINTER(tmd_job), _u32, _vp, _u64, _vp, _vp,
                                         ctypes.POINTER(_vp), ctypes.POINTER(_u64)]),
+    "tmd_batch_create_tiled": (ctypes.c_int, [_vp, ctypes.POINTER(tmd_job), _u32, _vp, _u64, _vp, _vp,
+                                              ctypes.POINTER(tmd_tiling), ctypes.POINTER(_vp),
+                                              ctypes.POINTER(_u64)]),
+    "tmd_autotune": (ctypes.c_int, [_vp, ctypes.POINTER(tmd_job), _u32, _vp, ctypes.POINTER(tmd_tiling),
+                                    ctypes.POINTER(ctypes.c_float)]),
+    "tmd_batch_tiling": (ctypes.c_int, [_vp, ctypes.POINTER(tmd_tiling)]),
     "tmd_batch_launch": (ctypes.c_int, [_vp, _vp]),
+    "tmd_pipe_rates": (ctypes.c_int, [ctypes.c_int, ctypes.POINTER(ctypes.c_double), ctypes.c_int]),
     "tmd_batch_stats": (ctypes.c_int, [_vp, ctypes.POINTER(tmd_stats), _vp]),
     "tmd_batch_destroy": (ctypes.c_int, [_vp]),
     "tmd_search_static": (ctypes.c_int, [ctypes.POINTER(tmd_job), _u32, _vp, _u64, _vp, _vp]),

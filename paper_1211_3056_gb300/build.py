@@ -1,6 +1,6 @@
 """Build the CUDA library libtmd.so in-tree for sm_103a.
 
-Three translation units (host planning/tables, kernels, C-ABI glue) are
+Four translation units (host planning/tables, kernels, C-ABI glue, pipe-rate probe) are
 compiled in parallel with nvcc and linked into one shared object next to
 this file.  `python -m paper_1211_3056_gb300.build` runs it.
 """
@@ -19,7 +19,7 @@ OBJ = os.path.join(HERE, "_build")
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-std=c++17", "-O3", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-Wall"]
-SOURCES = ["host.cpp", "kernels.cu", "api.cu"]
+SOURCES = ["host.cpp", "kernels.cu", "api.cu", "probe.cu"]
 
 
 def nvcc() -> str:

@@ -7,9 +7,12 @@
 #include <atomic>
 #include <cstdlib>
 #include <chrono>
+#include <cmath>
 #include <condition_variable>
 #include <cstring>
 #include <deque>
+#include <map>
+#include <string>
 #include <mutex>
 #include <thread>
 #include <vector>
@@ -87,6 +90,9 @@ struct tmd_ctx {
     bool resident = false;
     uint64_t upload_bytes = 0;
     const uint64_t* last_count = nullptr;
+    // tilings chosen by tmd_autotune, by batch signature (tiling_key)
+    std::mutex tune_mu;
+    std::map<std::string, tmd_tiling> tuned;
 };
 
 namespace {
@@ -121,10 +127,11 @@ void run_threads(unsigned n, F&& fn) {
     for (auto& t : th) t.join();
 }
 
-uint32_t choose_nu(const tmd_job& job, uint64_t n_sub_block) {
+uint32_t choose_nu(const tmd_job& job, uint64_t n_sub_block, uint32_t nu_max) {
     const char* env = getenv("TMD_NU");
     uint32_t nu = 8;  // at most the kernels' shared-memory stage (8 lines per lane)
-    if (env && atoi(env) > 0) nu = (uint32_t)atoi(env);
+    if (nu_max) nu = nu_max;
+    else if (env && atoi(env) > 0) nu = (uint32_t)atoi(env);
     if (nu > 8) nu = 8;
     if (nu > n_sub_block) nu = (uint32_t)n_sub_block;
     if (nu < 1) nu = 1;
@@ -137,7 +144,7 @@ uint32_t choose_nu(const tmd_job& job, uint64_t n_sub_block) {
 // device planning kernels expand them).  With host_tables the blocks, tasks
 // and correctly rounded tables are also materialised on the host (threads
 // over blocks).
-tmd_status build_plan(const tmd_job* jobs, uint32_t njobs, Plan& P, bool host_tables = true) {
+tmd_status build_plan(const tmd_job* jobs, uint32_t njobs, Plan& P, bool host_tables = true, uint32_t nu_max = 0) {
     // reuse the vectors' storage of a previous plan (no new pages per call)
     P.key.clear();
     P.jobs.clear();
@@ -197,7 +204,7 @@ tmd_status build_plan(const tmd_job* jobs, uint32_t njobs, Plan& P, bool host_ta
         dj.p = jb.p;
         const uint64_t T = 1ull << jb.log2_T, N = 1ull << jb.log2_N;
         const uint64_t SB = T >> jb.log2_N;  // sub-intervals of a full block
-        dj.nu = choose_nu(jb, SB);
+        dj.nu = choose_nu(jb, SB, nu_max);
         dj.ppb = (uint32_t)((SB + dj.nu - 1) / dj.nu);
         dj.words = (uint32_t)((2 * jb.d + 1) * jb.limbs);
         dj.n_seg = (uint32_t)segs.size();
@@ -681,6 +688,7 @@ struct tmd_batch {
     cudaStream_t cap_stream = nullptr;
     uint64_t upload_bytes = 0;
     const uint64_t* d_count = nullptr;
+    tmd_tiling tiling = {0, 0};
 };
 
 namespace {
@@ -695,6 +703,29 @@ void batch_free(tmd_batch* b) {
     delete b;
 }
 
+// Signature of a batch for the tuned-tiling cache: its distinct (limbs,
+// degree, log2 N) classes, the SM count and the order of magnitude of its
+// sub-interval count (the tiling decides how the tasks divide among the
+// resident warps, so the size matters).
+std::string tiling_key(const tmd_job* jobs, uint32_t njobs, int sms) {
+    std::vector<uint32_t> cls;
+    double subs = 0;
+    for (uint32_t j = 0; j < njobs; j++) {
+        cls.push_back(jobs[j].limbs * 1024u + (uint32_t)jobs[j].d * 32u + jobs[j].log2_N);
+        subs += (double)((jobs[j].count + (1ull << jobs[j].log2_N) - 1) >> jobs[j].log2_N);
+    }
+    std::sort(cls.begin(), cls.end());
+    cls.erase(std::unique(cls.begin(), cls.end()), cls.end());
+    std::string k = "sms" + std::to_string(sms) + "/subs2^" + std::to_string((int)std::log2(std::max(subs, 1.0)));
+    for (uint32_t v : cls)
+        k += "/L" + std::to_string(v >> 10) + "d" + std::to_string((v >> 5) & 31) + "N" + std::to_string(v & 31);
+    return k;
+}
+
+tmd_status batch_create(tmd_ctx* c, const tmd_job* jobs, uint32_t njobs, tmd_candidate* d_cand,
+                        uint64_t cand_cap, uint64_t* d_count, void* stream, const tmd_tiling& tiling,
+                        tmd_batch** out, uint64_t* upload_bytes);
+
 }  // namespace
 
 extern "C" {
@@ -703,18 +734,110 @@ tmd_status tmd_batch_create(tmd_ctx* c, const tmd_job* jobs, uint32_t njobs, tmd
                             uint64_t cand_cap, uint64_t* d_count, void* stream, tmd_batch** out,
                             uint64_t* upload_bytes) {
     if (!c || !jobs || njobs == 0 || !d_count || !out || (cand_cap && !d_cand)) return TMD_EINVAL;
+    tmd_tiling t = {0, 0};
+    {
+        std::lock_guard<std::mutex> lk(c->tune_mu);
+        auto it = c->tuned.find(tiling_key(jobs, njobs, c->sms));
+        if (it != c->tuned.end()) t = it->second;
+    }
+    return batch_create(c, jobs, njobs, d_cand, cand_cap, d_count, stream, t, out, upload_bytes);
+}
+
+tmd_status tmd_batch_create_tiled(tmd_ctx* c, const tmd_job* jobs, uint32_t njobs, tmd_candidate* d_cand,
+                                  uint64_t cand_cap, uint64_t* d_count, void* stream, const tmd_tiling* tiling,
+                                  tmd_batch** out, uint64_t* upload_bytes) {
+    if (!c || !jobs || njobs == 0 || !d_count || !out || (cand_cap && !d_cand)) return TMD_EINVAL;
+    tmd_tiling t = tiling ? *tiling : tmd_tiling{0, 0};
+    if (t.nu > 8 || t.ctas_per_sm > 64) return TMD_EINVAL;
+    return batch_create(c, jobs, njobs, d_cand, cand_cap, d_count, stream, t, out, upload_bytes);
+}
+
+tmd_status tmd_autotune(tmd_ctx* c, const tmd_job* jobs, uint32_t njobs, void* stream, tmd_tiling* best,
+                        float* best_ms) {
+    if (!c || !jobs || njobs == 0 || !best) return TMD_EINVAL;
+    CK(cudaSetDevice(c->device));
+    cudaStream_t s = (cudaStream_t)stream;
+    // the largest occupancy over the batch's classes bounds the CTA counts tried
+    int occ = 1;
+    for (uint32_t j = 0; j < njobs; j++) {
+        int per_sm = 0;
+        if (jobs[j].limbs >= 1 && jobs[j].limbs <= 3 && jobs[j].d >= 1 && jobs[j].d <= 4 &&
+            persistent_occupancy(jobs[j].limbs, (uint32_t)jobs[j].d, &per_sm) == cudaSuccess)
+            occ = std::max(occ, per_sm);
+    }
+    uint64_t* d_cnt = nullptr;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    if (cudaMalloc((void**)&d_cnt, sizeof(uint64_t)) != cudaSuccess) return TMD_ENOMEM;
+    if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
+        cudaFree(d_cnt);
+        if (e0) cudaEventDestroy(e0);
+        return TMD_ECUDA;
+    }
+    tmd_status st = TMD_OK;
+    tmd_tiling win = {0, 0};
+    float win_ms = 0.f;
+    static const uint32_t nus[] = {8, 6, 4, 2};
+    for (uint32_t nu : nus) {
+        for (int k = occ; k >= 1 && st == TMD_OK; k--) {
+            const tmd_tiling t = {nu, (uint32_t)k};
+            tmd_batch* b = nullptr;
+            st = batch_create(c, jobs, njobs, nullptr, 0, d_cnt, stream, t, &b, nullptr);
+            if (st != TMD_OK) break;
+            // one warm replay, then the mean of a few
+            const int reps = 4;
+            float ms = 0.f;
+            if (cudaGraphLaunch(b->exec, s) != cudaSuccess || cudaEventRecord(e0, s) != cudaSuccess) st = TMD_ECUDA;
+            for (int r = 0; r < reps && st == TMD_OK; r++)
+                if (cudaGraphLaunch(b->exec, s) != cudaSuccess) st = TMD_ECUDA;
+            if (st == TMD_OK && (cudaEventRecord(e1, s) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess ||
+                                 cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess))
+                st = TMD_ECUDA;
+            tmd_batch_destroy(b);
+            if (st != TMD_OK) break;
+            ms /= reps;
+            if (win.nu == 0 || ms < win_ms) {
+                win = t;
+                win_ms = ms;
+            }
+        }
+        if (st != TMD_OK) break;
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    cudaFree(d_cnt);
+    if (st != TMD_OK) return st;
+    {
+        std::lock_guard<std::mutex> lk(c->tune_mu);
+        c->tuned[tiling_key(jobs, njobs, c->sms)] = win;
+    }
+    *best = win;
+    if (best_ms) *best_ms = win_ms;
+    return TMD_OK;
+}
+
+}  // extern "C"
+
+namespace {
+
+tmd_status batch_create(tmd_ctx* c, const tmd_job* jobs, uint32_t njobs, tmd_candidate* d_cand,
+                        uint64_t cand_cap, uint64_t* d_count, void* stream, const tmd_tiling& tiling,
+                        tmd_batch** out, uint64_t* upload_bytes) {
     *out = nullptr;
     CK(cudaSetDevice(c->device));
     cudaStream_t s = (cudaStream_t)stream;
     tmd_batch* b = new tmd_batch();
     b->ctx = c;
     b->d_count = d_count;
-    tmd_status st = build_plan(jobs, njobs, b->plan, /*host_tables=*/false);
+    b->tiling = tiling;
+    tmd_status st = build_plan(jobs, njobs, b->plan, /*host_tables=*/false, tiling.nu);
     if (st != TMD_OK) {
         batch_free(b);
         return st;
     }
     Plan& P = b->plan;
+    b->tiling.nu = 0;
+    for (const DevJob& dj : P.jobs) b->tiling.nu = std::max(b->tiling.nu, dj.nu);
+    b->tiling.ctas_per_sm = 0;
     const Layout Lo = plan_layout(P);
     const size_t o_blocks = Lo.o_blocks, o_tasks = Lo.o_tasks, o_tables = Lo.o_tables;
     std::vector<char> host(Lo.upload, 0);
@@ -773,6 +896,8 @@ tmd_status tmd_batch_create(tmd_ctx* c, const tmd_job* jobs, uint32_t njobs, tmd
         const ClassRange& cr = P.classes[ci];
         int per_sm = 0;
         if (persistent_occupancy(cr.L, cr.D, &per_sm) != cudaSuccess || per_sm < 1) per_sm = 1;
+        if (tiling.ctas_per_sm) per_sm = std::min(per_sm, (int)tiling.ctas_per_sm);
+        b->tiling.ctas_per_sm = std::max(b->tiling.ctas_per_sm, (uint32_t)per_sm);
         const uint64_t want = (cr.count + 7) / 8;
         const int ctas = (int)std::min<uint64_t>((uint64_t)c->sms * (uint64_t)per_sm, std::max<uint64_t>(want, 1));
         LaunchArgs ac = a;
@@ -787,6 +912,16 @@ tmd_status tmd_batch_create(tmd_ctx* c, const tmd_job* jobs, uint32_t njobs, tmd
         return TMD_ECUDA;
     }
     *out = b;
+    return TMD_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+tmd_status tmd_batch_tiling(const tmd_batch* b, tmd_tiling* out) {
+    if (!b || !out) return TMD_EINVAL;
+    *out = b->tiling;
     return TMD_OK;
 }
 

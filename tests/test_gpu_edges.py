@@ -51,3 +51,13 @@ def test_cut_splits_a_subinterval():
     job = wl.Job(wl.FUNC_EXP, 0, 30, 20, 10, 2, 16, 1, 0, 1 << 29)
     segs = plan.segments(job)
     assert len(segs) == 2 and segs[1][0] % (1 << 10) != 0
+
+
+def test_pipe_rates_are_plausible():
+    """The probe behind the roofline's measured denominator: every rate is a
+    lane count per SM per clock between a quarter and twice the issue width."""
+    r = tmd.tmd_pipe_rates(0)
+    for k in ("add_u32", "lop3", "mad_u32", "ffma"):
+        assert 32 <= r[k] <= 260, (k, r[k])
+    assert r["add_u32"] >= r["lop3"]
+    assert 200 < r["sm_mhz"] < 4000

@@ -21,6 +21,11 @@ filter with it value by value:
                     the same computation unrolled twice (Algorithm 4),
                     with the degenerate endings (a remainder reaching 0
                     for rational a) made explicit;
+  lefevre_lb, lefevre_swap_lb, lefevre_test
+                    Lefevre's lower bound (Algorithm 1) and its branch-
+                    merged form with swaps (Algorithm 3), and the Boolean
+                    test of Algorithm 1;
+  nmdm              the loop-divergence indicator of Sect. II-B;
   forward_differences, tabulated_shift, straightforward_shift
                     Sect. IV difference tables (Figs. 5 and 6).
 """
@@ -121,6 +126,131 @@ def regular_lb_unrolled(B: int, A: int, N: int, M: int = 1 << 64) -> Tuple[int, 
         hs += 1
         if u + v >= N:
             return d, u + v, hs
+
+
+def lefevre_lb(B: int, A: int, N: int, M: int = 1 << 64) -> Tuple[int, int, int]:
+    """Algorithm 1 (Lefevre's lower bound computation) run to its Success
+    exit, i.e. the test with eps'' = 0; returns (d, u+v, loop iterations).
+    p <- a, q <- 1 - a, d <- b, u <- v <- 1 (scaled by M).  Each iteration
+    either (d < p: the point added last lies right of b) takes a whole
+    quotient k = floor(q/p) off q and the first unit of the next one off p,
+    or (d >= p) moves d to the point just added at its left (d -= p) and
+    takes k = floor(p/q) off p and one unit off q.  The test of Algorithm 1
+    fails exactly when this d is below eps'' (d never grows).
+    Degenerate endings (rational a, not covered by the printed algorithm):
+    a division leaving a zero remainder means every interval now has the
+    other length, so d reduced modulo that length is the distance over the
+    whole lattice of points and the loop ends there.  A = 0: every point
+    is 0, d = b."""
+    A %= M
+    B %= M
+    if A == 0:
+        return B, 1, 0
+    p, q, d, u, v = A, M - A, B, 1, 1
+    it = 0
+    while True:
+        it += 1
+        if d < p:
+            k = q // p
+            q -= k * p
+            u += k * v
+            if u + v >= N:
+                return d, u + v, it
+            if q == 0:
+                return d % p, u + v, it
+            p -= q
+            v += u
+        else:
+            d -= p
+            k = p // q
+            p -= k * q
+            v += k * u
+            if u + v >= N:
+                return d, u + v, it
+            if p == 0:
+                return d % q, u + v, it
+            q -= p
+            u += v
+
+
+def lefevre_swap_lb(B: int, A: int, N: int, M: int = 1 << 64) -> Tuple[int, int, int]:
+    """Algorithm 3: Algorithm 1 with its two branches merged by swapping
+    (p, q) and (u, v) whenever b changes side (are_swapped), so that only
+    the update of d stays conditional.  Reading of the printed listing
+    (which subtracts and compares p in the swapped state, and then differs
+    from Algorithm 1 on the first step of a = b): the length taken off d,
+    and compared with d to decide the next swap, is Algorithm 1's p, which
+    the swap has moved into q -- l = q when swapped, p otherwise.  Same
+    (d, u+v, iterations) as lefevre_lb, same degenerate endings."""
+    A %= M
+    B %= M
+    if A == 0:
+        return B, 1, 0
+    p, q, d, u, v = A, M - A, B, 1, 1
+    sw = False
+    if d >= p:
+        p, q, u, v, sw = q, p, v, u, True
+    it = 0
+    while True:
+        it += 1
+        if sw:
+            d -= q
+        k = q // p
+        q -= k * p
+        u += k * v
+        if u + v >= N:
+            return d, u + v, it
+        if q == 0:
+            return d % p, u + v, it
+        p -= q
+        v += u
+        if sw != (d >= (q if sw else p)):
+            p, q, u, v, sw = q, p, v, u, not sw
+
+
+def lefevre_test(B: int, A: int, N: int, eps: int, M: int = 1 << 64) -> bool:
+    """Algorithm 1 as a Boolean test, returning at the first d < eps''
+    (Failure, False) or at u + v >= N (Success, True); degenerate endings
+    as in lefevre_lb."""
+    A %= M
+    B %= M
+    if B < eps:
+        return False
+    if A == 0:
+        return True
+    p, q, d, u, v = A, M - A, B, 1, 1
+    while True:
+        if d < p:
+            k = q // p
+            q -= k * p
+            u += k * v
+            if u + v >= N:
+                return True
+            if q == 0:
+                return d % p >= eps
+            p -= q
+            v += u
+        else:
+            d -= p
+            if d < eps:
+                return False
+            k = p // q
+            p -= k * q
+            v += k * u
+            if u + v >= N:
+                return True
+            if p == 0:
+                return d % q >= eps
+            q -= p
+            u += v
+
+
+def nmdm(iterations: List[int]) -> float:
+    """Normalized mean deviation to the maximum of a warp's loop iteration
+    counts (Sect. II-B): 1 - mean / max, the share of the warp's iterations
+    a thread spends idle."""
+    mx = max(iterations)
+    return 0.0 if mx == 0 else 1.0 - (sum(iterations) / len(iterations)) / mx
 
 
 def forward_differences(values: List[int]) -> List[List[int]]:

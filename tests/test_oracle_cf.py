@@ -129,3 +129,59 @@ def test_brute_min_definition():
     # ties: the smallest x wins (A*32 = 0 mod 64)
     assert search.brute_min(3, 32, 4, 64) == (3, 0)
     assert search.brute_min(10, 3, 5, 64) == (1, 3)
+
+
+@pytest.mark.parametrize("M", [45, 64, 97])
+def test_lefevre_lb_exhaustive_small_moduli(M):
+    """Exhaustive over all (a, b, N): Algorithm 3 (swap form) gives exactly
+    Algorithm 1's bound, points and iteration count; the bound lies between
+    the minimum over the whole orbit and the brute-force minimum over x < N;
+    the Boolean test of Algorithm 1 succeeds exactly when the bound reaches
+    eps''."""
+    for A in range(M):
+        for B in range(M):
+            run = []
+            best = None
+            for x in range(2 * M + 2):
+                v = (B - A * x) % M
+                best = v if best is None or v < best else best
+                run.append(best)
+            for N in range(1, M + 2):
+                l1 = search.lefevre_lb(B, A, N, M)
+                assert search.lefevre_swap_lb(B, A, N, M) == l1
+                assert run[-1] <= l1[0] <= run[N - 1]
+                for eps in (1, 3, M // 4):
+                    assert search.lefevre_test(B, A, N, eps, M) == (l1[0] >= eps)
+
+
+def test_lefevre_lb_random_64bit():
+    rng = random.Random(13)
+    for _ in range(400):
+        N = rng.choice([16, 256, 1024])
+        A = rng.getrandbits(64)
+        B = rng.getrandbits(64)
+        lb, n, it = search.lefevre_lb(B, A, N)
+        true, _ = search.brute_min(B, A, N)
+        assert n >= N and lb <= true
+        assert search.lefevre_swap_lb(B, A, N) == (lb, n, it)
+
+
+def test_lefevre_filters_more_than_regular():
+    """Table 2: Lefevre's bound leaves several times fewer failing
+    sub-domains than the regular one (it adds points at the left of b one
+    at a time, so it stops closer to N points)."""
+    rng = random.Random(17)
+    fl = fr = 0
+    for _ in range(3000):
+        N = rng.choice([256, 1024, 4096])
+        A, B = rng.getrandbits(64), rng.getrandbits(64)
+        fl += search.lefevre_lb(B, A, N)[0] < (1 << 50)
+        fr += search.regular_lb_unrolled(B, A, N)[0] < (1 << 50)
+    assert 0 < 2 * fl < fr
+
+
+def test_nmdm_definition():
+    """Sect. II-B: NMDM = 1 - mean/max of a warp's loop iteration counts."""
+    assert search.nmdm([7] * 32) == 0.0
+    assert search.nmdm([0] * 31 + [10]) == pytest.approx(1 - (10 / 32) / 10)
+    assert search.nmdm([8, 19, 12, 12]) == pytest.approx(1 - 12.75 / 19)

@@ -272,6 +272,8 @@ def main():
                     help="jobs of the seeded serving stream to serve (0 = skip)")
     ap.add_argument("--count-log2", type=int, default=36,
                     help="slice size (smaller only for profiling captures)")
+    ap.add_argument("--lefevre", type=int, default=1,
+                    help="also time the same slice with Lefevre's filter (0 = skip)")
     ap.add_argument("--tiling", default="auto",
                     help="'auto' (tmd_autotune picks it) or 'nu,ctas_per_sm' for the batched form")
     args = ap.parse_args()
@@ -411,6 +413,26 @@ def main():
                 "half_steps_per_line": stats["half_steps"] / max(1, stats["lines"]),
                 "filter_fail_per_line": stats["filter_fail"] / max(1, stats["lines"])}
 
+    # Lefevre's filter (Algorithm 3) on the same slice, batched the same way
+    # (Table 4's comparison of the two searches; identical records)
+    lefevre = None
+    if args.lefevre:
+        ljob = job.replace(flags=job.flags | wl.FLAG_LEFEVRE)
+        d_cand_l, d_count_l = tmd.alloc_candidates(cap, local_rank)
+        ltune = tmd.tmd_autotune(ctx, [ljob])
+        lbatch = tmd.Batch(ctx, [ljob], d_cand_l, d_count_l)
+        lef_ms = max_over_ranks(statistics.mean(timed(lbatch.launch, max(args.steps // 4, 5), args.warmup)))
+        lst = lbatch.stats()
+        lrecs = tmd.tmd_candidates(ctx, d_cand_l, d_count_l)
+        assert lrecs == (recs, count), "the two filters must give the same records"
+        lefevre = {"value": total_args / (lef_ms / 1e3), "ms_per_step": lef_ms,
+                   "regular_over_lefevre_time": lef_ms / ms,
+                   "iterations_per_line": lst["half_steps"] / max(1, lst["lines"]),
+                   "filter_fail_per_line": lst["filter_fail"] / max(1, lst["lines"]),
+                   "tiling": {"nu": ltune["nu"], "ctas_per_sm": ltune["ctas_per_sm"]},
+                   "form": "batched, Lefevre's lower bound (Algorithm 3) as the filter"}
+        lbatch.close()
+
     mixed = None
     if args.mixed_jobs > 0:
         mjobs = wl.batched_jobs(njobs=args.mixed_jobs)
@@ -497,7 +519,8 @@ def main():
             "e2e": {"value": total_args / e2e_s, "unit": UNIT, "h2d_bytes_per_step": h2d,
                     "d2h_bytes_per_step": d2h, "ms_per_step": e2e_s * 1e3},
             "gpu_launches": args.steps * 1,
-            "roofline": roofline, "cpu_baseline": cpu, "clocks": clocks, "mixed_batch": mixed,
+            "roofline": roofline, "cpu_baseline": cpu, "clocks": clocks, "lefevre": lefevre,
+            "mixed_batch": mixed,
             "large_batch": large,
             "serving": serving,
         }

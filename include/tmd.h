@@ -60,6 +60,11 @@ typedef enum { TMD_EXP = 0, TMD_EXP2 = 1, TMD_LOG = 2 } tmd_func;
                                (Sect. II-A).                                          */
 #define TMD_ALL_HITS 2u     /* report every argument below the threshold, not only the
                                minimum of each sub-interval                            */
+#define TMD_LEFEVRE 4u      /* filter with Lefevre's lower bound (Algorithm 3, the swap
+                               form of Algorithm 1) instead of the regular one
+                               (Algorithm 4).  The records do not change (flagged lines
+                               are resolved exactly either way); the statistics'
+                               half_steps counter then counts Algorithm 3 iterations. */
 
 /* One search job: a slice of one binade of one function (Sect. III-A).
  * Argument index j in [0, 2^(p-1)) stands for X_j = (2^(p-1) + j) 2^(e_in - p).
@@ -77,7 +82,7 @@ typedef struct {
     uint32_t limbs;     /* fixed-point width W = 64 * limbs bits               */
     uint64_t start;     /* first argument index                                */
     uint64_t count;     /* number of arguments                                 */
-    uint32_t flags;     /* TMD_BP_DIRECTED | TMD_ALL_HITS                      */
+    uint32_t flags;     /* TMD_BP_DIRECTED | TMD_ALL_HITS | TMD_LEFEVRE        */
     uint32_t reserved;  /* must be 0                                           */
 } tmd_job;
 
@@ -206,7 +211,8 @@ tmd_status tmd_candidates(tmd_ctx* ctx, const tmd_candidate* d_cand,
 /* Search n lines given directly as device arrays d_B[n], d_A[n] (search
  * words as above) and d_len[n] (arguments per line, 1 .. 2^16).  Record i has
  * job = 0, subint = i, arg_index = x*, value = min.  threshold = 2^(65-m);
- * flags may hold TMD_ALL_HITS.  Same output contract as tmd_search. */
+ * flags may hold TMD_ALL_HITS and TMD_LEFEVRE.  Same output contract as
+ * tmd_search. */
 tmd_status tmd_search_lines(tmd_ctx* ctx, const uint64_t* d_B, const uint64_t* d_A,
                             const uint32_t* d_len, uint64_t n, int32_t m, uint32_t flags,
                             tmd_candidate* d_cand, uint64_t cand_cap, uint64_t* d_count,
@@ -220,6 +226,19 @@ tmd_status tmd_search_lines(tmd_ctx* ctx, const uint64_t* d_B, const uint64_t* d
 tmd_status tmd_lower_bounds(tmd_ctx* ctx, const uint64_t* d_B, const uint64_t* d_A,
                             const uint32_t* d_len, uint64_t n, uint64_t* d_lb,
                             uint32_t* d_hs, void* stream);
+
+/* Lefevre's lower bound alone (Algorithm 3 = Algorithm 1 with its branches
+ * merged by swaps, Sect. III-B), per line: d_lb[i] = d at the first
+ * u + v >= d_len[i] (Algorithm 1's test fails exactly when it is below
+ * eps''), d_iters[i] = main-loop iterations (may be NULL; Table 3).
+ * p <- a, q <- 1 - a, d <- b, u <- v <- 1 on the words scaled by 2^64; a
+ * division leaving a zero remainder (rational a) ends the loop with d
+ * reduced modulo the other length; A = 0 returns B with no iteration.
+ * Lengths as in tmd_lower_bounds (1 .. 2^16; others are clamped and
+ * reported by the next tmd_candidates/tmd_stats_read as TMD_EINVAL). */
+tmd_status tmd_lefevre_bounds(tmd_ctx* ctx, const uint64_t* d_B, const uint64_t* d_A,
+                              const uint32_t* d_len, uint64_t n, uint64_t* d_lb,
+                              uint32_t* d_iters, void* stream);
 
 /* Counters of the most recent tmd_search / tmd_search_lines / batch run on
  * this context, the size of the last plan upload and the last count.

@@ -12,6 +12,7 @@ TMD_OK, TMD_EINVAL, TMD_ENOMEM, TMD_EOVERFLOW, TMD_ETIMEOUT, TMD_ECUDA, TMD_EUNS
 TMD_EXP, TMD_EXP2, TMD_LOG = 0, 1, 2
 TMD_BP_DIRECTED = 1
 TMD_ALL_HITS = 2
+TMD_LEFEVRE = 4
 
 
 class TmdError(RuntimeError):
@@ -88,6 +89,7 @@ SIGNATURES = {
     "tmd_candidates": (ctypes.c_int, [_vp, _vp, _vp, _u64, _vp, _u64, ctypes.POINTER(_u64), _vp]),
     "tmd_search_lines": (ctypes.c_int, [_vp, _vp, _vp, _vp, _u64, _i32, _u32, _vp, _u64, _vp, _vp]),
     "tmd_lower_bounds": (ctypes.c_int, [_vp, _vp, _vp, _vp, _u64, _vp, _vp, _vp]),
+    "tmd_lefevre_bounds": (ctypes.c_int, [_vp, _vp, _vp, _vp, _u64, _vp, _vp, _vp]),
     "tmd_stats_read": (ctypes.c_int, [_vp, ctypes.POINTER(tmd_stats), _vp]),
     "tmd_batch_create": (ctypes.c_int, [_vp, ctypes.POINTER(tmd_job), _u32, _vp, _u64, _vp, _vp,
                                         ctypes.POINTER(_vp), ctypes.POINTER(_u64)]),

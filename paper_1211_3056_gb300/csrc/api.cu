@@ -36,7 +36,7 @@ cudaError_t launch_plan(const DevJob* jobs, uint32_t n_jobs, DevBlock* blocks, u
 
 namespace tmd {
 cudaError_t launch_search_lines(bool raw, const LineArgs& a, cudaStream_t s);
-cudaError_t launch_lower_bounds(const uint64_t* B, const uint64_t* A, const uint32_t* len, uint64_t n,
+cudaError_t launch_lower_bounds(bool lefevre, const uint64_t* B, const uint64_t* A, const uint32_t* len, uint64_t n,
                                 uint64_t* lb, uint32_t* hs, uint32_t* err, cudaStream_t s);
 }  // namespace tmd
 
@@ -619,7 +619,7 @@ tmd_status tmd_search_lines(tmd_ctx* c, const uint64_t* d_B, const uint64_t* d_A
                             uint64_t n, int32_t m, uint32_t flags, tmd_candidate* d_cand,
                             uint64_t cand_cap, uint64_t* d_count, void* stream) {
     if (!c || !d_count || (n && (!d_B || !d_A || !d_len)) || (cand_cap && !d_cand)) return TMD_EINVAL;
-    if (m < 2 || m > 63 || (flags & ~(uint32_t)TMD_ALL_HITS)) return TMD_EINVAL;
+    if (m < 2 || m > 63 || (flags & ~(uint32_t)(TMD_ALL_HITS | TMD_LEFEVRE))) return TMD_EINVAL;
     if (n >= (1ull << 32)) return TMD_EUNSUPPORTED;
     cudaStream_t s = (cudaStream_t)stream;
     CK(cudaSetDevice(c->device));
@@ -649,7 +649,17 @@ tmd_status tmd_lower_bounds(tmd_ctx* c, const uint64_t* d_B, const uint64_t* d_A
     cudaStream_t s = (cudaStream_t)stream;
     CK(cudaSetDevice(c->device));
     CK(cudaMemsetAsync(err_ptr(c), 0, sizeof(uint32_t), s));
-    CK(launch_lower_bounds(d_B, d_A, d_len, n, d_lb, d_hs, err_ptr(c), s));
+    CK(launch_lower_bounds(false, d_B, d_A, d_len, n, d_lb, d_hs, err_ptr(c), s));
+    return TMD_OK;
+}
+
+tmd_status tmd_lefevre_bounds(tmd_ctx* c, const uint64_t* d_B, const uint64_t* d_A, const uint32_t* d_len,
+                              uint64_t n, uint64_t* d_lb, uint32_t* d_iters, void* stream) {
+    if (!c || (n && (!d_B || !d_A || !d_len || !d_lb))) return TMD_EINVAL;
+    cudaStream_t s = (cudaStream_t)stream;
+    CK(cudaSetDevice(c->device));
+    CK(cudaMemsetAsync(err_ptr(c), 0, sizeof(uint32_t), s));
+    CK(launch_lower_bounds(true, d_B, d_A, d_len, n, d_lb, d_iters, err_ptr(c), s));
     return TMD_OK;
 }
 

@@ -391,7 +391,7 @@ tmd_status validate_job(const tmd_job& job) {
     if (job.log2_T - job.log2_N > 16) return TMD_EUNSUPPORTED;
     if (job.d < 1 || job.d > MAX_DEG) return TMD_EUNSUPPORTED;
     if (job.limbs < 1 || job.limbs > MAX_LIMBS) return TMD_EUNSUPPORTED;
-    if (job.flags & ~(uint32_t)(TMD_BP_DIRECTED | TMD_ALL_HITS)) return TMD_EINVAL;
+    if (job.flags & ~(uint32_t)(TMD_BP_DIRECTED | TMD_ALL_HITS | TMD_LEFEVRE)) return TMD_EINVAL;
     if (job.func == TMD_LOG) {
         if (job.e_in < 2 || job.e_in > 16) return TMD_EUNSUPPORTED;
     } else {

@@ -246,6 +246,80 @@ __device__ __forceinline__ uint64_t cf_lower_bound(uint64_t B, uint64_t A, uint3
     return d;
 }
 
+// ------------------------------------------------ Lefevre, Algorithm 3
+// k = floor(a / b) clamped to 2^20 (it only feeds the saturating counts) and
+// a mod b, for any a and b > 0: no division for k <= 1, else an FP32
+// estimate and one correction, else (k >= 2^19) the exact slow division.
+__device__ __forceinline__ uint64_t quot_rem(uint64_t a, uint64_t b, uint32_t& k) {
+    if (a < b) {
+        k = 0;
+        return a;
+    }
+    const uint64_t r1 = a - b;
+    if (r1 < b) {
+        k = 1;
+        return r1;
+    }
+    bool ok;
+    k = quot_estimate(u64_to_f32_rz(a), scaled_rcp(u64_to_f32_rz(b)), ok);
+    uint64_t r = rem_fix(a, b, k);
+    if (!ok) r = divmod_slow(a, b, k);
+    return r;
+}
+
+// Lefevre's lower bound (Algorithm 3, the swap form of Algorithm 1) of
+// min_{0<=x<n} (B - A x) mod 2^64: p <- A, q <- 2^64 - A, d <- B, u <- v <- 1.
+// Each iteration moves d to the point just added at its left when b is on
+// the swapped side (d -= l, l = Algorithm 1's p, held in q after a swap),
+// takes a whole quotient k = floor(q/p) off q (u += k v), the first unit of
+// the next one off p (v += u), and swaps (p, q), (u, v) when b changes side.
+// Returns d at the first u + v >= n; a division leaving a zero remainder
+// ends the loop with d reduced modulo the other length (rational a).
+// *iters = loop iterations (Table 3).  u, v saturate at n.
+__device__ __noinline__ uint64_t lefevre_lower_bound(uint64_t B, uint64_t A, uint32_t n, uint32_t* iters) {
+    if (A == 0) {
+        *iters = 0;
+        return B;
+    }
+    uint64_t p = A, q = 0ull - A, d = B;
+    uint32_t u = 1, v = 1, it = 0;
+    bool sw = false;
+    if (d >= p) {
+        const uint64_t t = p;
+        p = q;
+        q = t;
+        sw = true;
+    }
+#pragma unroll 1
+    for (; it < (1u << 17); ) {  // u + v grows by at least one per iteration
+        it++;
+        if (sw) d -= q;
+        uint32_t k;
+        q = quot_rem(q, p, k);
+        u = sat_madd(u, k, v, n);
+        if (u + v >= n) break;
+        if (q == 0) {
+            uint32_t kk;
+            d = quot_rem(d, p, kk);
+            break;
+        }
+        p -= q;
+        v = min(v + u, n);
+        const uint64_t l = sw ? q : p;
+        if (sw != (d >= l)) {
+            const uint64_t t = p;
+            p = q;
+            q = t;
+            const uint32_t w = u;
+            u = v;
+            v = w;
+            sw = !sw;
+        }
+    }
+    *iters = it;
+    return d;
+}
+
 // -------------------------------------------------------------- compaction
 __device__ __forceinline__ void emit_warp(bool has, uint32_t job, uint32_t sub, uint64_t arg,
                                           uint64_t val, tmd_candidate* cand, uint64_t cap,
@@ -598,6 +672,7 @@ __device__ __forceinline__ void fused_task(const DevTask& t, const LaunchArgs& a
     }
     __syncwarp();
     const uint64_t Tm = a.jobs[t.job].Tm;
+    const bool lefevre = (a.jobs[t.job].flags & TMD_LEFEVRE) != 0;
 #pragma unroll 1
     for (uint32_t r = 0; r < nu; r++) {
         const int s = (int)r * 32 + lane;
@@ -607,7 +682,7 @@ __device__ __forceinline__ void fused_task(const DevTask& t, const LaunchArgs& a
         const uint64_t A = st.A[slot];
         uint32_t hs = 0;
         uint64_t lb = ~0ull;
-        if (n) lb = cf_lower_bound(B, A, n, &hs);
+        if (n) lb = lefevre ? lefevre_lower_bound(B, A, n, &hs) : cf_lower_bound(B, A, n, &hs);
         const bool fail = n && lb < Tm;
         st_lines += n ? 1u : 0u;
         st_fail += fail ? 1u : 0u;
@@ -738,7 +813,7 @@ __global__ void __launch_bounds__(256) k_search_lines(LineArgs a) {
     }
     uint32_t hs = 0;
     uint64_t lb = ~0ull;
-    if (valid) lb = cf_lower_bound(B, A, n, &hs);
+    if (valid) lb = (flags & TMD_LEFEVRE) ? lefevre_lower_bound(B, A, n, &hs) : cf_lower_bound(B, A, n, &hs);
     const bool fail = valid && lb < Tm;
     // all lanes of a warp share ALL_HITS in practice; take the warp's OR
     const bool all_hits = __any_sync(FULLMASK, valid && (flags & TMD_ALL_HITS));
@@ -747,6 +822,7 @@ __global__ void __launch_bounds__(256) k_search_lines(LineArgs a) {
     flush_stats(a.stats, valid ? 1u : 0u, fail ? 1u : 0u, hs);
 }
 
+template <bool LEFEVRE>
 __global__ void __launch_bounds__(256) k_lower_bounds(const uint64_t* B, const uint64_t* A,
                                                       const uint32_t* len, uint64_t n, uint64_t* lb,
                                                       uint32_t* hs_out, uint32_t* err) {
@@ -758,7 +834,7 @@ __global__ void __launch_bounds__(256) k_lower_bounds(const uint64_t* B, const u
         ln = ln == 0 ? 1u : 65536u;
     }
     uint32_t hs = 0;
-    lb[s] = cf_lower_bound(B[s], A[s], ln, &hs);
+    lb[s] = LEFEVRE ? lefevre_lower_bound(B[s], A[s], ln, &hs) : cf_lower_bound(B[s], A[s], ln, &hs);
     if (hs_out) hs_out[s] = hs;
 }
 
@@ -930,10 +1006,13 @@ cudaError_t launch_search_lines(bool raw, const LineArgs& a, cudaStream_t s) {
     return cudaGetLastError();
 }
 
-cudaError_t launch_lower_bounds(const uint64_t* B, const uint64_t* A, const uint32_t* len, uint64_t n,
-                                uint64_t* lb, uint32_t* hs, uint32_t* err, cudaStream_t s) {
+cudaError_t launch_lower_bounds(bool lefevre, const uint64_t* B, const uint64_t* A, const uint32_t* len,
+                                uint64_t n, uint64_t* lb, uint32_t* hs, uint32_t* err, cudaStream_t s) {
     if (n == 0) return cudaSuccess;
-    k_lower_bounds<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(B, A, len, n, lb, hs, err);
+    if (lefevre)
+        k_lower_bounds<true><<<(unsigned)((n + 255) / 256), 256, 0, s>>>(B, A, len, n, lb, hs, err);
+    else
+        k_lower_bounds<false><<<(unsigned)((n + 255) / 256), 256, 0, s>>>(B, A, len, n, lb, hs, err);
     return cudaGetLastError();
 }
 

@@ -1,0 +1,116 @@
+"""GPU parity of Lefevre's filter (Algorithm 3) through the C ABI: the lower
+bound and loop iteration count line by line against the oracle's Algorithm
+1, the search and the fused/batched path with the flag against brute force
+and the oracle's candidate lists, and the loop statistics of Table 3 over a
+whole 2^-13 domain."""
+import random
+import statistics
+
+import pytest
+
+import workloads as wl
+from gpu_util import to_u32_list, to_u64_list, u32_tensor, u64_tensor
+from oracle import candidates as oc
+from oracle import search
+from test_gpu_search import brute_records, clustered_lines, edge_lines, random_lines, sort_by_line
+
+torch = pytest.importorskip("torch")
+tmd = pytest.importorskip("paper_1211_3056_gb300")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    c = tmd.Context(0)
+    yield c
+    c.close()
+
+
+def run_lefevre(ctx, lines):
+    B = u64_tensor([l[0] for l in lines])
+    A = u64_tensor([l[1] for l in lines])
+    n = u32_tensor([l[2] for l in lines])
+    lb = torch.empty_like(B)
+    it = torch.empty_like(n)
+    tmd.tmd_lefevre_bounds(ctx, B, A, n, lb, it)
+    torch.cuda.synchronize()
+    return to_u64_list(lb), to_u32_list(it)
+
+
+@pytest.mark.parametrize("kind", ["edges", "random", "clustered"])
+def test_lefevre_bound_equals_algorithm1(ctx, kind):
+    lines = {"edges": edge_lines, "random": lambda: random_lines(20000, 23),
+             "clustered": lambda: clustered_lines(600, 29)}[kind]()
+    lb, it = run_lefevre(ctx, lines)
+    for (B, A, n), g, h in zip(lines, lb, it):
+        want, _, wit = search.lefevre_lb(B, A, n)
+        assert (g, h) == (want, wit), (hex(B), hex(A), n)
+
+
+@pytest.mark.parametrize("m", [6, 20])
+def test_search_lines_with_lefevre_filter(ctx, m):
+    """Same records as brute force; the filter flags exactly the lines whose
+    Algorithm 1 bound is below the threshold."""
+    lines = random_lines(3000, 300 + m) + edge_lines()
+    B = u64_tensor([l[0] for l in lines])
+    A = u64_tensor([l[1] for l in lines])
+    n = u32_tensor([l[2] for l in lines])
+    d_cand, d_count = tmd.alloc_candidates(len(lines) + 16)
+    tmd.tmd_search_lines(ctx, B, A, n, m, tmd.TMD_LEFEVRE, d_cand, d_count)
+    got, count = tmd.tmd_candidates(ctx, d_cand, d_count)
+    want = brute_records(lines, m)
+    assert count == len(want) and sort_by_line(got) == sort_by_line(want)
+    T = 1 << (65 - m)
+    st = tmd.tmd_stats_read(ctx)
+    assert st["filter_fail"] == sum(1 for (Bv, Av, nv) in lines if search.lefevre_lb(Bv, Av, nv)[0] < T)
+
+
+def test_fused_and_batched_with_lefevre_filter(ctx):
+    jobs = [
+        wl.toy_job(flags=wl.FLAG_LEFEVRE),
+        wl.Job(wl.FUNC_LOG, 2, 30, 14, 8, 3, 14, 2, 12345, 1 << 20, wl.FLAG_LEFEVRE),
+        wl.Job(wl.FUNC_EXP, 0, 53, 20, 14, 3, 24, 3, wl.plain_start(), 1 << 26, wl.FLAG_LEFEVRE),
+        wl.Job(wl.FUNC_EXP2, 1, 24, 16, 8, 2, 12, 1, 0, 1 << 16),           # regular filter in the same batch
+    ]
+    want = oc.candidates(jobs)
+    got, n = tmd.run(jobs, ctx=ctx, fused=True, cap=1 << 16)
+    assert got == want and n == len(want)
+    d_cand, d_count = tmd.alloc_candidates(1 << 16)
+    b = tmd.Batch(ctx, jobs, d_cand, d_count)
+    b.launch()
+    got_b, n_b = tmd.tmd_candidates(ctx, d_cand, d_count)
+    b.close()
+    assert got_b == want and n_b == len(want)
+
+
+def test_table3_statistics_whole_domain(ctx):
+    """Table 3 on the GPU: every one of the 2^24 sub-domains of N = 2^15
+    binary64 arguments of exp in [1, 1+2^-13] (2^19 warps of 32 neighbouring
+    sub-domains), both filters.  Printed: regular 8..19 iterations, mean 12,
+    NMDM 0.1 %; Lefevre 5..328, mean 24, NMDM 25.6 %."""
+    job = wl.Job(wl.FUNC_EXP, 1, 53, 40, 15, 3, 24, 3, 0, 1 << 39)
+    need = tmd.tmd_generate(ctx, [job], None)
+    d_lin = torch.empty(need // 8, dtype=torch.int64, device="cuda:0")
+    tmd.tmd_generate(ctx, [job], d_lin)
+    half = d_lin.numel() // 2
+    assert half == 1 << 24
+    B, A = d_lin[:half], d_lin[half:]
+    n = torch.full((half,), 1 << 15, dtype=torch.int32, device="cuda:0")
+    lb = torch.empty_like(B)
+    it_r = torch.empty_like(n)
+    it_l = torch.empty_like(n)
+    tmd.tmd_lower_bounds(ctx, B, A, n, lb, it_r)
+    tmd.tmd_lefevre_bounds(ctx, B, A, n, lb, it_l)
+    torch.cuda.synchronize()
+
+    def stats(it):
+        w = it.view(-1, 32).double()
+        mx = w.max(dim=1).values
+        nm = 1.0 - w.mean(dim=1) / mx
+        return int(it.min()), int(it.max()), float(it.double().mean()), float(nm.mean())
+    r = stats(it_r)
+    l = stats(it_l)
+    print("regular", r, "lefevre", l)
+    assert 6 <= r[0] <= 10 and 14 <= r[1] <= 25 and 9 <= r[2] <= 13
+    assert 3 <= l[0] <= 10 and 100 <= l[1] <= 2000 and 18 <= l[2] <= 36
+    assert 0.15 <= l[3] <= 0.40 and r[3] < l[3] / 3

@@ -185,3 +185,40 @@ def test_nmdm_definition():
     assert search.nmdm([7] * 32) == 0.0
     assert search.nmdm([0] * 31 + [10]) == pytest.approx(1 - (10 / 32) / 10)
     assert search.nmdm([8, 19, 12, 12]) == pytest.approx(1 - 12.75 / 19)
+
+
+def test_table3_loop_statistics_on_exp_lines():
+    """Table 3: main-loop iterations per thread on exp in [1, 1+2^-13]
+    (binary64, sub-domains of N = 2^15 arguments, 32 neighbouring
+    sub-domains per warp): the regular search takes 8..19 iterations (mean
+    12), Lefevre's 5..328 (mean 24), with a mean NMDM of 25.6 % for
+    Lefevre's.  On a seeded sample of 36 warps of the oracle's own lines the
+    counts fall in those ranges and Lefevre's loop diverges several times
+    more; the regular NMDM comes out near 5 % here, not the printed 0.1 %
+    (neighbouring lines part in their last partial quotient)."""
+    import statistics
+    import workloads as wl
+    from oracle import plan, poly
+    job = wl.Job(wl.FUNC_EXP, 1, 53, 40, 15, 3, 24, 3, 0, 1 << 39)
+    blocks = plan.blocks(job)
+    rng = random.Random(2012)
+    W, N = 64 * job.limbs, 1 << job.log2_N
+    reg, lef, nm_r, nm_l = [], [], [], []
+    for b in rng.sample(range(len(blocks)), 6):
+        blk = blocks[b]
+        c = poly.taylor_coeffs(job, blk)
+        for _ in range(6):
+            i0 = rng.randrange(0, (blk.length // N) // 32) * 32
+            r, l = [], []
+            for i in range(i0, i0 + 32):
+                B, A = poly.search_words(*poly.line(c, i, N, W), job.m, W)
+                r.append(search.regular_lb_unrolled(B, A, N)[2])
+                l.append(search.lefevre_lb(B, A, N)[2])
+            reg += r
+            lef += l
+            nm_r.append(search.nmdm(r))
+            nm_l.append(search.nmdm(l))
+    assert 8 <= min(reg) and max(reg) <= 19 and 9 <= statistics.mean(reg) <= 13
+    assert 5 <= min(lef) and max(lef) <= 328 and 18 <= statistics.mean(lef) <= 36
+    assert 0.15 <= statistics.mean(nm_l) <= 0.40
+    assert statistics.mean(nm_r) < statistics.mean(nm_l) / 3

@@ -19,7 +19,8 @@ Field meanings:
   start   first argument index j (X = 2^(e_in-1) + j*2^(e_in-p))
   count   number of consecutive arguments
   flags   FLAG_BP_DIRECTED selects scale 2^p instead of 2^(p+1);
-          FLAG_ALL_HITS reports every argument below the threshold
+          FLAG_ALL_HITS reports every argument below the threshold;
+          FLAG_LEFEVRE filters with Lefevre's bound (Algorithm 3)
 """
 from __future__ import annotations
 
@@ -33,6 +34,7 @@ FUNC_NAMES = {FUNC_EXP: "exp", FUNC_EXP2: "exp2", FUNC_LOG: "log"}
 
 FLAG_BP_DIRECTED = 1
 FLAG_ALL_HITS = 2
+FLAG_LEFEVRE = 4
 
 
 @dataclasses.dataclass(frozen=True)

@@ -28,6 +28,7 @@ from __future__ import annotations
 
 import argparse
 import json
+import math
 import os
 import statistics
 import subprocess
@@ -63,7 +64,7 @@ OPS_PER_HALF_STEP = 35
 # k_persistent<3,3> on this 2^36 workload, from one single-pass ncu capture of
 # the kernel as it stands; None until the kernel's current form is captured,
 # and reset to None whenever that kernel changes.
-TRAFFIC_BYTES_PER_LAUNCH = 1_405_696
+TRAFFIC_BYTES_PER_LAUNCH = None
 
 
 def ops_per_line(job) -> int:
@@ -272,6 +273,8 @@ def main():
                     help="jobs of the seeded serving stream to serve (0 = skip)")
     ap.add_argument("--count-log2", type=int, default=36,
                     help="slice size (smaller only for profiling captures)")
+    ap.add_argument("--sound", type=int, default=1,
+                    help="also time the sound-mode search of exp on [1, 1+2^-13[ (0 = skip)")
     ap.add_argument("--lefevre", type=int, default=1,
                     help="also time the same slice with Lefevre's filter (0 = skip)")
     ap.add_argument("--tiling", default="auto",
@@ -433,6 +436,25 @@ def main():
                    "form": "batched, Lefevre's lower bound (Algorithm 3) as the filter"}
         lbatch.close()
 
+    # sound mode on Table 2's domain: exp on [1, 1+2^-13[ (2^39 binary64
+    # arguments), directed (53, 2^-32) cases: filter at eps1, exhaustive
+    # phase at eps3 (Sect. II-A / III-A), one batched launch
+    sound_run = None
+    if args.sound:
+        sjob = tmd.sound_job(wl.Job(wl.FUNC_EXP, 1, 53, 32, 15, 3, 24, 3, 0, 1 << 39, wl.FLAG_BP_DIRECTED))
+        d_cand_s, d_count_s = tmd.alloc_candidates(1 << 16, local_rank)
+        sb = tmd.Batch(ctx, [sjob], d_cand_s, d_count_s)
+        s_ms = max_over_ranks(statistics.mean(timed(sb.launch, 10, 3)))
+        sst = sb.stats()
+        _, s_count = tmd.tmd_candidates(ctx, d_cand_s, d_count_s)
+        sound_run = {"workload": "exp binary64 [1, 1+2^-13[ (2^39 args), directed (53, 2^-32) cases, "
+                                 "d=3, W=192, N=2^15", "value": sjob.count / (s_ms / 1e3), "unit": UNIT,
+                     "ms_per_step": s_ms, "listed_arguments": s_count,
+                     "eps1_log2": math.log2(sjob.eps1) - 64, "eps3_log2": math.log2(sjob.eps3) - 64,
+                     "filter_fail_per_line": sst["filter_fail"] / max(1, sst["lines"]),
+                     "form": "batched, sound filter then exhaustive evaluation of the flagged lines"}
+        sb.close()
+
     mixed = None
     if args.mixed_jobs > 0:
         mjobs = wl.batched_jobs(njobs=args.mixed_jobs)
@@ -520,6 +542,7 @@ def main():
                     "d2h_bytes_per_step": d2h, "ms_per_step": e2e_s * 1e3},
             "gpu_launches": args.steps * 1,
             "roofline": roofline, "cpu_baseline": cpu, "clocks": clocks, "lefevre": lefevre,
+            "sound_table2": sound_run,
             "mixed_batch": mixed,
             "large_batch": large,
             "serving": serving,

@@ -60,6 +60,21 @@ typedef enum { TMD_EXP = 0, TMD_EXP2 = 1, TMD_LOG = 2 } tmd_func;
                                (Sect. II-A).                                          */
 #define TMD_ALL_HITS 2u     /* report every argument below the threshold, not only the
                                minimum of each sub-interval                            */
+#define TMD_SOUND 8u        /* sound mode (Sect. II-A's eps'' = eps + eps_approx +
+                               eps_trunc, then Sect. III-A's exhaustive phase): the
+                               filter tests each line against the job's eps1 instead
+                               of 2^-m; a line whose exact minimum is below 2 eps1 has
+                               its block polynomial R_t evaluated at every argument
+                               (tabulated differences of step 32 from the stored Taylor
+                               coefficients), and every argument with
+                               (top64(R_t(y)) + eps3) mod 2^64 < 2 eps3 is reported
+                               (record value = that quantity).  With eps1, eps3 from
+                               tmd_sound_eps (or any larger values) every argument
+                               whose s f(X) lies within 2^-m of a breakpoint is
+                               reported: the list to re-check exactly (Ziv).  Not
+                               with TMD_ALL_HITS; fused and batched forms, the server
+                               and the allocation-free entry (not the unfused
+                               tmd_generate + tmd_search pair).                      */
 #define TMD_LEFEVRE 4u      /* filter with Lefevre's lower bound (Algorithm 3, the swap
                                form of Algorithm 1) instead of the regular one
                                (Algorithm 4).  The records do not change (flagged lines
@@ -82,8 +97,14 @@ typedef struct {
     uint32_t limbs;     /* fixed-point width W = 64 * limbs bits               */
     uint64_t start;     /* first argument index                                */
     uint64_t count;     /* number of arguments                                 */
-    uint32_t flags;     /* TMD_BP_DIRECTED | TMD_ALL_HITS | TMD_LEFEVRE        */
+    uint32_t flags;     /* TMD_BP_DIRECTED | TMD_ALL_HITS | TMD_LEFEVRE |
+                           TMD_SOUND                                           */
     uint32_t reserved;  /* must be 0                                           */
+    uint64_t eps1;      /* TMD_SOUND only: the filter's half-width eps'' on the
+                           64-bit words (units of 2^-64 of the breakpoint
+                           spacing); eps3 + N + 2 <= eps1 < 2^62               */
+    uint64_t eps3;      /* TMD_SOUND only: the exhaustive phase's half-width,
+                           2^(64-m) <= eps3; both 0 otherwise                  */
 } tmd_job;
 
 /* One reported sub-interval (or argument, with TMD_ALL_HITS): the index of the
@@ -106,6 +127,21 @@ typedef struct {
     int32_t  e_out_first;    /* e(f(X)) at the first argument                  */
     uint64_t cut[4];         /* first argument index of segments 1..3          */
 } tmd_plan_info;
+
+/* Sound thresholds of a job (host only; no device call): eps3 =
+ * 2^(64-m) + eps_approx + margin, eps1 = eps3 + eps_trunc + N + margin, in
+ * units of 2^-64 of the breakpoint spacing, where (Sect. II-A)
+ *   eps_approx bounds |R_t(y)/2^W - s f(X)| over the job: the degree-d Taylor
+ *     remainder over a block of T arguments, s (u T)^(d+1) max|f^(d+1)|/(d+1)!,
+ *     plus the rounding of the d+1 coefficients;
+ *   eps_trunc bounds the degree >= 2 terms of R_t(iN + x) = sum_j r_j(i)
+ *     binom(x, j) (Sect. IV-A) that the degree-1 line drops, x < N, from
+ *     |c_k| <= 2^W s u^k max|f^(k)|/k! + 1/2;
+ *   N + 2 covers the truncation of the line to 64-bit words.
+ * Computed in double precision with a relative margin of 2^-10 and a few
+ * units, so that the values are never below the exact bounds.  Fills
+ * *eps1, *eps3; TMD_EINVAL if the job is invalid or the bounds exceed 2^61. */
+tmd_status tmd_sound_eps(const tmd_job* job, uint64_t* eps1, uint64_t* eps3);
 
 /* Per-block description returned by tmd_block_tables. */
 typedef struct {

@@ -12,7 +12,7 @@ import ctypes
 from typing import List, Optional, Sequence, Tuple
 
 from . import _lib
-from ._lib import (TMD_ALL_HITS, TMD_BP_DIRECTED, TMD_LEFEVRE, TMD_EXP, TMD_EXP2, TMD_LOG, TMD_OK,  # noqa: F401
+from ._lib import (TMD_ALL_HITS, TMD_BP_DIRECTED, TMD_LEFEVRE, TMD_SOUND, TMD_EXP, TMD_EXP2, TMD_LOG, TMD_OK,  # noqa: F401
                    TMD_EOVERFLOW, TmdError, check, job_array, lib, make_job)
 
 lib()  # fail loudly at import when the extension is missing
@@ -150,6 +150,20 @@ def tmd_search_lines(ctx: Context, d_B, d_A, d_len, m: int, flags: int, d_cand, 
 def tmd_lower_bounds(ctx: Context, d_B, d_A, d_len, d_lb, d_hs=None, stream=None) -> None:
     check(lib().tmd_lower_bounds(ctx.handle, _ptr(d_B), _ptr(d_A), _ptr(d_len), d_B.numel(),
                                  _ptr(d_lb), _ptr(d_hs), _stream_ptr(stream)), "tmd_lower_bounds")
+
+
+def tmd_sound_eps(job) -> tuple:
+    """(eps1, eps3): the sound thresholds of a job on the 64-bit words (host)."""
+    j = make_job(job)
+    e1, e3 = ctypes.c_uint64(0), ctypes.c_uint64(0)
+    check(lib().tmd_sound_eps(ctypes.byref(j), ctypes.byref(e1), ctypes.byref(e3)), "tmd_sound_eps")
+    return e1.value, e3.value
+
+
+def sound_job(job):
+    """The job in sound mode with the library's sound thresholds."""
+    e1, e3 = tmd_sound_eps(job)
+    return job.replace(flags=job.flags | TMD_SOUND, eps1=e1, eps3=e3)
 
 
 def tmd_lefevre_bounds(ctx: Context, d_B, d_A, d_len, d_lb, d_iters=None, stream=None) -> None:

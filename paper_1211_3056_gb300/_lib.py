@@ -13,6 +13,7 @@ TMD_EXP, TMD_EXP2, TMD_LOG = 0, 1, 2
 TMD_BP_DIRECTED = 1
 TMD_ALL_HITS = 2
 TMD_LEFEVRE = 4
+TMD_SOUND = 8
 
 
 class TmdError(RuntimeError):
@@ -25,7 +26,8 @@ class tmd_job(ctypes.Structure):
     _fields_ = [("func", ctypes.c_int32), ("e_in", ctypes.c_int32), ("p", ctypes.c_int32),
                 ("m", ctypes.c_int32), ("log2_N", ctypes.c_uint32), ("d", ctypes.c_int32),
                 ("log2_T", ctypes.c_uint32), ("limbs", ctypes.c_uint32), ("start", ctypes.c_uint64),
-                ("count", ctypes.c_uint64), ("flags", ctypes.c_uint32), ("reserved", ctypes.c_uint32)]
+                ("count", ctypes.c_uint64), ("flags", ctypes.c_uint32), ("reserved", ctypes.c_uint32),
+                ("eps1", ctypes.c_uint64), ("eps3", ctypes.c_uint64)]
 
 
 class tmd_candidate(ctypes.Structure):
@@ -90,6 +92,7 @@ SIGNATURES = {
     "tmd_search_lines": (ctypes.c_int, [_vp, _vp, _vp, _vp, _u64, _i32, _u32, _vp, _u64, _vp, _vp]),
     "tmd_lower_bounds": (ctypes.c_int, [_vp, _vp, _vp, _vp, _u64, _vp, _vp, _vp]),
     "tmd_lefevre_bounds": (ctypes.c_int, [_vp, _vp, _vp, _vp, _u64, _vp, _vp, _vp]),
+    "tmd_sound_eps": (ctypes.c_int, [ctypes.POINTER(tmd_job), ctypes.POINTER(_u64), ctypes.POINTER(_u64)]),
     "tmd_stats_read": (ctypes.c_int, [_vp, ctypes.POINTER(tmd_stats), _vp]),
     "tmd_batch_create": (ctypes.c_int, [_vp, ctypes.POINTER(tmd_job), _u32, _vp, _u64, _vp, _vp,
                                         ctypes.POINTER(_vp), ctypes.POINTER(_u64)]),
@@ -148,7 +151,7 @@ def check(status: int, where: str, ok=(TMD_OK,)):
 def make_job(job) -> tmd_job:
     """tmd_job from any object with the descriptor fields (e.g. workloads.Job)."""
     return tmd_job(job.func, job.e_in, job.p, job.m, job.log2_N, job.d, job.log2_T, job.limbs,
-                   job.start, job.count, job.flags, 0)
+                   job.start, job.count, job.flags, 0, getattr(job, "eps1", 0), getattr(job, "eps3", 0))
 
 
 def job_array(jobs):

@@ -23,9 +23,9 @@
 #include "planrec.cuh"
 
 namespace tmd {
-cudaError_t launch_tasks(bool fused, uint32_t L, uint32_t D, const LaunchArgs& a, cudaStream_t s);
-cudaError_t launch_persistent(uint32_t L, uint32_t D, const LaunchArgs& a, int ctas, cudaStream_t s);
-cudaError_t persistent_occupancy(uint32_t L, uint32_t D, int* blocks_per_sm);
+cudaError_t launch_tasks(bool fused, uint32_t L, uint32_t D, bool G, const LaunchArgs& a, cudaStream_t s);
+cudaError_t launch_persistent(uint32_t L, uint32_t D, bool G, const LaunchArgs& a, int ctas, cudaStream_t s);
+cudaError_t persistent_occupancy(uint32_t L, uint32_t D, bool G, int* blocks_per_sm);
 cudaError_t upload_coeff_consts(const CoeffConsts& C);
 cudaError_t launch_block_tables(const DevJob* jobs, const DevBlock* blocks, uint64_t n_blocks, uint64_t* tables,
                                 uint32_t* status, uint32_t* err, cudaStream_t s);
@@ -46,6 +46,7 @@ namespace {
 
 struct ClassRange {
     uint32_t L, D;
+    bool G;                 // general kernel variant (Lefevre filter or sound mode)
     uint64_t first, count;  // task range
 };
 
@@ -192,7 +193,11 @@ tmd_status build_plan(const tmd_job* jobs, uint32_t njobs, Plan& P, bool host_ta
         segs.assign(seg_of[j].begin(), seg_of[j].begin() + nseg_of[j]);
         DevJob dj;
         memset(&dj, 0, sizeof dj);
-        dj.Tm = 1ull << (65 - jb.m);
+        const bool sound = (jb.flags & TMD_SOUND) != 0;
+        dj.shift = sound ? jb.eps1 : 1ull << (64 - jb.m);
+        dj.Tm = 2 * dj.shift;
+        dj.shift3 = sound ? jb.eps3 : 0;
+        dj.T3 = 2 * dj.shift3;
         dj.log2_N = jb.log2_N;
         dj.log2_T = jb.log2_T;
         dj.d = (uint32_t)jb.d;
@@ -206,7 +211,9 @@ tmd_status build_plan(const tmd_job* jobs, uint32_t njobs, Plan& P, bool host_ta
         const uint64_t SB = T >> jb.log2_N;  // sub-intervals of a full block
         dj.nu = choose_nu(jb, SB, nu_max);
         dj.ppb = (uint32_t)((SB + dj.nu - 1) / dj.nu);
-        dj.words = (uint32_t)((2 * jb.d + 1) * jb.limbs);
+        // the 2d+1 step-N difference words, then (sound mode) the d+1
+        // Taylor coefficients of the exhaustive phase
+        dj.words = (uint32_t)(((sound ? 3 : 2) * jb.d + (sound ? 2 : 1)) * jb.limbs);
         dj.n_seg = (uint32_t)segs.size();
         uint64_t nb = 0, ns = 0, np = 0;
         for (size_t k = 0; k < segs.size(); k++) {
@@ -241,21 +248,24 @@ tmd_status build_plan(const tmd_job* jobs, uint32_t njobs, Plan& P, bool host_ta
     P.total_lines = line;
     P.table_words = toff;
     P.n_blocks = nblk_total;
-    // tasks class by class, job by job (stable)
+    // tasks class by class, job by job (stable); a class is (limbs, degree,
+    // kernel variant: general when the job uses Lefevre's filter or the
+    // sound mode)
     uint64_t task = 0;
-    for (uint32_t key = 0; key < 8 * (MAX_LIMBS + 1); key++) {
+    for (uint32_t key = 0; key < 16 * (MAX_LIMBS + 1); key++) {
         const uint64_t first = task;
         uint32_t Lk = 0, Dk = 0;
         for (uint32_t j = 0; j < njobs; j++) {
             const DevJob& dj = P.jobs[j];
-            if (dj.L * 8 + dj.d != key) continue;
+            const uint32_t g = (dj.flags & (TMD_LEFEVRE | TMD_SOUND)) ? 1u : 0u;
+            if ((dj.L * 8 + dj.d) * 2 + g != key) continue;
             P.class_jobs.push_back(j);
             P.class_task0.push_back(task);
             task += (dj.n_packets + 31) / 32;
             Lk = dj.L;
             Dk = dj.d;
         }
-        if (task > first) P.classes.push_back(ClassRange{Lk, Dk, first, task - first});
+        if (task > first) P.classes.push_back(ClassRange{Lk, Dk, (key & 1) != 0, first, task - first});
     }
     P.n_tasks = task;
     if (!host_tables) return TMD_OK;
@@ -298,7 +308,10 @@ tmd_status build_plan(const tmd_job* jobs, uint32_t njobs, Plan& P, bool host_ta
                 bp.length = db.length;
                 bp.first_sub = db.first_sub;
                 bp.e_out = db.e_out;
-                if (block_table(jobs[db.job], bp, nullptr, &P.tables[db.table_off], &anchors[db.job]) != TMD_OK)
+                const tmd_job& bj = jobs[db.job];
+                uint64_t* tw = &P.tables[db.table_off];
+                uint64_t* cw = (bj.flags & TMD_SOUND) ? tw + (2 * bj.d + 1) * bj.limbs : nullptr;
+                if (block_table(bj, bp, cw, tw, &anchors[db.job]) != TMD_OK)
                     bad.store(1);
             }
         }
@@ -501,6 +514,11 @@ tmd_status tmd_plan(const tmd_job* job, tmd_plan_info* info) {
     return TMD_OK;
 }
 
+tmd_status tmd_sound_eps(const tmd_job* job, uint64_t* eps1, uint64_t* eps3) {
+    if (!job || !eps1 || !eps3) return TMD_EINVAL;
+    return sound_eps(*job, eps1, eps3);
+}
+
 tmd_status tmd_block_tables(const tmd_job* job, uint64_t block, uint64_t* coeffs, uint64_t* table,
                             tmd_block_info* info) {
     if (!job) return TMD_EINVAL;
@@ -541,7 +559,7 @@ tmd_status tmd_generate(tmd_ctx* c, const tmd_job* jobs, uint32_t njobs, void* d
         LaunchArgs a = base;
         a.tasks = base.tasks + cr.first;
         a.n_tasks = cr.count;
-        CK(launch_tasks(false, cr.L, cr.D, a, s));
+        CK(launch_tasks(false, cr.L, cr.D, cr.G, a, s));
     }
     return TMD_OK;
 }
@@ -549,6 +567,9 @@ tmd_status tmd_generate(tmd_ctx* c, const tmd_job* jobs, uint32_t njobs, void* d
 tmd_status tmd_search(tmd_ctx* c, const tmd_job* jobs, uint32_t njobs, const void* d_lin,
                       tmd_candidate* d_cand, uint64_t cand_cap, uint64_t* d_count, void* stream) {
     if (!c || !jobs || njobs == 0 || !d_count || (cand_cap && !d_cand)) return TMD_EINVAL;
+    if (d_lin)  // the exhaustive phase of sound mode needs the fused kernels' block state
+        for (uint32_t j = 0; j < njobs; j++)
+            if (jobs[j].flags & TMD_SOUND) return TMD_EUNSUPPORTED;
     cudaStream_t s = (cudaStream_t)stream;
     CK(cudaSetDevice(c->device));
     tmd_status st = make_resident(c, jobs, njobs, s);
@@ -581,7 +602,7 @@ tmd_status tmd_search(tmd_ctx* c, const tmd_job* jobs, uint32_t njobs, const voi
         LaunchArgs a = base;
         a.tasks = base.tasks + cr.first;
         a.n_tasks = cr.count;
-        CK(launch_tasks(true, cr.L, cr.D, a, s));
+        CK(launch_tasks(true, cr.L, cr.D, cr.G, a, s));
     }
     return TMD_OK;
 }
@@ -685,7 +706,7 @@ tmd_status tmd_stats_read(tmd_ctx* c, tmd_stats* out, void* stream) {
 }  // extern "C"
 
 // batch counters: stats[4] | error | unused | plan error | pad | queue heads (one per class)
-enum { BATCH_MISC_BYTES = 128, BATCH_QUEUE_OFF = 64 };
+enum { BATCH_MISC_BYTES = 192, BATCH_QUEUE_OFF = 64 };
 
 struct tmd_batch {
     tmd_ctx* ctx = nullptr;
@@ -772,7 +793,8 @@ tmd_status tmd_autotune(tmd_ctx* c, const tmd_job* jobs, uint32_t njobs, void* s
     for (uint32_t j = 0; j < njobs; j++) {
         int per_sm = 0;
         if (jobs[j].limbs >= 1 && jobs[j].limbs <= 3 && jobs[j].d >= 1 && jobs[j].d <= 4 &&
-            persistent_occupancy(jobs[j].limbs, (uint32_t)jobs[j].d, &per_sm) == cudaSuccess)
+            persistent_occupancy(jobs[j].limbs, (uint32_t)jobs[j].d, (jobs[j].flags & (TMD_LEFEVRE | TMD_SOUND)) != 0,
+                                 &per_sm) == cudaSuccess)
             occ = std::max(occ, per_sm);
     }
     uint64_t* d_cnt = nullptr;
@@ -896,8 +918,8 @@ tmd_status batch_create(tmd_ctx* c, const tmd_job* jobs, uint32_t njobs, tmd_can
     }
     cudaMemsetAsync(b->d_misc, 0, BATCH_MISC_BYTES, b->cap_stream);
     cudaMemsetAsync(d_count, 0, sizeof(uint64_t), b->cap_stream);
-    static_assert(BATCH_QUEUE_OFF + 4 * 3 * 4 <= BATCH_MISC_BYTES, "one queue head per class");
-    if (P.classes.size() > 12) {
+    static_assert(BATCH_QUEUE_OFF + 4 * 3 * 4 * 2 <= BATCH_MISC_BYTES, "one queue head per class");
+    if (P.classes.size() > 24) {
         cudaStreamEndCapture(b->cap_stream, &b->graph);
         batch_free(b);
         return TMD_EUNSUPPORTED;
@@ -905,7 +927,7 @@ tmd_status batch_create(tmd_ctx* c, const tmd_job* jobs, uint32_t njobs, tmd_can
     for (size_t ci = 0; ci < P.classes.size(); ci++) {
         const ClassRange& cr = P.classes[ci];
         int per_sm = 0;
-        if (persistent_occupancy(cr.L, cr.D, &per_sm) != cudaSuccess || per_sm < 1) per_sm = 1;
+        if (persistent_occupancy(cr.L, cr.D, cr.G, &per_sm) != cudaSuccess || per_sm < 1) per_sm = 1;
         if (tiling.ctas_per_sm) per_sm = std::min(per_sm, (int)tiling.ctas_per_sm);
         b->tiling.ctas_per_sm = std::max(b->tiling.ctas_per_sm, (uint32_t)per_sm);
         const uint64_t want = (cr.count + 7) / 8;
@@ -913,8 +935,8 @@ tmd_status batch_create(tmd_ctx* c, const tmd_job* jobs, uint32_t njobs, tmd_can
         LaunchArgs ac = a;
         ac.tasks = (const DevTask*)(b->d_arena + o_tasks) + cr.first;
         ac.n_tasks = cr.count;
-        ac.queue_head = (uint32_t*)((char*)b->d_misc + BATCH_QUEUE_OFF) + ci;  // ci < 12: inside the 128 B
-        launch_persistent(cr.L, cr.D, ac, ctas, b->cap_stream);
+        ac.queue_head = (uint32_t*)((char*)b->d_misc + BATCH_QUEUE_OFF) + ci;  // ci < 24: inside the 192 B
+        launch_persistent(cr.L, cr.D, cr.G, ac, ctas, b->cap_stream);
     }
     if (cudaStreamEndCapture(b->cap_stream, &b->graph) != cudaSuccess ||
         cudaGraphInstantiate(&b->exec, b->graph, 0) != cudaSuccess) {
@@ -1099,7 +1121,7 @@ tmd_status slot_launch_chunk(tmd_server* S, Slot& sl) {
         a.count = (uint64_t*)(sl.d_meta + META_COUNT_OFF);
         a.stats = (uint64_t*)sl.d_meta;
         a.queue_head = (uint32_t*)(sl.d_meta + sizeof(uint64_t) * ST_COUNT) + 1;
-        CK(launch_tasks(true, cr.L, cr.D, a, sl.stream));
+        CK(launch_tasks(true, cr.L, cr.D, cr.G, a, sl.stream));
         sl.class_pos += n;
         if (sl.class_pos >= cr.count) {
             sl.class_idx++;
@@ -1449,7 +1471,7 @@ tmd_status tmd_search_static(const tmd_job* jobs, uint32_t njobs, tmd_candidate*
         LaunchArgs la = a;
         la.tasks = a.tasks + cr.first;
         la.n_tasks = cr.count;
-        CK(launch_tasks(true, cr.L, cr.D, la, s));
+        CK(launch_tasks(true, cr.L, cr.D, cr.G, la, s));
     }
     return TMD_OK;
 }

@@ -38,6 +38,9 @@ struct DevJob {
     int32_t seg_e_out[4];
     uint32_t log2_T;
     uint32_t pad;
+    uint64_t shift;        // added to the top word of b: 2^(64-m), or eps1 in sound mode (Tm = 2 shift)
+    uint64_t shift3;       // sound mode: the exhaustive phase's half-width eps3 (T3 = 2 eps3)
+    uint64_t T3;
 };
 
 // One Taylor block.

@@ -8,6 +8,8 @@
 // enclosure round to the same integer; otherwise P grows (Ziv's strategy).
 #include "host.hpp"
 
+#include <algorithm>
+#include <cmath>
 #include <cstring>
 
 #include "bigint.hpp"
@@ -391,7 +393,15 @@ tmd_status validate_job(const tmd_job& job) {
     if (job.log2_T - job.log2_N > 16) return TMD_EUNSUPPORTED;
     if (job.d < 1 || job.d > MAX_DEG) return TMD_EUNSUPPORTED;
     if (job.limbs < 1 || job.limbs > MAX_LIMBS) return TMD_EUNSUPPORTED;
-    if (job.flags & ~(uint32_t)(TMD_BP_DIRECTED | TMD_ALL_HITS | TMD_LEFEVRE)) return TMD_EINVAL;
+    if (job.flags & ~(uint32_t)(TMD_BP_DIRECTED | TMD_ALL_HITS | TMD_LEFEVRE | TMD_SOUND)) return TMD_EINVAL;
+    if (job.flags & TMD_SOUND) {
+        if (job.flags & TMD_ALL_HITS) return TMD_EINVAL;
+        if (job.eps3 < (1ull << (64 - job.m)) || job.eps1 >= (1ull << 62) ||
+            job.eps1 < job.eps3 + (1ull << job.log2_N) + 2)
+            return TMD_EINVAL;
+    } else if (job.eps1 || job.eps3) {
+        return TMD_EINVAL;
+    }
     if (job.func == TMD_LOG) {
         if (job.e_in < 2 || job.e_in > 16) return TMD_EUNSUPPORTED;
     } else {
@@ -585,6 +595,70 @@ tmd_status block_table(const tmd_job& job, const BlockPlan& blk, uint64_t* coeff
     if (coeffs)
         for (int i = 0; i < (job.d + 1) * (int)job.limbs; i++) coeffs[i] = c[i];
     if (table) block_table_words(J, c, table);
+    return TMD_OK;
+}
+
+// ------------------------------------------------------------ sound mode
+// Upper bound of |f^(k)| over [x_lo, x_hi] (k >= 1 for log), in double with
+// a relative margin.
+static double deriv_max(int func, int k, double x_lo, double x_hi) {
+    double v;
+    if (func == TMD_EXP) {
+        v = std::exp(x_hi);
+    } else if (func == TMD_EXP2) {
+        v = std::exp2(x_hi) * std::pow(std::log(2.0), (double)k);
+    } else {
+        double f = 1;
+        for (int i = 2; i < k; i++) f *= i;  // (k-1)!
+        v = k == 0 ? std::log(x_hi) : f / std::pow(x_lo, (double)k);
+    }
+    return v * (1.0 + 1e-9);
+}
+
+tmd_status sound_eps(const tmd_job& job, uint64_t* eps1, uint64_t* eps3) {
+    tmd_job j = job;
+    j.flags &= ~(uint32_t)TMD_SOUND;
+    j.eps1 = j.eps3 = 0;
+    tmd_status st = validate_job(j);
+    if (st != TMD_OK) return st;
+    std::vector<Segment> segs;
+    st = plan_segments(j, segs);
+    if (st != TMD_OK) return st;
+    int e_min = segs[0].e_out;
+    for (const Segment& s : segs) e_min = std::min(e_min, s.e_out);
+    const int d = j.d, W = 64 * (int)j.limbs;
+    const double u = std::ldexp(1.0, j.e_in - j.p);
+    const double x_lo = std::ldexp((double)arg_mantissa(j, j.start), j.e_in - j.p);
+    const double x_hi = std::ldexp((double)arg_mantissa(j, j.start + j.count - 1), j.e_in - j.p);
+    const int s_log2 = scale_log2(j, e_min);
+    const double T = std::ldexp(1.0, (int)j.log2_T), N = std::ldexp(1.0, (int)j.log2_N);
+    double fact[8] = {1, 1, 2, 6, 24, 120, 720, 5040};
+    // eps_approx * 2^64: Taylor remainder plus coefficient rounding
+    double ea = std::ldexp(std::pow(u * T, d + 1) * deriv_max(j.func, d + 1, x_lo, x_hi) / fact[d + 1],
+                           s_log2 + 64);
+    for (int k = 0; k <= d; k++) ea += std::ldexp(0.5 * std::pow(T, k), 64 - W);
+    // eps_trunc * 2^64: dropped terms j >= 2 of the binomial expansion
+    double cb[8];
+    for (int k = 2; k <= d; k++)
+        cb[k] = std::ldexp(std::pow(u, k) * deriv_max(j.func, k, x_lo, x_hi) / fact[k], s_log2 + W) + 0.5;
+    double et = 0;
+    for (int jj = 2; jj <= d; jj++) {
+        double rj = 0;
+        for (int k = jj; k <= d; k++) rj += cb[k] * fact[k] / fact[k - jj] * std::pow(T + d, k - jj);
+        double binom = 1;
+        for (int i = 0; i < jj; i++) binom *= (N - 1 - i) / (i + 1);
+        et += rj * binom;
+    }
+    et = std::ldexp(et, 64 - W);
+    const double margin = 1.0 + 1.0 / 1024;
+    ea = ea * margin + 4;
+    et = et * margin + 4;
+    if (!(ea < 0x1p61) || !(et < 0x1p61)) return TMD_EINVAL;
+    const uint64_t e3 = (1ull << (64 - j.m)) + (uint64_t)std::ceil(ea) + 1;
+    const uint64_t e1 = e3 + (uint64_t)std::ceil(et) + (1ull << j.log2_N) + 2;
+    if (e1 >= (1ull << 62)) return TMD_EINVAL;
+    *eps1 = e1;
+    *eps3 = e3;
     return TMD_OK;
 }
 

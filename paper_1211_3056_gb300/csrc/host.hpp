@@ -22,6 +22,8 @@ struct BlockPlan {
 
 // Validation of one job (domain of this build); TMD_OK when usable.
 tmd_status validate_job(const tmd_job& job);
+// The sound thresholds (eps1, eps3) of a job, on the 64-bit words.
+tmd_status sound_eps(const tmd_job& job, uint64_t* eps1, uint64_t* eps3);
 
 // e(f(X_j)) (Def. 1) for argument index j.
 int output_exponent(const tmd_job& job, uint64_t j);

@@ -53,6 +53,21 @@ __device__ __forceinline__ void w_add(Word<L>& a, const Word<L>& b) {
     }
 }
 
+template <int L>
+__device__ __forceinline__ void w_sub(Word<L>& a, const Word<L>& b) {
+    if constexpr (L == 1) {
+        a.l[0] -= b.l[0];
+    } else if constexpr (L == 2) {
+        asm("sub.cc.u64 %0, %0, %2;\n\tsubc.u64 %1, %1, %3;"
+            : "+l"(a.l[0]), "+l"(a.l[1])
+            : "l"(b.l[0]), "l"(b.l[1]));
+    } else {
+        asm("sub.cc.u64 %0, %0, %3;\n\tsubc.cc.u64 %1, %1, %4;\n\tsubc.u64 %2, %2, %5;"
+            : "+l"(a.l[0]), "+l"(a.l[1]), "+l"(a.l[2])
+            : "l"(b.l[0]), "l"(b.l[1]), "l"(b.l[2]));
+    }
+}
+
 // a * c mod 2^W
 template <int L>
 __device__ __forceinline__ Word<L> w_mul_u64(const Word<L>& a, uint64_t c) {
@@ -607,14 +622,76 @@ __device__ __forceinline__ void packet_step(Packet<L, D>& P) {
     for (int l = 0; l + 1 < D; l++) w_add<L>(P.d1[l], P.d1[l + 1]);
 }
 
-// search words of the current line (top limb of b + 2^(W-m), top limb of -alpha)
+// search words of the current line (top limb of b plus the shift -- 2^(64-m),
+// or eps1 in sound mode --, top limb of -alpha)
 template <int L, int D>
-__device__ __forceinline__ void packet_words(const Packet<L, D>& P, uint32_t m, uint64_t& B, uint64_t& A) {
-    B = P.d0[0].l[L - 1] + (1ull << (64 - m));
+__device__ __forceinline__ void packet_words(const Packet<L, D>& P, uint64_t shift, uint64_t& B, uint64_t& A) {
+    B = P.d0[0].l[L - 1] + shift;
     uint64_t low = 0;
 #pragma unroll
     for (int l = 0; l + 1 < L; l++) low |= P.d1[0].l[l];
     A = ~P.d1[0].l[L - 1] + (low == 0 ? 1ull : 0ull);
+}
+
+// Sound mode, the exhaustive phase (Sect. III-A phase 3): each line of the
+// warp that failed the filter and whose exact minimum is below 2 eps1 has
+// its block polynomial R_t evaluated at every argument y = iN + x, x < n,
+// by the whole warp: lane l starts at y0 = iN + l with the step-32 forward
+// differences of R_t (from the block's Taylor coefficients by Horner at
+// y0, y0 + 32, ..., y0 + 32 D) and steps them; every argument with
+// (top64(R_t(y)) + eps3) mod 2^64 < 2 eps3 is emitted.
+template <int L, int D>
+__device__ __noinline__ void sound_exhaustive(bool fail, uint64_t B, uint64_t A, uint32_t n, uint64_t table_off,
+                                              uint32_t i, uint32_t sub, uint64_t arg_base, uint32_t job,
+                                              const DevJob& jb, const LaunchArgs& a) {
+    const int lane = threadIdx.x & 31;
+    bool go = false;
+    if (fail) {
+        uint32_t xm;
+        go = exact_min(B, A, n, &xm) < jb.Tm;
+    }
+    unsigned todo = __ballot_sync(FULLMASK, go);
+    while (todo) {
+        const int src = __ffs(todo) - 1;
+        todo &= todo - 1u;
+        const uint64_t toff = __shfl_sync(FULLMASK, table_off, src);
+        const uint32_t is = __shfl_sync(FULLMASK, i, src);
+        const uint32_t ns = __shfl_sync(FULLMASK, n, src);
+        const uint32_t ss = __shfl_sync(FULLMASK, sub, src);
+        const uint64_t ab = __shfl_sync(FULLMASK, arg_base, src);
+        const uint32_t js = __shfl_sync(FULLMASK, job, src);
+        const uint64_t* cw = a.tables + toff + (2 * D + 1) * L;
+        Word<L> c[D + 1], v[D + 1];
+#pragma unroll
+        for (int k = 0; k <= D; k++)
+#pragma unroll
+            for (int l = 0; l < L; l++) c[k].l[l] = __ldg(cw + k * L + l);
+        const uint64_t y0 = ((uint64_t)is << jb.log2_N) + (uint64_t)lane;
+#pragma unroll
+        for (int j = 0; j <= D; j++) {
+            const uint64_t y = y0 + 32ull * (uint64_t)j;
+            Word<L> acc = c[D];
+#pragma unroll
+            for (int k = D - 1; k >= 0; k--) {
+                acc = w_mul_u64<L>(acc, y);
+                w_add<L>(acc, c[k]);
+            }
+            v[j] = acc;
+        }
+#pragma unroll
+        for (int lev = 1; lev <= D; lev++)
+#pragma unroll
+            for (int j = D; j >= lev; j--) w_sub<L>(v[j], v[j - 1]);
+        const uint32_t trips = (ns + 31u) >> 5;
+#pragma unroll 1
+        for (uint32_t t = 0; t < trips; t++) {
+            const uint32_t x = t * 32u + (uint32_t)lane;
+            const uint64_t val = v[0].l[L - 1] + jb.shift3;
+            emit_warp(x < ns && val < jb.T3, js, ss, ab + x, val, a.cand, a.cap, a.count);
+#pragma unroll
+            for (int l = 0; l < D; l++) w_add<L>(v[l], v[l + 1]);
+        }
+    }
 }
 
 // Lines per packet held in shared memory between the two phases of a task.
@@ -645,7 +722,10 @@ struct LineStage {
 // the search loop.  Only the search state is live in phase 2 (the W-bit
 // packet state is dead by then); block fields are reloaded only on the rare
 // resolve path.
-template <int L, int D>
+// G = false: jobs with the regular filter and the literal threshold only
+// (the hot path, no other code in the kernel); G = true: jobs that may use
+// Lefevre's filter or the sound mode.
+template <int L, int D, bool G>
 __device__ __forceinline__ void fused_task(const DevTask& t, const LaunchArgs& a, LineStage& st,
                                            uint32_t& st_lines, uint32_t& st_fail, uint32_t& st_half) {
     const int lane = threadIdx.x & 31;
@@ -660,7 +740,7 @@ __device__ __forceinline__ void fused_task(const DevTask& t, const LaunchArgs& a
 #pragma unroll 1
         for (uint32_t it = 0; it < nu; it++) {
             uint64_t B, A;
-            packet_words<L, D>(P, job.m, B, A);
+            packet_words<L, D>(P, job.shift, B, A);
             const uint32_t i = P.i0 + it;
             const bool valid = P.active && i < P.i1;
             const int s = stage_slot(lane * (int)nu + (int)it);
@@ -672,7 +752,7 @@ __device__ __forceinline__ void fused_task(const DevTask& t, const LaunchArgs& a
     }
     __syncwarp();
     const uint64_t Tm = a.jobs[t.job].Tm;
-    const bool lefevre = (a.jobs[t.job].flags & TMD_LEFEVRE) != 0;
+    const bool lefevre = G && (a.jobs[t.job].flags & TMD_LEFEVRE) != 0;
 #pragma unroll 1
     for (uint32_t r = 0; r < nu; r++) {
         const int s = (int)r * 32 + lane;
@@ -692,9 +772,13 @@ __device__ __forceinline__ void fused_task(const DevTask& t, const LaunchArgs& a
             const uint32_t i = st.i0[pk] + (uint32_t)s % nu;
             const DevBlock& bk = a.blocks[st.blk[pk]];
             const DevJob& jb = a.jobs[t.job];
-            resolve_and_emit(fail, B, A, n ? n : 1u, Tm, (jb.flags & TMD_ALL_HITS) != 0, t.job,
-                             (uint32_t)(bk.first_sub + i), bk.start + ((uint64_t)i << jb.log2_N),
-                             a.cand, a.cap, a.count);
+            if (G && (jb.flags & TMD_SOUND))
+                sound_exhaustive<L, D>(fail, B, A, n ? n : 1u, bk.table_off, i, (uint32_t)(bk.first_sub + i),
+                                       bk.start + ((uint64_t)i << jb.log2_N), t.job, jb, a);
+            else
+                resolve_and_emit(fail, B, A, n ? n : 1u, Tm, (jb.flags & TMD_ALL_HITS) != 0, t.job,
+                                 (uint32_t)(bk.first_sub + i), bk.start + ((uint64_t)i << jb.log2_N),
+                                 a.cand, a.cap, a.count);
         }
     }
     __syncwarp();
@@ -710,7 +794,7 @@ __device__ __forceinline__ void generate_task(const DevTask& t, const LaunchArgs
         const uint32_t i = P.i0 + it;
         if (P.active && i < P.i1) {
             uint64_t B, A;
-            packet_words<L, D>(P, job.m, B, A);
+            packet_words<L, D>(P, job.shift, B, A);
             const uint64_t line = job.line_off + P.blk.first_sub + i;
             a.lin_B[line] = B;
             a.lin_A[line] = A;
@@ -724,14 +808,18 @@ __device__ __forceinline__ void generate_task(const DevTask& t, const LaunchArgs
 // wave than 8-warp CTAs).
 constexpr int FUSED_WARPS_PER_CTA = 4;
 
-template <int L, int D>
-__global__ void __launch_bounds__(128) k_fused(LaunchArgs a) {
+// Register caps (3 CTAs of 256 threads per SM, 6 of 128): the search needs
+// ~75 registers; the rarely called non-inlined resolve and exhaustive paths
+// would otherwise set the kernels' register counts and cut their occupancy,
+// so they spill instead.
+template <int L, int D, bool G>
+__global__ void __launch_bounds__(128, 6) k_fused(LaunchArgs a) {
     __shared__ LineStage stage[FUSED_WARPS_PER_CTA];
     const uint64_t w = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     if (w >= a.n_tasks) return;  // whole warp
     uint32_t sl = 0, sf = 0, sh = 0;
     const DevTask t = a.tasks[w];
-    fused_task<L, D>(t, a, stage[threadIdx.x >> 5], sl, sf, sh);
+    fused_task<L, D, G>(t, a, stage[threadIdx.x >> 5], sl, sf, sh);
     flush_stats(a.stats, sl, sf, sh);
 }
 
@@ -747,8 +835,8 @@ __global__ void __launch_bounds__(256) k_generate(LaunchArgs a) {
 // warp takes the next task of its class from a device counter until the
 // class's list is exhausted (no waiting on other warps: one atomicAdd per
 // task).
-template <int L, int D>
-__global__ void __launch_bounds__(256) k_persistent(LaunchArgs a) {
+template <int L, int D, bool G>
+__global__ void __launch_bounds__(256, 3) k_persistent(LaunchArgs a) {
     __shared__ LineStage stage[WARPS_PER_CTA];
     LineStage& stg = stage[threadIdx.x >> 5];
     const int lane = threadIdx.x & 31;
@@ -759,7 +847,7 @@ __global__ void __launch_bounds__(256) k_persistent(LaunchArgs a) {
         t = __shfl_sync(FULLMASK, t, 0);
         if ((uint64_t)t >= a.n_tasks) break;
         const DevTask task = a.tasks[t];
-        fused_task<L, D>(task, a, stg, sl, sf, sh);
+        fused_task<L, D, G>(task, a, stg, sl, sf, sh);
     }
     flush_stats(a.stats, sl, sf, sh);
 }
@@ -915,6 +1003,8 @@ __global__ void __launch_bounds__(64) k_block_tables(const DevJob* jobs, const D
     uint64_t c[(COEFF_MAX_DEG + 1) * COEFF_MAX_LIMBS];
     const bool ok = block_coeffs<8>(J, M, 64, c_coeff, c);
     if (ok) block_table_words(J, c, tables + bk.table_off);
+    if (ok && (jb.flags & TMD_SOUND))
+        for (int w = 0; w < (J.d + 1) * J.L; w++) tables[bk.table_off + (2 * J.d + 1) * J.L + w] = c[w];
     status[b] = ok ? 0 : 1;
 }
 
@@ -930,6 +1020,8 @@ __global__ void __launch_bounds__(64) k_block_tables_wide(const DevJob* jobs, co
     uint64_t c[(COEFF_MAX_DEG + 1) * COEFF_MAX_LIMBS];
     if (block_coeffs<12>(J, M, 320, c_coeff, c)) {
         block_table_words(J, c, tables + bk.table_off);
+        if (jb.flags & TMD_SOUND)
+            for (int w = 0; w < (J.d + 1) * J.L; w++) tables[bk.table_off + (2 * J.d + 1) * J.L + w] = c[w];
         status[b] = 0;
     } else {
         atomicOr(err, (uint32_t)ERR_ROUNDING);
@@ -953,12 +1045,15 @@ cudaError_t launch_block_tables(const DevJob* jobs, const DevBlock* blocks, uint
 // --------------------------------------------------------------- launchers
 typedef void (*TaskKernel)(LaunchArgs);
 
-static TaskKernel fused_kernel(uint32_t L, uint32_t D) {
-    static const TaskKernel tab[3][4] = {
-        {k_fused<1, 1>, k_fused<1, 2>, k_fused<1, 3>, k_fused<1, 4>},
-        {k_fused<2, 1>, k_fused<2, 2>, k_fused<2, 3>, k_fused<2, 4>},
-        {k_fused<3, 1>, k_fused<3, 2>, k_fused<3, 3>, k_fused<3, 4>}};
-    return tab[L - 1][D - 1];
+static TaskKernel fused_kernel(uint32_t L, uint32_t D, bool G) {
+    static const TaskKernel tab[2][3][4] = {
+        {{k_fused<1, 1, false>, k_fused<1, 2, false>, k_fused<1, 3, false>, k_fused<1, 4, false>},
+         {k_fused<2, 1, false>, k_fused<2, 2, false>, k_fused<2, 3, false>, k_fused<2, 4, false>},
+         {k_fused<3, 1, false>, k_fused<3, 2, false>, k_fused<3, 3, false>, k_fused<3, 4, false>}},
+        {{k_fused<1, 1, true>, k_fused<1, 2, true>, k_fused<1, 3, true>, k_fused<1, 4, true>},
+         {k_fused<2, 1, true>, k_fused<2, 2, true>, k_fused<2, 3, true>, k_fused<2, 4, true>},
+         {k_fused<3, 1, true>, k_fused<3, 2, true>, k_fused<3, 3, true>, k_fused<3, 4, true>}}};
+    return tab[G ? 1 : 0][L - 1][D - 1];
 }
 
 static TaskKernel generate_kernel(uint32_t L, uint32_t D) {
@@ -969,30 +1064,33 @@ static TaskKernel generate_kernel(uint32_t L, uint32_t D) {
     return tab[L - 1][D - 1];
 }
 
-cudaError_t launch_tasks(bool fused, uint32_t L, uint32_t D, const LaunchArgs& a, cudaStream_t s) {
+cudaError_t launch_tasks(bool fused, uint32_t L, uint32_t D, bool G, const LaunchArgs& a, cudaStream_t s) {
     if (a.n_tasks == 0) return cudaSuccess;
     const uint64_t warps_per_cta = fused ? FUSED_WARPS_PER_CTA : 8;
     const uint64_t ctas = (a.n_tasks + warps_per_cta - 1) / warps_per_cta;
-    TaskKernel k = fused ? fused_kernel(L, D) : generate_kernel(L, D);
+    TaskKernel k = fused ? fused_kernel(L, D, G) : generate_kernel(L, D);
     k<<<(unsigned)ctas, (unsigned)(32 * warps_per_cta), 0, s>>>(a);
     return cudaGetLastError();
 }
 
-static TaskKernel persistent_kernel(uint32_t L, uint32_t D) {
-    static const TaskKernel tab[3][4] = {
-        {k_persistent<1, 1>, k_persistent<1, 2>, k_persistent<1, 3>, k_persistent<1, 4>},
-        {k_persistent<2, 1>, k_persistent<2, 2>, k_persistent<2, 3>, k_persistent<2, 4>},
-        {k_persistent<3, 1>, k_persistent<3, 2>, k_persistent<3, 3>, k_persistent<3, 4>}};
-    return tab[L - 1][D - 1];
+static TaskKernel persistent_kernel(uint32_t L, uint32_t D, bool G) {
+    static const TaskKernel tab[2][3][4] = {
+        {{k_persistent<1, 1, false>, k_persistent<1, 2, false>, k_persistent<1, 3, false>, k_persistent<1, 4, false>},
+         {k_persistent<2, 1, false>, k_persistent<2, 2, false>, k_persistent<2, 3, false>, k_persistent<2, 4, false>},
+         {k_persistent<3, 1, false>, k_persistent<3, 2, false>, k_persistent<3, 3, false>, k_persistent<3, 4, false>}},
+        {{k_persistent<1, 1, true>, k_persistent<1, 2, true>, k_persistent<1, 3, true>, k_persistent<1, 4, true>},
+         {k_persistent<2, 1, true>, k_persistent<2, 2, true>, k_persistent<2, 3, true>, k_persistent<2, 4, true>},
+         {k_persistent<3, 1, true>, k_persistent<3, 2, true>, k_persistent<3, 3, true>, k_persistent<3, 4, true>}}};
+    return tab[G ? 1 : 0][L - 1][D - 1];
 }
 
-cudaError_t launch_persistent(uint32_t L, uint32_t D, const LaunchArgs& a, int ctas, cudaStream_t s) {
-    persistent_kernel(L, D)<<<ctas, 256, 0, s>>>(a);
+cudaError_t launch_persistent(uint32_t L, uint32_t D, bool G, const LaunchArgs& a, int ctas, cudaStream_t s) {
+    persistent_kernel(L, D, G)<<<ctas, 256, 0, s>>>(a);
     return cudaGetLastError();
 }
 
-cudaError_t persistent_occupancy(uint32_t L, uint32_t D, int* blocks_per_sm) {
-    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, persistent_kernel(L, D), 256, 0);
+cudaError_t persistent_occupancy(uint32_t L, uint32_t D, bool G, int* blocks_per_sm) {
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, persistent_kernel(L, D, G), 256, 0);
 }
 
 cudaError_t launch_search_lines(bool raw, const LineArgs& a, cudaStream_t s) {

@@ -96,7 +96,7 @@ def test_toy_every_block_table():
     ("limbs", 4, tmd._lib.TMD_EUNSUPPORTED), ("count", 0, tmd._lib.TMD_EINVAL),
     ("start", 1 << 52, tmd._lib.TMD_EINVAL), ("e_in", 3, tmd._lib.TMD_EUNSUPPORTED),
     ("log2_T", 13, tmd._lib.TMD_EINVAL), ("func", 7, tmd._lib.TMD_EINVAL),
-    ("flags", 8, tmd._lib.TMD_EINVAL)])
+    ("flags", 16, tmd._lib.TMD_EINVAL), ("flags", 8, tmd._lib.TMD_EINVAL), ("eps1", 5, tmd._lib.TMD_EINVAL)])
 def test_validation(field, value, status):
     job = wl.plain_job().replace(**{field: value})
     if field == "log2_T":
@@ -110,3 +110,35 @@ def test_log_binade_near_one_rejected():
     job = wl.Job(wl.FUNC_LOG, 1, 53, 40, 14, 3, 24, 3, 0, 1 << 30)
     with pytest.raises(tmd.TmdError):
         tmd.tmd_plan(job)
+
+
+SOUND_JOBS = [
+    wl.Job(wl.FUNC_EXP, 1, 53, 32, 15, 3, 24, 3, 0, 1 << 39, wl.FLAG_BP_DIRECTED),
+    wl.plain_job(),
+    wl.Job(wl.FUNC_EXP, 0, 24, 10, 8, 2, 12, 1, 3 << 20, 1 << 13),
+    wl.Job(wl.FUNC_EXP2, 1, 22, 7, 7, 3, 11, 1, 12345, 1 << 11, wl.FLAG_BP_DIRECTED),
+    wl.Job(wl.FUNC_LOG, 2, 20, 8, 6, 2, 10, 1, 100, 1 << 12),
+    wl.Job(wl.FUNC_LOG, 3, 53, 40, 16, 2, 18, 3, 1 << 44, 1 << 30),
+    wl.Job(wl.FUNC_EXP, 0, 20, 7, 6, 2, 10, 2, 0, 1 << 19),
+]
+
+
+@pytest.mark.parametrize("job", SOUND_JOBS, ids=lambda j: f"f{j.func}p{j.p}N{j.log2_N}")
+def test_sound_eps_not_below_the_oracle_bounds(job):
+    """tmd_sound_eps (double precision with margins) never returns less than
+    the oracle's exact-rational smallest sound thresholds, and not much more."""
+    from oracle import sound
+    e1, e3 = tmd.tmd_sound_eps(job)
+    o1, o3 = sound.min_eps(job)
+    assert e1 >= o1 and e3 >= o3
+    assert e1 <= o1 * 1.01 + 64 and e3 <= o3 * 1.01 + 64
+
+
+def test_sound_job_validation():
+    job = tmd.sound_job(wl.toy_job())
+    tmd.tmd_plan(job)                                   # accepted
+    for bad in (job.replace(eps3=1), job.replace(eps1=job.eps3), job.replace(eps1=1 << 62),
+                job.replace(flags=job.flags | wl.FLAG_ALL_HITS), wl.toy_job().replace(eps3=5)):
+        with pytest.raises(tmd.TmdError) as e:
+            tmd.tmd_plan(bad)
+        assert e.value.status == tmd._lib.TMD_EINVAL

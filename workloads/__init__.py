@@ -20,7 +20,9 @@ Field meanings:
   count   number of consecutive arguments
   flags   FLAG_BP_DIRECTED selects scale 2^p instead of 2^(p+1);
           FLAG_ALL_HITS reports every argument below the threshold;
-          FLAG_LEFEVRE filters with Lefevre's bound (Algorithm 3)
+          FLAG_LEFEVRE filters with Lefevre's bound (Algorithm 3);
+          FLAG_SOUND reports every argument whose polynomial value is
+          within eps3 of a breakpoint (eps1: the filter's half-width)
 """
 from __future__ import annotations
 
@@ -35,6 +37,7 @@ FUNC_NAMES = {FUNC_EXP: "exp", FUNC_EXP2: "exp2", FUNC_LOG: "log"}
 FLAG_BP_DIRECTED = 1
 FLAG_ALL_HITS = 2
 FLAG_LEFEVRE = 4
+FLAG_SOUND = 8
 
 
 @dataclasses.dataclass(frozen=True)
@@ -50,6 +53,8 @@ class Job:
     start: int
     count: int
     flags: int = 0
+    eps1: int = 0       # sound mode only: filter half-width on the 64-bit words
+    eps3: int = 0       # sound mode only: exhaustive-phase half-width
 
     def replace(self, **kw) -> "Job":
         return dataclasses.replace(self, **kw)

@@ -574,16 +574,18 @@ __device__ __forceinline__ uint32_t packet_init(Packet<L, D>& P, const DevTask& 
     const int lane = threadIdx.x & 31;
     P.active = (uint32_t)lane < t.count;
     const uint64_t g = t.g0 + (P.active ? (uint64_t)lane : 0ull);
-    // the task's packets lie in its first block and at most count - 1 more
-    uint32_t lo = t.block0;
-    uint32_t hi = min(t.block0 + t.count - 1, job.block_off + job.n_blocks - 1);
-    while (lo < hi) {
-        uint32_t mid = (lo + hi + 1) >> 1;
-        if (a.blocks[mid].packet_off <= g)
-            lo = mid;
-        else
-            hi = mid - 1;
-    }
+    // the packet's block from the job's segment table: within a segment
+    // every block but the last holds ppb packets (the block records' own
+    // formula, planrec.cuh), so no search over the block records is needed
+    // (segment fields read from the job record in global memory: indexing a
+    // register copy by the segment number would move it to local memory)
+    const DevJob& jg = a.jobs[t.job];
+    const uint64_t rp = g - job.packet_off;
+    uint32_t sg = 0;
+    for (uint32_t k = 1; k < job.n_seg; k++)
+        if (jg.seg_packet0[k] <= rp) sg = k;
+    const uint32_t bis = (uint32_t)(rp - jg.seg_packet0[sg]) / job.ppb;
+    const uint32_t lo = job.block_off + (uint32_t)jg.seg_block0[sg] + bis;
     P.blk = a.blocks[lo];
     const uint64_t pk = g - P.blk.packet_off;
     P.i0 = (uint32_t)(pk * job.nu);

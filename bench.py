@@ -452,7 +452,8 @@ def main():
                      "ms_per_step": s_ms, "listed_arguments": s_count,
                      "eps1_log2": math.log2(sjob.eps1) - 64, "eps3_log2": math.log2(sjob.eps3) - 64,
                      "filter_fail_per_line": sst["filter_fail"] / max(1, sst["lines"]),
-                     "form": "batched, sound filter then exhaustive evaluation of the flagged lines"}
+                     "form": "batched: filter at eps1, exact line minimum, 32 refined pieces per failing "
+                             "line at eps2 (phase 2), exhaustive evaluation of failing pieces (phase 3)"}
         sb.close()
 
     mixed = None

@@ -64,9 +64,11 @@ typedef enum { TMD_EXP = 0, TMD_EXP2 = 1, TMD_LOG = 2 } tmd_func;
                                eps_trunc, then Sect. III-A's exhaustive phase): the
                                filter tests each line against the job's eps1 instead
                                of 2^-m; a line whose exact minimum is below 2 eps1 has
+                               its 32 pieces tested with their own lines against
+                               eps2 (tmd_sound_piece_eps), and each failing piece has
                                its block polynomial R_t evaluated at every argument
                                (tabulated differences of step 32 from the stored Taylor
-                               coefficients), and every argument with
+                               coefficients); every argument with
                                (top64(R_t(y)) + eps3) mod 2^64 < 2 eps3 is reported
                                (record value = that quantity).  With eps1, eps3 from
                                tmd_sound_eps (or any larger values) every argument
@@ -142,6 +144,16 @@ typedef struct {
  * units, so that the values are never below the exact bounds.  Fills
  * *eps1, *eps3; TMD_EINVAL if the job is invalid or the bounds exceed 2^61. */
 tmd_status tmd_sound_eps(const tmd_job* job, uint64_t* eps1, uint64_t* eps3);
+
+/* The phase-2 half-width of a sound job (host only): a failing sub-interval
+ * is cut into 32 pieces of ceil(N/32) arguments, each with its own line from
+ * the block polynomial (Sect. III-A phase 2); a piece goes to the
+ * exhaustive phase only if its exact minimum is below 2 eps2, with
+ * eps2 = job->eps3 + eps_trunc(ceil(N/32)) + ceil(N/32) + margin (the bound
+ * of tmd_sound_eps for the shorter lines).  The library computes it itself
+ * when it plans a sound job; this call reports it.  TMD_EINVAL for an invalid
+ * job or eps3 >= 2^62. */
+tmd_status tmd_sound_piece_eps(const tmd_job* job, uint64_t* eps2);
 
 /* Per-block description returned by tmd_block_tables. */
 typedef struct {

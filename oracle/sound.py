@@ -27,6 +27,9 @@ The thresholds of a sound job, in units of 2^-64:
           such an argument has a 64-bit line within [-eps1, eps1): the two
           64-bit words lose at most one unit each, the slope's unit over
           up to N - 1 steps)
+  eps2 >= eps3 + ceil(eps_trunc(N/32) 2^64) + N/32 + 2  (the same for the 32
+          pieces of a failing sub-interval, each with its own line: the
+          paper's phase 2)
 
 sound_candidates() is the definition of what the sound path reports: every
 argument whose polynomial value R_t(y), evaluated by direct Horner, has
@@ -82,10 +85,11 @@ def eps_approx(job) -> Fraction:
     return rem + rnd
 
 
-def eps_trunc(job) -> Fraction:
-    """Bound of |R_t(iN + x) - (b_i + alpha_i x)| / 2^W over x < N."""
+def eps_trunc(job, length: int = 0) -> Fraction:
+    """Bound of |R_t(y0 + x) - (R_t(y0) + (R_t(y0 + 1) - R_t(y0)) x)| / 2^W
+    over x < length (default N: the sub-interval lines of the filter)."""
     d, W = job.d, 64 * job.limbs
-    N = 1 << job.log2_N
+    N = length or (1 << job.log2_N)
     T = Fraction((1 << job.log2_T) + d)
     u = fmath._pow2(job.e_in - job.p)
     s = _scale_max(job)
@@ -105,6 +109,20 @@ def min_eps(job) -> Tuple[int, int]:
     eps3 = (1 << (64 - job.m)) + _ceil(eps_approx(job) * M64) + 1
     eps1 = eps3 + _ceil(eps_trunc(job) * M64) + (1 << job.log2_N) + 2
     return eps1, eps3
+
+
+def piece_length(job) -> int:
+    """Arguments of a phase-2 piece: a sub-interval is cut into 32 pieces."""
+    N = 1 << job.log2_N
+    return (N + 31) // 32
+
+
+def min_eps2(job, eps3: int) -> int:
+    """The smallest sound phase-2 half-width for pieces of piece_length()
+    arguments (a piece holding an argument within eps3 has its 64-bit line
+    within eps2)."""
+    n2 = piece_length(job)
+    return eps3 + _ceil(eps_trunc(job, n2) * M64) + n2 + 2
 
 
 def sound_candidates(jobs, eps3s) -> List[Tuple[int, int, int, int]]:

@@ -160,6 +160,14 @@ def tmd_sound_eps(job) -> tuple:
     return e1.value, e3.value
 
 
+def tmd_sound_piece_eps(job) -> int:
+    """The phase-2 half-width the library uses for a sound job (host)."""
+    j = make_job(job)
+    e2 = ctypes.c_uint64(0)
+    check(lib().tmd_sound_piece_eps(ctypes.byref(j), ctypes.byref(e2)), "tmd_sound_piece_eps")
+    return e2.value
+
+
 def sound_job(job):
     """The job in sound mode with the library's sound thresholds."""
     e1, e3 = tmd_sound_eps(job)

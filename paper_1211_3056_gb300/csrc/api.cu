@@ -198,6 +198,14 @@ tmd_status build_plan(const tmd_job* jobs, uint32_t njobs, Plan& P, bool host_ta
         dj.Tm = 2 * dj.shift;
         dj.shift3 = sound ? jb.eps3 : 0;
         dj.T3 = 2 * dj.shift3;
+        dj.shift2 = 0;
+        if (sound) {
+            uint64_t e2 = 0;
+            const tmd_status s2 = sound_piece_eps(jb, jb.eps3, &e2);
+            if (s2 != TMD_OK) return s2;
+            dj.shift2 = e2;
+        }
+        dj.T2 = 2 * dj.shift2;
         dj.log2_N = jb.log2_N;
         dj.log2_T = jb.log2_T;
         dj.d = (uint32_t)jb.d;
@@ -517,6 +525,11 @@ tmd_status tmd_plan(const tmd_job* job, tmd_plan_info* info) {
 tmd_status tmd_sound_eps(const tmd_job* job, uint64_t* eps1, uint64_t* eps3) {
     if (!job || !eps1 || !eps3) return TMD_EINVAL;
     return sound_eps(*job, eps1, eps3);
+}
+
+tmd_status tmd_sound_piece_eps(const tmd_job* job, uint64_t* eps2) {
+    if (!job || !eps2) return TMD_EINVAL;
+    return sound_piece_eps(*job, job->eps3, eps2);
 }
 
 tmd_status tmd_block_tables(const tmd_job* job, uint64_t block, uint64_t* coeffs, uint64_t* table,

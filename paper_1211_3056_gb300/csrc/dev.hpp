@@ -41,6 +41,8 @@ struct DevJob {
     uint64_t shift;        // added to the top word of b: 2^(64-m), or eps1 in sound mode (Tm = 2 shift)
     uint64_t shift3;       // sound mode: the exhaustive phase's half-width eps3 (T3 = 2 eps3)
     uint64_t T3;
+    uint64_t shift2;       // sound mode: the phase-2 pieces' half-width eps2 (T2 = 2 eps2)
+    uint64_t T2;
 };
 
 // One Taylor block.

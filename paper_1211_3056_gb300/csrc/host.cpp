@@ -615,7 +615,10 @@ static double deriv_max(int func, int k, double x_lo, double x_hi) {
     return v * (1.0 + 1e-9);
 }
 
-tmd_status sound_eps(const tmd_job& job, uint64_t* eps1, uint64_t* eps3) {
+// eps_approx * 2^64 and eps_trunc * 2^64 for lines over `length` arguments
+// (double precision, before the margins).
+static tmd_status sound_bounds(const tmd_job& job, double length, double* ea_out, double* et_out, int* m_out,
+                               uint32_t* log2_N) {
     tmd_job j = job;
     j.flags &= ~(uint32_t)TMD_SOUND;
     j.eps1 = j.eps3 = 0;
@@ -631,7 +634,7 @@ tmd_status sound_eps(const tmd_job& job, uint64_t* eps1, uint64_t* eps3) {
     const double x_lo = std::ldexp((double)arg_mantissa(j, j.start), j.e_in - j.p);
     const double x_hi = std::ldexp((double)arg_mantissa(j, j.start + j.count - 1), j.e_in - j.p);
     const int s_log2 = scale_log2(j, e_min);
-    const double T = std::ldexp(1.0, (int)j.log2_T), N = std::ldexp(1.0, (int)j.log2_N);
+    const double T = std::ldexp(1.0, (int)j.log2_T), N = length > 0 ? length : std::ldexp(1.0, (int)j.log2_N);
     double fact[8] = {1, 1, 2, 6, 24, 120, 720, 5040};
     // eps_approx * 2^64: Taylor remainder plus coefficient rounding
     double ea = std::ldexp(std::pow(u * T, d + 1) * deriv_max(j.func, d + 1, x_lo, x_hi) / fact[d + 1],
@@ -651,14 +654,41 @@ tmd_status sound_eps(const tmd_job& job, uint64_t* eps1, uint64_t* eps3) {
     }
     et = std::ldexp(et, 64 - W);
     const double margin = 1.0 + 1.0 / 1024;
-    ea = ea * margin + 4;
-    et = et * margin + 4;
+    *ea_out = ea * margin + 4;
+    *et_out = et * margin + 4;
+    *m_out = j.m;
+    *log2_N = j.log2_N;
+    return TMD_OK;
+}
+
+tmd_status sound_eps(const tmd_job& job, uint64_t* eps1, uint64_t* eps3) {
+    double ea, et;
+    int m;
+    uint32_t lN;
+    tmd_status st = sound_bounds(job, 0, &ea, &et, &m, &lN);
+    if (st != TMD_OK) return st;
     if (!(ea < 0x1p61) || !(et < 0x1p61)) return TMD_EINVAL;
-    const uint64_t e3 = (1ull << (64 - j.m)) + (uint64_t)std::ceil(ea) + 1;
-    const uint64_t e1 = e3 + (uint64_t)std::ceil(et) + (1ull << j.log2_N) + 2;
+    const uint64_t e3 = (1ull << (64 - m)) + (uint64_t)std::ceil(ea) + 1;
+    const uint64_t e1 = e3 + (uint64_t)std::ceil(et) + (1ull << lN) + 2;
     if (e1 >= (1ull << 62)) return TMD_EINVAL;
     *eps1 = e1;
     *eps3 = e3;
+    return TMD_OK;
+}
+
+uint32_t sound_piece_length(uint32_t log2_N) { return ((1u << log2_N) + 31u) / 32u; }
+
+tmd_status sound_piece_eps(const tmd_job& job, uint64_t eps3, uint64_t* eps2) {
+    double ea, et;
+    int m;
+    uint32_t lN;
+    const uint32_t n2 = sound_piece_length(job.log2_N);
+    tmd_status st = sound_bounds(job, (double)n2, &ea, &et, &m, &lN);
+    if (st != TMD_OK) return st;
+    if (!(et < 0x1p61) || eps3 >= (1ull << 62)) return TMD_EINVAL;
+    const uint64_t e2 = eps3 + (uint64_t)std::ceil(et) + n2 + 2;
+    if (e2 >= (1ull << 62)) return TMD_EINVAL;
+    *eps2 = e2;
     return TMD_OK;
 }
 

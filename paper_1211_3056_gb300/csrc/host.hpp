@@ -24,6 +24,10 @@ struct BlockPlan {
 tmd_status validate_job(const tmd_job& job);
 // The sound thresholds (eps1, eps3) of a job, on the 64-bit words.
 tmd_status sound_eps(const tmd_job& job, uint64_t* eps1, uint64_t* eps3);
+// Arguments of a phase-2 piece (a sub-interval is cut into 32) and the
+// phase-2 half-width for a sound job's eps3.
+uint32_t sound_piece_length(uint32_t log2_N);
+tmd_status sound_piece_eps(const tmd_job& job, uint64_t eps3, uint64_t* eps2);
 
 // e(f(X_j)) (Def. 1) for argument index j.
 int output_exponent(const tmd_job& job, uint64_t j);

@@ -635,13 +635,28 @@ __device__ __forceinline__ void packet_words(const Packet<L, D>& P, uint64_t shi
     A = ~P.d1[0].l[L - 1] + (low == 0 ? 1ull : 0ull);
 }
 
-// Sound mode, the exhaustive phase (Sect. III-A phase 3): each line of the
-// warp that failed the filter and whose exact minimum is below 2 eps1 has
-// its block polynomial R_t evaluated at every argument y = iN + x, x < n,
-// by the whole warp: lane l starts at y0 = iN + l with the step-32 forward
-// differences of R_t (from the block's Taylor coefficients by Horner at
-// y0, y0 + 32, ..., y0 + 32 D) and steps them; every argument with
-// (top64(R_t(y)) + eps3) mod 2^64 < 2 eps3 is emitted.
+// R_t(y) mod 2^W by Horner from the block's Taylor coefficients.
+template <int L, int D>
+__device__ __forceinline__ Word<L> poly_at(const Word<L>* c, uint64_t y) {
+    Word<L> acc = c[D];
+#pragma unroll
+    for (int k = D - 1; k >= 0; k--) {
+        acc = w_mul_u64<L>(acc, y);
+        w_add<L>(acc, c[k]);
+    }
+    return acc;
+}
+
+// Sound mode after the filter (Sect. III-A phases 2 and 3).  A line of the
+// warp that failed Algorithm 4 and whose exact minimum is below 2 eps1 is
+// cut into 32 pieces of ceil(N/32) arguments, one per lane; each lane forms
+// its piece's own line from the block polynomial (R_t at the piece start
+// and the next argument, the search words shifted by eps2) and keeps the
+// piece if its exact minimum is below 2 eps2 (phase 2).  Every kept piece
+// has R_t evaluated at each of its arguments by the whole warp: lane l
+// starts at the piece start + l with the step-32 forward differences of R_t
+// (Horner at y0, y0 + 32, ..., y0 + 32 D) and steps them; every argument
+// with (top64(R_t(y)) + eps3) mod 2^64 < 2 eps3 is emitted (phase 3).
 template <int L, int D>
 __device__ __noinline__ void sound_exhaustive(bool fail, uint64_t B, uint64_t A, uint32_t n, uint64_t table_off,
                                               uint32_t i, uint32_t sub, uint64_t arg_base, uint32_t job,
@@ -652,6 +667,7 @@ __device__ __noinline__ void sound_exhaustive(bool fail, uint64_t B, uint64_t A,
         uint32_t xm;
         go = exact_min(B, A, n, &xm) < jb.Tm;
     }
+    const uint32_t n2 = ((1u << jb.log2_N) + 31u) >> 5;
     unsigned todo = __ballot_sync(FULLMASK, go);
     while (todo) {
         const int src = __ffs(todo) - 1;
@@ -663,35 +679,52 @@ __device__ __noinline__ void sound_exhaustive(bool fail, uint64_t B, uint64_t A,
         const uint64_t ab = __shfl_sync(FULLMASK, arg_base, src);
         const uint32_t js = __shfl_sync(FULLMASK, job, src);
         const uint64_t* cw = a.tables + toff + (2 * D + 1) * L;
-        Word<L> c[D + 1], v[D + 1];
+        Word<L> c[D + 1];
 #pragma unroll
         for (int k = 0; k <= D; k++)
 #pragma unroll
             for (int l = 0; l < L; l++) c[k].l[l] = __ldg(cw + k * L + l);
-        const uint64_t y0 = ((uint64_t)is << jb.log2_N) + (uint64_t)lane;
+        const uint64_t ybase = (uint64_t)is << jb.log2_N;
+        // phase 2: this lane's piece [x0, x0 + len)
+        const uint32_t x0 = (uint32_t)lane * n2;
+        const uint32_t len = x0 < ns ? min(n2, ns - x0) : 0u;
+        bool keep = false;
+        if (len) {
+            const Word<L> r0 = poly_at<L, D>(c, ybase + x0);
+            Word<L> al = poly_at<L, D>(c, ybase + x0 + 1);
+            w_sub<L>(al, r0);
+            uint64_t low = 0;
 #pragma unroll
-        for (int j = 0; j <= D; j++) {
-            const uint64_t y = y0 + 32ull * (uint64_t)j;
-            Word<L> acc = c[D];
-#pragma unroll
-            for (int k = D - 1; k >= 0; k--) {
-                acc = w_mul_u64<L>(acc, y);
-                w_add<L>(acc, c[k]);
-            }
-            v[j] = acc;
+            for (int l = 0; l + 1 < L; l++) low |= al.l[l];
+            const uint64_t B2 = r0.l[L - 1] + jb.shift2;
+            const uint64_t A2 = ~al.l[L - 1] + (low == 0 ? 1ull : 0ull);
+            uint32_t xm;
+            keep = exact_min(B2, A2, len, &xm) < jb.T2;
         }
+        unsigned pieces = __ballot_sync(FULLMASK, keep);
+        while (pieces) {
+            const uint32_t pc = (uint32_t)(__ffs(pieces) - 1);
+            pieces &= pieces - 1u;
+            const uint32_t px0 = pc * n2;
+            const uint32_t pend = min(px0 + n2, ns);
+            // phase 3 over the piece
+            Word<L> v[D + 1];
+            const uint64_t y0 = ybase + px0 + (uint64_t)lane;
 #pragma unroll
-        for (int lev = 1; lev <= D; lev++)
+            for (int jj = 0; jj <= D; jj++) v[jj] = poly_at<L, D>(c, y0 + 32ull * (uint64_t)jj);
 #pragma unroll
-            for (int j = D; j >= lev; j--) w_sub<L>(v[j], v[j - 1]);
-        const uint32_t trips = (ns + 31u) >> 5;
+            for (int lev = 1; lev <= D; lev++)
+#pragma unroll
+                for (int jj = D; jj >= lev; jj--) w_sub<L>(v[jj], v[jj - 1]);
+            const uint32_t trips = (pend - px0 + 31u) >> 5;
 #pragma unroll 1
-        for (uint32_t t = 0; t < trips; t++) {
-            const uint32_t x = t * 32u + (uint32_t)lane;
-            const uint64_t val = v[0].l[L - 1] + jb.shift3;
-            emit_warp(x < ns && val < jb.T3, js, ss, ab + x, val, a.cand, a.cap, a.count);
+            for (uint32_t t = 0; t < trips; t++) {
+                const uint32_t x = px0 + t * 32u + (uint32_t)lane;
+                const uint64_t val = v[0].l[L - 1] + jb.shift3;
+                emit_warp(x < pend && val < jb.T3, js, ss, ab + x, val, a.cand, a.cap, a.count);
 #pragma unroll
-            for (int l = 0; l < D; l++) w_add<L>(v[l], v[l + 1]);
+                for (int l = 0; l < D; l++) w_add<L>(v[l], v[l + 1]);
+            }
         }
     }
 }

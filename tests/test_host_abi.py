@@ -134,6 +134,16 @@ def test_sound_eps_not_below_the_oracle_bounds(job):
     assert e1 <= o1 * 1.01 + 64 and e3 <= o3 * 1.01 + 64
 
 
+@pytest.mark.parametrize("job", SOUND_JOBS, ids=lambda j: f"f{j.func}p{j.p}N{j.log2_N}")
+def test_sound_piece_eps_not_below_the_oracle_bound(job):
+    from oracle import sound
+    sj = tmd.sound_job(job)
+    e2 = tmd.tmd_sound_piece_eps(sj)
+    o2 = sound.min_eps2(job, sj.eps3)
+    assert o2 <= e2 <= o2 * 1.01 + 64
+    assert sj.eps3 < e2 < sj.eps1
+
+
 def test_sound_job_validation():
     job = tmd.sound_job(wl.toy_job())
     tmd.tmd_plan(job)                                   # accepted

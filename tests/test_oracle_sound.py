@@ -100,3 +100,30 @@ def test_planted_exact_point_is_hard_to_round():
     assert sound.is_hard_to_round(job, 0)
     e1, e3 = sound.min_eps(job)
     assert sound.sound_candidates([job], [e3])[0][:3] == (0, 0, 0)
+
+
+@pytest.mark.parametrize("job", SMALL[:3] + [wl.plain_job(count_log2=30)], ids=lambda j: f"f{j.func}p{j.p}N{j.log2_N}")
+def test_piece_truncation_bound_holds(job):
+    """eps_trunc for the phase-2 pieces (N/32 arguments, a line from the two
+    values at the piece start) against the exact integer polynomial."""
+    n2 = sound.piece_length(job)
+    et = sound.eps_trunc(job, n2)
+    W = 64 * job.limbs
+    mod = 1 << W
+    rng = random.Random(31 + job.count)
+    worst = Fraction(0)
+    blocks = plan.blocks(job)
+    for blk in rng.sample(blocks, min(2, len(blocks))):
+        c = poly.taylor_coeffs(job, blk)
+        for _ in range(6):
+            y0 = rng.randrange(0, max(1, blk.length - n2))
+            r0 = poly.horner(c, y0, W)
+            a = (poly.horner(c, y0 + 1, W) - r0) % mod
+            for x in range(n2):
+                diff = (poly.horner(c, y0 + x, W) - r0 - a * x) % mod
+                if diff >= mod // 2:
+                    diff -= mod
+                worst = max(worst, Fraction(abs(diff), mod))
+    assert worst <= et
+    e1, e3 = sound.min_eps(job)
+    assert e3 < sound.min_eps2(job, e3) < e1

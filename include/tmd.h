@@ -17,8 +17,13 @@
  *             (Sect. IV-B, IV-C), giving one line b_i + alpha_i x per
  *             sub-interval;
  *   search    Sect. III-B: the regular continued-fraction lower bound
- *             (Algorithm 4) per line as a filter, exact resolution of the
- *             lines it flags, warp-ballot compaction of the candidates;
+ *             (Algorithm 4) per line as a filter -- or Lefevre's
+ *             (Algorithm 3, TMD_LEFEVRE) --, the exact minimum and smallest
+ *             argmin of the lines it flags (a Euclid-like recursion, no
+ *             visit of the N points), warp-ballot compaction of the
+ *             candidates; in sound mode (TMD_SOUND) the filter uses Sect.
+ *             II-A's eps'' and flagged lines go through Sect. III-A's
+ *             phases 2 (refined pieces) and 3 (every argument);
  *   candidates  stream-ordered read-back, sorted.
  *
  * Conventions for every entry point:
@@ -28,7 +33,7 @@
  *     context's device; the library never frees caller memory.
  *   - host pointers ("h_" prefix or plain) are caller-owned host memory.
  *   - the library synchronises the host only inside tmd_candidates,
- *     tmd_stats_read, tmd_batch_wait and the serving calls that say so.
+ *     tmd_stats_read, the batch calls and the serving calls that say so.
  *   - a context is used by one host thread at a time.
  */
 #ifndef TMD_H
@@ -235,8 +240,10 @@ tmd_status tmd_generate(tmd_ctx* ctx, const tmd_job* jobs, uint32_t njobs,
                         void* stream);
 
 /* Stage 2: search.  With d_lin != NULL, the lines written by tmd_generate
- * for the same jobs are searched (one line per lane, Algorithm 4 filter,
- * exact resolution, warp-ballot compaction).  With d_lin == NULL the fused
+ * for the same jobs are searched (one line per lane, Algorithm 4 or
+ * Algorithm 3 filter, exact minimum of the flagged lines, warp-ballot
+ * compaction; sound jobs are not accepted here: TMD_EUNSUPPORTED).  With
+ * d_lin == NULL the fused
  * kernel regenerates the lines in registers from the resident tables
  * (planning them first if these jobs are not the resident ones).
  * Records go to d_cand[0 .. cand_cap), unordered; *d_count (device uint64)

@@ -7,11 +7,15 @@
 //               steps the tabulated differences with W-bit carry-chain adds.
 //   search      Sect. III-B: Algorithm 4 (regular continued-fraction lower
 //               bound, unrolled twice) on the 64-bit search words of each
-//               line, one line per lane; lines whose bound falls below the
-//               threshold are resolved exactly by the whole warp (every
-//               argument of the line, smallest argmin kept) and emitted by
+//               line, one line per lane, the warp's 32 lines being
+//               neighbouring sub-intervals; lines whose bound falls below
+//               the threshold get their exact minimum and smallest argmin
+//               from a Euclid-like recursion (exact_min) and are emitted by
 //               warp ballot with one atomic per warp (Sect. III-C
-//               compaction of failing sub-domains).
+//               compaction of failing sub-domains).  Lefevre's filter
+//               (Algorithm 3) and the sound mode (eps'' filter, phase-2
+//               pieces, phase-3 exhaustive evaluation) live in the general
+//               kernel variant only.
 //
 // Quotients: GB300 has no integer divide instruction and a slow FP64 unit,
 // so floor(a/b) comes from an FP32 estimate built from 32-bit halves

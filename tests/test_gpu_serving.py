@@ -87,3 +87,29 @@ def test_group_overflow_reruns_jobs_alone_with_exact_counts():
     r, recs = got[1]
     assert r["status"] == tmd.TMD_EOVERFLOW and r["count"] == solo[1][1]
     assert len(recs) == 8 and set(recs) <= set(solo[1][0])
+
+
+def test_served_filter_variants_and_sound_jobs_equal_the_oracle():
+    """Jobs of the general kernel variant (Lefevre's filter, sound mode)
+    served in a mix with ordinary ones, admitted together: each result
+    equals the oracle's list for that job alone (the candidate list, or for
+    a sound job the exhaustive list at its eps3)."""
+    from oracle import candidates as oc
+    from oracle import sound
+    base = [wl.Job(wl.FUNC_EXP, 0, 24, 10, 8, 2, 12, 1, 3 << 20, 1 << 13),
+            wl.Job(wl.FUNC_LOG, 2, 20, 8, 6, 2, 10, 1, 100, 1 << 12),
+            wl.Job(wl.FUNC_EXP, 0, 53, 18, 14, 3, 24, 3, wl.plain_start(), 1 << 26)]
+    jobs = [tmd.sound_job(base[0]), base[1].replace(flags=wl.FLAG_LEFEVRE), base[2],
+            tmd.sound_job(base[1]), base[2].replace(flags=wl.FLAG_LEFEVRE)]
+    with tmd.Context(0) as ctx:
+        with tmd.Server(ctx, max_inflight=2, chunk_tasks=8, cand_cap=1 << 16, max_batch=8) as srv:
+            got = serve_all(srv, jobs, [0.0] * len(jobs))
+        assert len(got) == len(jobs)
+    for tag, job in enumerate(jobs):
+        r, recs = got[tag]
+        if job.flags & wl.FLAG_SOUND:
+            want = [(0,) + w[1:] for w in sound.sound_candidates([job], [job.eps3])]
+        else:
+            want = oc.job_candidates(job, 0)
+        assert r["status"] == 0 and r["count"] == len(want)
+        assert recs == sorted(want, key=lambda w: (w[0], w[2], w[3])), tag

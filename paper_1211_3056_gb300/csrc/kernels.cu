@@ -126,13 +126,28 @@ __device__ __forceinline__ float scaled_rcp(float bf) {
     return rcp_approx(bf) * 0.99999904632568359375f;  // 1 - 2^-20
 }
 
+// x >= b ? x - b : x on 64-bit words without a compare and select: the
+// borrow of x - b, as a 0 / all-ones mask, adds b back (the subtract-with-
+// borrow and add-with-carry chains issue at the full 32-bit add rate, the
+// compares and selects they replace on the half-rate logic pipe).
+__device__ __forceinline__ uint64_t csub(uint64_t x, uint64_t b) {
+    uint32_t t0, t1, bw;
+    asm("sub.cc.u32 %0, %3, %5;\n\tsubc.cc.u32 %1, %4, %6;\n\tsubc.u32 %2, 0, 0;"
+        : "=r"(t0), "=r"(t1), "=r"(bw)
+        : "r"((uint32_t)x), "r"((uint32_t)(x >> 32)), "r"((uint32_t)b), "r"((uint32_t)(b >> 32)));
+    asm("add.cc.u32 %0, %0, %2;\n\taddc.u32 %1, %1, %3;"
+        : "+r"(t0), "+r"(t1)
+        : "r"((uint32_t)b & bw), "r"((uint32_t)(b >> 32) & bw));
+    return ((uint64_t)t1 << 32) | t0;
+}
+
 // r = a - k b for an estimate k in {floor(a/b) - 1, floor(a/b)}, then one
-// compare-and-subtract; k is raised when the subtract happens.
+// conditional subtract; k is raised when the subtract happens.
 __device__ __forceinline__ uint64_t rem_fix(uint64_t a, uint64_t b, uint32_t& k) {
     const uint64_t r = a - (uint64_t)k * b;
-    const bool up = r >= b;
-    k += up ? 1u : 0u;
-    return up ? r - b : r;
+    const uint64_t rr = csub(r, b);
+    k += rr != r ? 1u : 0u;
+    return rr;
 }
 
 // exact floor(a/b), a mod b (b > 0) by shift-subtract; the quotient is
@@ -235,7 +250,7 @@ __device__ __forceinline__ uint64_t cf_lower_bound(uint64_t B, uint64_t A, uint3
             if (r < q) {
                 p = r;
                 v = min(v + u, n);
-                d = d >= p ? d - p : d;  // d - p < k q = q
+                d = csub(d, p);  // d - p < k q = q
             } else {
                 uint32_t k;
                 second_half_div(p, q, d, k);
@@ -251,7 +266,7 @@ __device__ __forceinline__ uint64_t cf_lower_bound(uint64_t B, uint64_t A, uint3
             if (r < p) {
                 q = r;
                 u = min(u + v, n);
-                d = d >= p ? d - p : d;  // d < q < 2p
+                d = csub(d, p);  // d < q < 2p
             } else {
                 uint32_t k;
                 half_step_div(q, p, d, q, k, d);

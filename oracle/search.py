@@ -128,7 +128,7 @@ def regular_lb_unrolled(B: int, A: int, N: int, M: int = 1 << 64) -> Tuple[int, 
             return d, u + v, hs
 
 
-def lefevre_lb(B: int, A: int, N: int, M: int = 1 << 64) -> Tuple[int, int, int]:
+def lefevre_lb(B: int, A: int, N: int, M: int = 1 << 64, specific: bool = False) -> Tuple[int, int, int]:
     """Algorithm 1 (Lefevre's lower bound computation) run to its Success
     exit, i.e. the test with eps'' = 0; returns (d, u+v, loop iterations).
     p <- a, q <- 1 - a, d <- b, u <- v <- 1 (scaled by M).  Each iteration
@@ -141,7 +141,15 @@ def lefevre_lb(B: int, A: int, N: int, M: int = 1 << 64) -> Tuple[int, int, int]
     a division leaving a zero remainder means every interval now has the
     other length, so d reduced modulo that length is the distance over the
     whole lattice of points and the loop ends there.  A = 0: every point
-    is 0, d = b."""
+    is 0, d = b.
+
+    specific=True: Lefevre's "specific instructions" (Sect. III-B mentions
+    them without printing them), read here as taking a run of consecutive
+    second-branch iterations whose quotient is 0 (d >= p and p < q: each
+    one d -= p, q -= p, u += v) in one iteration with divisions: r =
+    min(floor(d/p), ceil(q/p) - 1, the iterations left before u + v >= N).
+    The states, hence d and u + v at the exit, are those of the plain loop;
+    only the iteration count shrinks."""
     A %= M
     B %= M
     if A == 0:
@@ -160,6 +168,15 @@ def lefevre_lb(B: int, A: int, N: int, M: int = 1 << 64) -> Tuple[int, int, int]
                 return d % p, u + v, it
             p -= q
             v += u
+        elif specific and p < q:
+            r = min(d // p, (q - 1) // p)
+            jx = 1 if u + v >= N else (N - u - v + v - 1) // v + 1
+            r = min(r, jx)
+            d -= r * p
+            if u + r * v >= N:
+                return d, u + r * v, it
+            q -= r * p
+            u += r * v
         else:
             d -= p
             k = p // q

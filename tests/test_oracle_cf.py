@@ -149,6 +149,8 @@ def test_lefevre_lb_exhaustive_small_moduli(M):
             for N in range(1, M + 2):
                 l1 = search.lefevre_lb(B, A, N, M)
                 assert search.lefevre_swap_lb(B, A, N, M) == l1
+                ls = search.lefevre_lb(B, A, N, M, specific=True)
+                assert ls[:2] == l1[:2] and ls[2] <= l1[2]
                 assert run[-1] <= l1[0] <= run[N - 1]
                 for eps in (1, 3, M // 4):
                     assert search.lefevre_test(B, A, N, eps, M) == (l1[0] >= eps)
@@ -203,22 +205,28 @@ def test_table3_loop_statistics_on_exp_lines():
     blocks = plan.blocks(job)
     rng = random.Random(2012)
     W, N = 64 * job.limbs, 1 << job.log2_N
-    reg, lef, nm_r, nm_l = [], [], [], []
+    reg, lef, spec, nm_r, nm_l, nm_s = [], [], [], [], [], []
     for b in rng.sample(range(len(blocks)), 6):
         blk = blocks[b]
         c = poly.taylor_coeffs(job, blk)
         for _ in range(6):
             i0 = rng.randrange(0, (blk.length // N) // 32) * 32
-            r, l = [], []
+            r, l, sp = [], [], []
             for i in range(i0, i0 + 32):
                 B, A = poly.search_words(*poly.line(c, i, N, W), job.m, W)
                 r.append(search.regular_lb_unrolled(B, A, N)[2])
                 l.append(search.lefevre_lb(B, A, N)[2])
+                sp.append(search.lefevre_lb(B, A, N, specific=True)[2])
             reg += r
             lef += l
+            spec += sp
             nm_r.append(search.nmdm(r))
             nm_l.append(search.nmdm(l))
+            nm_s.append(search.nmdm(sp))
     assert 8 <= min(reg) and max(reg) <= 19 and 9 <= statistics.mean(reg) <= 13
     assert 5 <= min(lef) and max(lef) <= 328 and 18 <= statistics.mean(lef) <= 36
     assert 0.15 <= statistics.mean(nm_l) <= 0.40
     assert statistics.mean(nm_r) < statistics.mean(nm_l) / 3
+    # with the specific instructions: printed 5..31, mean 16, NMDM 25.7 %
+    assert 5 <= min(spec) and max(spec) <= 40 and 13 <= statistics.mean(spec) <= 20
+    assert 0.15 <= statistics.mean(nm_s) <= 0.35

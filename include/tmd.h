@@ -83,7 +83,8 @@ typedef enum { TMD_EXP = 0, TMD_EXP2 = 1, TMD_LOG = 2 } tmd_func;
                                and the allocation-free entry (not the unfused
                                tmd_generate + tmd_search pair).                      */
 #define TMD_LEFEVRE 4u      /* filter with Lefevre's lower bound (Algorithm 3, the swap
-                               form of Algorithm 1) instead of the regular one
+                               form of Algorithm 1, with his specific instructions,
+                               see tmd_lefevre_bounds) instead of the regular one
                                (Algorithm 4).  The records do not change (flagged lines
                                are resolved exactly either way); the statistics'
                                half_steps counter then counts Algorithm 3 iterations. */
@@ -286,14 +287,21 @@ tmd_status tmd_lower_bounds(tmd_ctx* ctx, const uint64_t* d_B, const uint64_t* d
  * merged by swaps, Sect. III-B), per line: d_lb[i] = d at the first
  * u + v >= d_len[i] (Algorithm 1's test fails exactly when it is below
  * eps''), d_iters[i] = main-loop iterations (may be NULL; Table 3).
+ * specific = 1 adds Lefevre's specific instructions, which the paper uses
+ * but does not print, read as: a run of consecutive iterations with
+ * quotient 0 -- moving d left one point at a time (d -= p, q -= p, u += v
+ * each) or taking a partial quotient one unit at a time (p -= q, v += u
+ * each) -- is taken in one iteration by exact divisions: same d, far fewer
+ * iterations, no pathological loop counts (Table 3's second row).  The TMD_LEFEVRE filter of the searches uses
+ * them; specific = 0 is the plain algorithm (Table 3's first row).
  * p <- a, q <- 1 - a, d <- b, u <- v <- 1 on the words scaled by 2^64; a
  * division leaving a zero remainder (rational a) ends the loop with d
  * reduced modulo the other length; A = 0 returns B with no iteration.
  * Lengths as in tmd_lower_bounds (1 .. 2^16; others are clamped and
  * reported by the next tmd_candidates/tmd_stats_read as TMD_EINVAL). */
 tmd_status tmd_lefevre_bounds(tmd_ctx* ctx, const uint64_t* d_B, const uint64_t* d_A,
-                              const uint32_t* d_len, uint64_t n, uint64_t* d_lb,
-                              uint32_t* d_iters, void* stream);
+                              const uint32_t* d_len, uint64_t n, uint32_t specific,
+                              uint64_t* d_lb, uint32_t* d_iters, void* stream);
 
 /* Counters of the most recent tmd_search / tmd_search_lines / batch run on
  * this context, the size of the last plan upload and the last count.

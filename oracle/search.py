@@ -145,11 +145,13 @@ def lefevre_lb(B: int, A: int, N: int, M: int = 1 << 64, specific: bool = False)
 
     specific=True: Lefevre's "specific instructions" (Sect. III-B mentions
     them without printing them), read here as taking a run of consecutive
-    second-branch iterations whose quotient is 0 (d >= p and p < q: each
-    one d -= p, q -= p, u += v) in one iteration with divisions: r =
-    min(floor(d/p), ceil(q/p) - 1, the iterations left before u + v >= N).
-    The states, hence d and u + v at the exit, are those of the plain loop;
-    only the iteration count shrinks."""
+    iterations whose quotient is 0 in one iteration with divisions: in the
+    second branch (d >= p, p < q: each d -= p, q -= p, u += v) r =
+    min(floor(d/p), ceil(q/p) - 1, iterations left before u + v >= N); in
+    the first (d < p, q < p: each p -= q, v += u) r = ceil((p - max(d, q))
+    / q), the run ending earlier if u + v reaches N.  The states, hence d
+    and u + v at the exit, are those of the plain loop; only the iteration
+    count shrinks."""
     A %= M
     B %= M
     if A == 0:
@@ -158,7 +160,16 @@ def lefevre_lb(B: int, A: int, N: int, M: int = 1 << 64, specific: bool = False)
     it = 0
     while True:
         it += 1
-        if d < p:
+        if specific and d < p and q < p:
+            # a run of first-branch iterations with quotient 0: each p -= q,
+            # v += u while p stays above both d and q
+            r = (p - max(d, q) + q - 1) // q
+            jx = 1 if u + v >= N else (N - v + u - 1) // u
+            if jx <= r:
+                return d, u + v + (jx - 1) * u, it
+            p -= r * q
+            v += r * u
+        elif d < p:
             k = q // p
             q -= k * p
             u += k * v

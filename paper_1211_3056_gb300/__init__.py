@@ -174,9 +174,11 @@ def sound_job(job):
     return job.replace(flags=job.flags | TMD_SOUND, eps1=e1, eps3=e3)
 
 
-def tmd_lefevre_bounds(ctx: Context, d_B, d_A, d_len, d_lb, d_iters=None, stream=None) -> None:
+def tmd_lefevre_bounds(ctx: Context, d_B, d_A, d_len, d_lb, d_iters=None, stream=None,
+                       specific: bool = True) -> None:
     check(lib().tmd_lefevre_bounds(ctx.handle, _ptr(d_B), _ptr(d_A), _ptr(d_len), d_B.numel(),
-                                   _ptr(d_lb), _ptr(d_iters), _stream_ptr(stream)), "tmd_lefevre_bounds")
+                                   1 if specific else 0, _ptr(d_lb), _ptr(d_iters), _stream_ptr(stream)),
+          "tmd_lefevre_bounds")
 
 
 def tmd_stats_read(ctx: Context, stream=None) -> dict:

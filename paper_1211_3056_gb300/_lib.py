@@ -91,7 +91,7 @@ SIGNATURES = {
     "tmd_candidates": (ctypes.c_int, [_vp, _vp, _vp, _u64, _vp, _u64, ctypes.POINTER(_u64), _vp]),
     "tmd_search_lines": (ctypes.c_int, [_vp, _vp, _vp, _vp, _u64, _i32, _u32, _vp, _u64, _vp, _vp]),
     "tmd_lower_bounds": (ctypes.c_int, [_vp, _vp, _vp, _vp, _u64, _vp, _vp, _vp]),
-    "tmd_lefevre_bounds": (ctypes.c_int, [_vp, _vp, _vp, _vp, _u64, _vp, _vp, _vp]),
+    "tmd_lefevre_bounds": (ctypes.c_int, [_vp, _vp, _vp, _vp, _u64, _u32, _vp, _vp, _vp]),
     "tmd_sound_eps": (ctypes.c_int, [ctypes.POINTER(tmd_job), ctypes.POINTER(_u64), ctypes.POINTER(_u64)]),
     "tmd_sound_piece_eps": (ctypes.c_int, [ctypes.POINTER(tmd_job), ctypes.POINTER(_u64)]),
     "tmd_stats_read": (ctypes.c_int, [_vp, ctypes.POINTER(tmd_stats), _vp]),

@@ -36,7 +36,7 @@ cudaError_t launch_plan(const DevJob* jobs, uint32_t n_jobs, DevBlock* blocks, u
 
 namespace tmd {
 cudaError_t launch_search_lines(bool raw, const LineArgs& a, cudaStream_t s);
-cudaError_t launch_lower_bounds(bool lefevre, const uint64_t* B, const uint64_t* A, const uint32_t* len, uint64_t n,
+cudaError_t launch_lower_bounds(int mode, const uint64_t* B, const uint64_t* A, const uint32_t* len, uint64_t n,
                                 uint64_t* lb, uint32_t* hs, uint32_t* err, cudaStream_t s);
 }  // namespace tmd
 
@@ -683,17 +683,17 @@ tmd_status tmd_lower_bounds(tmd_ctx* c, const uint64_t* d_B, const uint64_t* d_A
     cudaStream_t s = (cudaStream_t)stream;
     CK(cudaSetDevice(c->device));
     CK(cudaMemsetAsync(err_ptr(c), 0, sizeof(uint32_t), s));
-    CK(launch_lower_bounds(false, d_B, d_A, d_len, n, d_lb, d_hs, err_ptr(c), s));
+    CK(launch_lower_bounds(0, d_B, d_A, d_len, n, d_lb, d_hs, err_ptr(c), s));
     return TMD_OK;
 }
 
 tmd_status tmd_lefevre_bounds(tmd_ctx* c, const uint64_t* d_B, const uint64_t* d_A, const uint32_t* d_len,
-                              uint64_t n, uint64_t* d_lb, uint32_t* d_iters, void* stream) {
-    if (!c || (n && (!d_B || !d_A || !d_len || !d_lb))) return TMD_EINVAL;
+                              uint64_t n, uint32_t specific, uint64_t* d_lb, uint32_t* d_iters, void* stream) {
+    if (!c || (n && (!d_B || !d_A || !d_len || !d_lb)) || specific > 1) return TMD_EINVAL;
     cudaStream_t s = (cudaStream_t)stream;
     CK(cudaSetDevice(c->device));
     CK(cudaMemsetAsync(err_ptr(c), 0, sizeof(uint32_t), s));
-    CK(launch_lower_bounds(true, d_B, d_A, d_len, n, d_lb, d_iters, err_ptr(c), s));
+    CK(launch_lower_bounds(specific ? 2 : 1, d_B, d_A, d_len, n, d_lb, d_iters, err_ptr(c), s));
     return TMD_OK;
 }
 

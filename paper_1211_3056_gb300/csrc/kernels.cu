@@ -280,6 +280,8 @@ __device__ __forceinline__ uint64_t cf_lower_bound(uint64_t B, uint64_t A, uint3
     return d;
 }
 
+__device__ __forceinline__ uint64_t udivmod64(uint64_t x, uint64_t b, uint64_t* r);
+
 // ------------------------------------------------ Lefevre, Algorithm 3
 // k = floor(a / b) clamped to 2^20 (it only feeds the saturating counts) and
 // a mod b, for any a and b > 0: no division for k <= 1, else an FP32
@@ -310,6 +312,13 @@ __device__ __forceinline__ uint64_t quot_rem(uint64_t a, uint64_t b, uint32_t& k
 // Returns d at the first u + v >= n; a division leaving a zero remainder
 // ends the loop with d reduced modulo the other length (rational a).
 // *iters = loop iterations (Table 3).  u, v saturate at n.
+// SPEC: Lefevre's specific instructions, read as taking a run of
+// consecutive iterations with quotient 0 in one iteration by exact
+// divisions: on the swapped side (q < p here: each d -= q, p -= q, v += u)
+// r = min(floor(d/q), floor((p-1)/q), the iterations left before u + v >= n);
+// on the other (q < p: each p -= q, v += u) r = ceil((p - max(d, q))/q) or
+// fewer if u + v reaches n.  Same states, far fewer iterations.
+template <bool SPEC>
 __device__ __noinline__ uint64_t lefevre_lower_bound(uint64_t B, uint64_t A, uint32_t n, uint32_t* iters) {
     if (A == 0) {
         *iters = 0;
@@ -327,18 +336,42 @@ __device__ __noinline__ uint64_t lefevre_lower_bound(uint64_t B, uint64_t A, uin
 #pragma unroll 1
     for (; it < (1u << 17); ) {  // u + v grows by at least one per iteration
         it++;
-        if (sw) d -= q;
-        uint32_t k;
-        q = quot_rem(q, p, k);
-        u = sat_madd(u, k, v, n);
-        if (u + v >= n) break;
-        if (q == 0) {
-            uint32_t kk;
-            d = quot_rem(d, p, kk);
-            break;
+        if (SPEC && !sw && q < p) {
+            // a run of unswapped iterations with quotient 0 (d < p, q < p:
+            // each p -= q, v += u while p stays above d and q)
+            uint64_t rem;
+            const uint64_t big = d > q ? d : q;
+            const uint64_t r = udivmod64(p - big - 1, q, &rem) + 1;
+            const uint64_t jx = u + v >= n ? 1ull : (uint64_t)((n - v + u - 1) / u);
+            if (jx <= r) break;  // d is unchanged by the run
+            p -= r * q;
+            v += (uint32_t)r * u;  // < n
+        } else if (SPEC && sw && q < p) {
+            uint64_t rem;
+            const uint64_t rd = udivmod64(d, q, &rem);
+            const uint64_t rp = udivmod64(p - 1, q, &rem);
+            // iterations up to the one whose exit test fires: the least j >= 1
+            // with v + j u >= n (u >= 1; v <= n)
+            const uint64_t jx = v + u >= n ? 1ull : (uint64_t)((n - v + u - 1) / u);
+            const uint64_t r = min(min(rd, rp), jx);
+            d -= r * q;
+            if ((uint64_t)v + r * (uint64_t)u >= (uint64_t)n) break;
+            p -= r * q;
+            v += (uint32_t)r * u;  // < n
+        } else {
+            if (sw) d -= q;
+            uint32_t k;
+            q = quot_rem(q, p, k);
+            u = sat_madd(u, k, v, n);
+            if (u + v >= n) break;
+            if (q == 0) {
+                uint32_t kk;
+                d = quot_rem(d, p, kk);
+                break;
+            }
+            p -= q;
+            v = min(v + u, n);
         }
-        p -= q;
-        v = min(v + u, n);
         const uint64_t l = sw ? q : p;
         if (sw != (d >= l)) {
             const uint64_t t = p;
@@ -816,7 +849,7 @@ __device__ __forceinline__ void fused_task(const DevTask& t, const LaunchArgs& a
         const uint64_t A = st.A[slot];
         uint32_t hs = 0;
         uint64_t lb = ~0ull;
-        if (n) lb = lefevre ? lefevre_lower_bound(B, A, n, &hs) : cf_lower_bound(B, A, n, &hs);
+        if (n) lb = lefevre ? lefevre_lower_bound<true>(B, A, n, &hs) : cf_lower_bound(B, A, n, &hs);
         const bool fail = n && lb < Tm;
         st_lines += n ? 1u : 0u;
         st_fail += fail ? 1u : 0u;
@@ -955,7 +988,7 @@ __global__ void __launch_bounds__(256) k_search_lines(LineArgs a) {
     }
     uint32_t hs = 0;
     uint64_t lb = ~0ull;
-    if (valid) lb = (flags & TMD_LEFEVRE) ? lefevre_lower_bound(B, A, n, &hs) : cf_lower_bound(B, A, n, &hs);
+    if (valid) lb = (flags & TMD_LEFEVRE) ? lefevre_lower_bound<true>(B, A, n, &hs) : cf_lower_bound(B, A, n, &hs);
     const bool fail = valid && lb < Tm;
     // all lanes of a warp share ALL_HITS in practice; take the warp's OR
     const bool all_hits = __any_sync(FULLMASK, valid && (flags & TMD_ALL_HITS));
@@ -964,7 +997,8 @@ __global__ void __launch_bounds__(256) k_search_lines(LineArgs a) {
     flush_stats(a.stats, valid ? 1u : 0u, fail ? 1u : 0u, hs);
 }
 
-template <bool LEFEVRE>
+// MODE 0: Algorithm 4; 1: Algorithm 3; 2: Algorithm 3 with the specific instructions
+template <int MODE>
 __global__ void __launch_bounds__(256) k_lower_bounds(const uint64_t* B, const uint64_t* A,
                                                       const uint32_t* len, uint64_t n, uint64_t* lb,
                                                       uint32_t* hs_out, uint32_t* err) {
@@ -976,7 +1010,9 @@ __global__ void __launch_bounds__(256) k_lower_bounds(const uint64_t* B, const u
         ln = ln == 0 ? 1u : 65536u;
     }
     uint32_t hs = 0;
-    lb[s] = LEFEVRE ? lefevre_lower_bound(B[s], A[s], ln, &hs) : cf_lower_bound(B[s], A[s], ln, &hs);
+    lb[s] = MODE == 0 ? cf_lower_bound(B[s], A[s], ln, &hs)
+                      : (MODE == 1 ? lefevre_lower_bound<false>(B[s], A[s], ln, &hs)
+                                   : lefevre_lower_bound<true>(B[s], A[s], ln, &hs));
     if (hs_out) hs_out[s] = hs;
 }
 
@@ -1158,13 +1194,16 @@ cudaError_t launch_search_lines(bool raw, const LineArgs& a, cudaStream_t s) {
     return cudaGetLastError();
 }
 
-cudaError_t launch_lower_bounds(bool lefevre, const uint64_t* B, const uint64_t* A, const uint32_t* len,
+cudaError_t launch_lower_bounds(int mode, const uint64_t* B, const uint64_t* A, const uint32_t* len,
                                 uint64_t n, uint64_t* lb, uint32_t* hs, uint32_t* err, cudaStream_t s) {
     if (n == 0) return cudaSuccess;
-    if (lefevre)
-        k_lower_bounds<true><<<(unsigned)((n + 255) / 256), 256, 0, s>>>(B, A, len, n, lb, hs, err);
+    const unsigned grid = (unsigned)((n + 255) / 256);
+    if (mode == 2)
+        k_lower_bounds<2><<<grid, 256, 0, s>>>(B, A, len, n, lb, hs, err);
+    else if (mode == 1)
+        k_lower_bounds<1><<<grid, 256, 0, s>>>(B, A, len, n, lb, hs, err);
     else
-        k_lower_bounds<false><<<(unsigned)((n + 255) / 256), 256, 0, s>>>(B, A, len, n, lb, hs, err);
+        k_lower_bounds<0><<<grid, 256, 0, s>>>(B, A, len, n, lb, hs, err);
     return cudaGetLastError();
 }
 

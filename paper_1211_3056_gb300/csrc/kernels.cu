@@ -174,7 +174,11 @@ __device__ __forceinline__ uint32_t sat_madd(uint32_t u, uint32_t k, uint32_t v,
 }
 
 // General half-step by FP32 estimates: k = floor(a/b) (a > b > 0),
-// a' = a mod b, and the reduction of x modulo b whose quotient is at most k.
+// a' = a mod b, and the reduction of x modulo b.  X_BELOW: x < a is known
+// (inside the loop d stays below the dividend), so x's estimate is in the
+// fast range whenever a's is (the estimate is monotonic in the dividend)
+// and only a's range is checked.
+template <bool X_BELOW>
 __device__ __forceinline__ void half_step_div(uint64_t a, uint64_t b, uint64_t x, uint64_t& a_out,
                                               uint32_t& k_out, uint64_t& x_out) {
     const float rbs = scaled_rcp(u64_to_f32_rz(b));
@@ -183,7 +187,7 @@ __device__ __forceinline__ void half_step_div(uint64_t a, uint64_t b, uint64_t x
     uint32_t kx = quot_estimate(u64_to_f32_rz(x), rbs, ok2);
     uint64_t an = rem_fix(a, b, k);
     uint64_t xn = rem_fix(x, b, kx);
-    if (!(ok1 && ok2)) {
+    if (!(ok1 && (X_BELOW || ok2))) {
         an = divmod_slow(a, b, k);
         xn = divmod_slow(x, b, kx);
     }
@@ -193,7 +197,8 @@ __device__ __forceinline__ void half_step_div(uint64_t a, uint64_t b, uint64_t x
 }
 
 // Second half-step by FP32 estimates: k = floor(p/q), p' = p mod q, then
-// d <- (d - p') mod q when d >= p' (the quotient of d - p' < k q is < k).
+// d <- (d - p') mod q when d >= p' (d - p' < k q <= p: its estimate is in
+// the fast range whenever p's is, so only p's range is checked).
 __device__ __forceinline__ void second_half_div(uint64_t& p, uint64_t q, uint64_t& d, uint32_t& k) {
     const float rqs = scaled_rcp(u64_to_f32_rz(q));
     bool ok1, ok2;
@@ -203,7 +208,8 @@ __device__ __forceinline__ void second_half_div(uint64_t& p, uint64_t q, uint64_
     uint64_t e = ge ? d - pn : 0ull;
     uint32_t ke = quot_estimate(u64_to_f32_rz(e), rqs, ok2);
     uint64_t en = rem_fix(e, q, ke);
-    if (!(ok1 && ok2)) {
+    (void)ok2;
+    if (!ok1) {
         pn = divmod_slow(p, q, kk);
         ge = d >= pn;
         en = divmod_slow(ge ? d - pn : 0ull, q, ke);
@@ -236,7 +242,7 @@ __device__ __forceinline__ uint64_t cf_lower_bound(uint64_t B, uint64_t A, uint3
     // and u = 1 + k * 0 stays 1
     {
         uint32_t k;
-        half_step_div(0ull - p, p, d, q, k, d);
+        half_step_div<false>(0ull - p, p, d, q, k, d);
     }
     if (1u >= n || q == 0) {
         *hs = h;
@@ -269,7 +275,7 @@ __device__ __forceinline__ uint64_t cf_lower_bound(uint64_t B, uint64_t A, uint3
                 d = csub(d, p);  // d < q < 2p
             } else {
                 uint32_t k;
-                half_step_div(q, p, d, q, k, d);
+                half_step_div<true>(q, p, d, q, k, d);
                 u = sat_madd(u, k, v, n);
             }
             h++;

@@ -277,6 +277,8 @@ def main():
                     help="also time the sound-mode search of exp on [1, 1+2^-13[ (0 = skip)")
     ap.add_argument("--lefevre", type=int, default=1,
                     help="also time the same slice with Lefevre's filter (0 = skip)")
+    ap.add_argument("--binade128", type=int, default=1,
+                    help="also time the sound search of exp on [128, 256), Table 7's regime (0 = skip)")
     ap.add_argument("--tiling", default="auto",
                     help="'auto' (tmd_autotune picks it) or 'nu,ctas_per_sm' for the batched form")
     args = ap.parse_args()
@@ -456,6 +458,43 @@ def main():
                              "line at eps2 (phase 2), exhaustive evaluation of failing pieces (phase 3)"}
         sb.close()
 
+    # Table 7's second binade: exp on [128, 256), where the degree-1 lines'
+    # truncation error is far above eps: a 2^36-argument slice at a seeded
+    # block-aligned start, sound (53, 2^-32) cases with N = 2^16, the
+    # regular and Lefevre's filter; the phases' argument counts are the
+    # table's rows (phase 2 = lines failing the first filter times N)
+    binade128 = None
+    if args.binade128:
+        import random
+        bstart = random.Random(128256).randrange(0, (1 << 52) - (1 << 36), 1 << 20)
+        bjob = wl.Job(wl.FUNC_EXP, 8, 53, 32, 16, 3, 20, 3, bstart, 1 << 36)
+        binade128 = {"workload": "exp binary64 [128, 256), 2^36-arg slice at Random(128256) block-aligned "
+                                 "start, sound (53, 2^-32) cases, d=3, W=192, N=2^16, T=2^20",
+                     "start": bstart, "unit": UNIT}
+        d_cand_b, d_count_b = tmd.alloc_candidates(1 << 16, local_rank)
+        recs_b = None
+        for name, flags in (("regular", 0), ("lefevre", wl.FLAG_LEFEVRE)):
+            sj = tmd.sound_job(bjob.replace(flags=bjob.flags | flags))
+            bb = tmd.Batch(ctx, [sj], d_cand_b, d_count_b)
+            b_ms = max_over_ranks(statistics.mean(timed(bb.launch, 10, 3)))
+            bst = bb.stats()
+            got_b = tmd.tmd_candidates(ctx, d_cand_b, d_count_b)
+            if recs_b is None:
+                recs_b = got_b
+            assert got_b == recs_b, "the two filters must give the same records"
+            nl = max(1, bst["lines"])
+            binade128[name] = {"value": sj.count / (b_ms / 1e3), "ms_per_step": b_ms,
+                               "phase1_args": sj.count,
+                               "phase2_args": bst["filter_fail"] << sj.log2_N,
+                               "phase3_args": bst["exhaustive_args"],
+                               "phase2_fraction": bst["filter_fail"] / nl,
+                               "phase3_fraction": bst["exhaustive_args"] / sj.count,
+                               "eps1_log2": math.log2(sj.eps1) - 64, "eps3_log2": math.log2(sj.eps3) - 64}
+            bb.close()
+        binade128["listed_arguments"] = recs_b[1]
+        binade128["form"] = ("batched: filter at eps1, exact line minimum, 32 refined pieces per failing line "
+                             "at eps2 (phase 2), exhaustive evaluation of failing pieces (phase 3)")
+
     mixed = None
     if args.mixed_jobs > 0:
         mjobs = wl.batched_jobs(njobs=args.mixed_jobs)
@@ -544,6 +583,7 @@ def main():
             "gpu_launches": args.steps * 1,
             "roofline": roofline, "cpu_baseline": cpu, "clocks": clocks, "lefevre": lefevre,
             "sound_table2": sound_run,
+            "binade_128_256": binade128,
             "mixed_batch": mixed,
             "large_batch": large,
             "serving": serving,

@@ -178,6 +178,8 @@ typedef struct {
     uint64_t half_steps;     /* continued-fraction half-steps, all lanes       */
     uint64_t upload_bytes;   /* bytes of the last plan upload (host -> device)  */
     uint64_t count;          /* the last search's *d_count                      */
+    uint64_t exhaustive_args; /* sound mode: arguments evaluated one by one in
+                                 the exhaustive phase (Sect. III-A phase 3)   */
 } tmd_stats;
 
 typedef struct tmd_ctx tmd_ctx;

@@ -9,10 +9,12 @@ enclosures come from exact partial sums of power series plus an explicit
 bound on the tail, so a reader can check each one against the series it
 sums:
 
-  exp(x)     = sum_n x^n / n!                      (x >= 0)
+  exp(x)     = sum_n x^n / n!                      (0 <= x <= 4)
+  exp(x)     = exp(x / 2^j)^(2^j)                   (x > 4, x / 2^j <= 1)
   atanh(z)   = sum_n z^(2n+1) / (2n+1)              (0 <= z < 1)
   ln 2       = 2 atanh(1/3)
-  2^x        = exp(x ln 2)
+  2^x        = exp(x ln 2)                          (x < 4)
+  2^x        = 2^n 2^(x - n),  n = floor(x)         (x >= 4, 2^n exact)
   log(X)     = e ln 2 - 2 atanh((1 - Y)/(1 + Y)),   X = Y 2^e, 1/2 <= Y < 1
 
 The Taylor coefficients f^(k)(X)/k! needed by the block polynomials of
@@ -44,12 +46,16 @@ def exp_interval(x: Fraction, bits: int) -> Interval:
     """exp(x) for rational x >= 0.
 
     Partial sum S_n = sum_{i<=n} x^i/i!; for n + 2 > x the tail is bounded by
-    the geometric majorant x^(n+1)/(n+1)! * 1/(1 - x/(n+2))."""
+    the geometric majorant x^(n+1)/(n+1)! * 1/(1 - x/(n+2)).  Above x = 4
+    (the binades [4, 8) and up) the argument is halved j times and the
+    enclosure squared back, see _exp_by_squaring."""
     x = Fraction(x)
     if x < 0:
         raise ValueError("exp_interval needs x >= 0")
     if x == 0:
         return Fraction(1), Fraction(1)
+    if x > 4:
+        return _exp_by_squaring(x, bits)
     eps = _pow2(-bits)
     term = Fraction(1)
     s = Fraction(1)
@@ -105,8 +111,34 @@ def _round_up(x: Fraction, bits: int) -> Fraction:
     return Fraction(-((-x.numerator << bits) // x.denominator), 1 << bits)
 
 
+def _exp_by_squaring(x: Fraction, bits: int) -> Interval:
+    """exp(x) = exp(x / 2^j)^(2^j) for x > 4 with x / 2^j <= 1.
+
+    The series encloses exp(x / 2^j); each squaring maps an enclosure of
+    positive numbers to one of their squares (t -> t^2 increases on t > 0),
+    and the ends are rounded outward to the grid 2^-g after every step so
+    that the fractions stay short.  The relative width at most doubles per
+    squaring plus two grid steps, which g = bits + 1.45 x + 2 j + 8 covers;
+    the width is checked at the end and g raised if it is not met."""
+    j = 0
+    while x / (1 << j) > 1:
+        j += 1
+    y = x / (1 << j)
+    eps = _pow2(-bits)
+    g = bits + int(x * Fraction(145, 100)) + 2 * j + 8
+    while True:
+        lo, hi = exp_interval(y, g)
+        lo, hi = _round_down(lo, g), _round_up(hi, g)
+        for _ in range(j):
+            lo, hi = _round_down(lo * lo, g), _round_up(hi * hi, g)
+        if hi - lo <= eps:
+            return lo, hi
+        g += 64
+
+
 def exp2_interval(x: Fraction, bits: int) -> Interval:
-    """2^x for rational x >= 0: exact at integers, else exp(x ln 2).
+    """2^x for rational x >= 0: exact at integers, else exp(x ln 2) (x >= 4:
+    2^n times 2^(x - n), n = floor(x)).
 
     The argument x ln 2 is enclosed, rounded outward to a dyadic grid, and
     exp is increasing, so exp(lower argument) <= 2^x <= exp(upper argument)."""
@@ -116,6 +148,10 @@ def exp2_interval(x: Fraction, bits: int) -> Interval:
     if x.denominator == 1:
         v = Fraction(1 << int(x))
         return v, v
+    if x >= 4:  # 2^x = 2^n 2^(x - n), the power of two exact
+        n = x.numerator // x.denominator
+        lo, hi = exp2_interval(x - n, bits + n)
+        return lo * (1 << n), hi * (1 << n)
     g = bits + 8 + int(x) + 2
     l_lo, l_hi = ln2_interval(g + 2)
     a_lo = _round_down(x * l_lo, g)

@@ -185,7 +185,8 @@ def tmd_stats_read(ctx: Context, stream=None) -> dict:
     s = _lib.tmd_stats()
     check(lib().tmd_stats_read(ctx.handle, ctypes.byref(s), _stream_ptr(stream)), "tmd_stats_read")
     return {"lines": s.lines, "filter_fail": s.filter_fail, "candidates": s.candidates,
-            "half_steps": s.half_steps, "upload_bytes": s.upload_bytes, "count": s.count}
+            "half_steps": s.half_steps, "upload_bytes": s.upload_bytes, "count": s.count,
+            "exhaustive_args": s.exhaustive_args}
 
 
 class Batch:
@@ -225,7 +226,8 @@ class Batch:
         s = _lib.tmd_stats()
         check(lib().tmd_batch_stats(self.handle, ctypes.byref(s), _stream_ptr(stream)), "tmd_batch_stats")
         return {"lines": s.lines, "filter_fail": s.filter_fail, "candidates": s.candidates,
-                "half_steps": s.half_steps, "upload_bytes": s.upload_bytes, "count": s.count}
+                "half_steps": s.half_steps, "upload_bytes": s.upload_bytes, "count": s.count,
+                "exhaustive_args": s.exhaustive_args}
 
     def close(self):
         if getattr(self, "handle", None):

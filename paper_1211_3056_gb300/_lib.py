@@ -62,7 +62,8 @@ class tmd_job_result(ctypes.Structure):
 class tmd_stats(ctypes.Structure):
     _fields_ = [("lines", ctypes.c_uint64), ("filter_fail", ctypes.c_uint64),
                 ("candidates", ctypes.c_uint64), ("half_steps", ctypes.c_uint64),
-                ("upload_bytes", ctypes.c_uint64), ("count", ctypes.c_uint64)]
+                ("upload_bytes", ctypes.c_uint64), ("count", ctypes.c_uint64),
+                ("exhaustive_args", ctypes.c_uint64)]
 
 
 class tmd_tiling(ctypes.Structure):

@@ -712,6 +712,7 @@ tmd_status tmd_stats_read(tmd_ctx* c, tmd_stats* out, void* stream) {
     out->half_steps = h[ST_HALF];
     out->upload_bytes = c->upload_bytes;
     out->count = cnt;
+    out->exhaustive_args = h[ST_EXH];
     return TMD_OK;
 }
 
@@ -990,6 +991,7 @@ tmd_status tmd_batch_stats(tmd_batch* b, tmd_stats* out, void* stream) {
     out->half_steps = h[ST_HALF];
     out->upload_bytes = b->upload_bytes;
     out->count = cnt;
+    out->exhaustive_args = h[ST_EXH];
     return TMD_OK;
 }
 

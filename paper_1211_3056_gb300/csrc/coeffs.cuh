@@ -7,7 +7,11 @@
 // with X_t = M 2^(e_in - p), M = 2^(p-1) + j_t.  exp and 2^x take one
 // enclosure of f(X_t) at precision P = E_0 + guard for every order (E_0 is
 // the largest scale); log takes one enclosure for k = 0 and exact rationals
-// (-1)^(k-1) / (k X^k) for k >= 1.  A coefficient is accepted when both ends
+// (-1)^(k-1) / (k X^k) for k >= 1.  Above the binade [2, 4) exp and 2^x are
+// range-reduced by the block's output exponent: with red = e_out - 1,
+// f(X) = 2^red g(X), g(X) = exp(X - red ln 2) or 2^(X - red), in [1, 2), and
+// 2^E_k f = 2^(E_k + red) g, so that the fixed-point widths are those of the
+// binade [1, 2) whatever the size of f.  A coefficient is accepted when both ends
 // of its enclosure round alike; the caller retries undecided blocks with
 // more limbs (Ziv's strategy).  RN rounds halves up (floor(v + 1/2)); halves
 // only occur for exact values, which are handled exactly.
@@ -28,7 +32,12 @@ struct CoeffConsts {
 
 struct CoeffJob {
     int func, e_in, p, d, L, scale_log2, log2_N;
+    int red;  // range-reduction exponent (0: none), see reduction_exponent
 };
+
+// red = e_out - 1 for exp and 2^x above the binade [2, 4), else 0 (the
+// arguments of the smaller binades keep their direct evaluation).
+TMD_HD int reduction_exponent(int func, int e_in, int e_out) { return (func != 2 && e_in > 2) ? e_out - 1 : 0; }
 
 namespace cf_detail {
 
@@ -129,6 +138,48 @@ TMD_HD bool exp2_arg(const CoeffJob& J, uint64_t M, unsigned PB, const CoeffCons
     return true;
 }
 
+// exp(X) 2^-red = exp(r), r = X - red ln 2 in [0, ln 2), X = M 2^-q, with
+// PB fractional bits.  r is enclosed from an enclosure of ln 2 with PB + 28
+// fractional bits (red < 2^11, so red ln 2 is known to 2^-(PB+17)) and
+// rounded outward to PB + 16 bits; exp is increasing, so exp(r_lo) and
+// exp(r_hi) enclose exp(r).  False when the enclosure of r is not inside
+// [0, 1) (red is not the output exponent's) or a width is exceeded.
+template <int NL>
+TMD_HD bool exp_reduced(const CoeffJob& J, uint64_t M, unsigned PB, const CoeffConsts& C, fx::Enc<NL>& f) {
+    using namespace fx;
+    const unsigned q = (unsigned)(J.p - J.e_in);
+    const unsigned PA = PB + 28;
+    if (J.red <= 0 || J.red >= 2048 || PA > LN2_BITS || PA < q || PA - q + 64 > 64u * NL) return false;
+    U<NL> llo, lhi;
+    cf_detail::ln2_at<NL>(C, PA, llo, lhi);
+    mul_u64(llo, (uint64_t)J.red);
+    mul_u64(lhi, (uint64_t)J.red);
+    U<NL> rlo, rhi;
+    set_zero(rlo);
+    rlo.w[0] = M;
+    shl(rlo, PA - q);
+    rhi = rlo;
+    if (sub(rlo, lhi)) return false;
+    if (sub(rhi, llo)) return false;
+    shr(rlo, 12);
+    const bool up = low_bits(rhi, 12);
+    shr(rhi, 12);
+    if (up) add_u64(rhi, 1);
+    if (bit_length(rhi) > PB + 16) return false;  // r < 1
+    uint64_t e_lo, e_hi;
+    U<NL> vlo, vhi;
+    if (!exp_big<NL>(rlo, PB + 16, 1, C.div, vlo, e_lo)) return false;
+    if (!exp_big<NL>(rhi, PB + 16, 1, C.div, vhi, e_hi)) return false;
+    add_u64(vhi, e_hi);
+    shr(vlo, 16);
+    const bool up2 = low_bits(vhi, 16);
+    shr(vhi, 16);
+    if (up2) add_u64(vhi, 1);
+    f.lo = vlo;
+    f.hi = vhi;
+    return true;
+}
+
 // Per-job anchor: an enclosure of f at the job's first block X_a (exp and
 // 2^x: f(X_a) with P2 fractional bits; log: log X_a with P), at the
 // precision of the job's first segment (the largest scale of the job).
@@ -141,6 +192,8 @@ struct Anchor {
     uint64_t Ma;
     uint32_t P;     // fractional bits of lo, hi
     uint32_t ok;
+    int32_t red;    // the reduction exponent the anchor's value carries
+    uint32_t pad;
     uint64_t lo[ANCHOR_LIMBS], hi[ANCHOR_LIMBS];
 };
 
@@ -148,12 +201,12 @@ namespace cf_detail {
 
 // fractional bits of the base enclosure of f for a block with this scale
 TMD_HD unsigned base_bits(const CoeffJob& J, int guard) {
-    const int E0 = 64 * J.L + J.scale_log2;
+    const int E0 = 64 * J.L + J.scale_log2 + J.red;
     const unsigned P = (unsigned)((E0 > 0 ? E0 : 0) + guard);
     return J.func == 2 ? P : P + 16;
 }
 
-// direct enclosure of f(X) (exp, 2^x: P2 = P + 16 bits; log: P bits)
+// direct enclosure of f(X) 2^-red (exp, 2^x: P2 = P + 16 bits; log: P bits)
 template <int NL>
 TMD_HD bool f_direct(const CoeffJob& J, uint64_t M, unsigned PB, const CoeffConsts& C, fx::Enc<NL>& f, bool& exact) {
     using namespace fx;
@@ -164,7 +217,11 @@ TMD_HD bool f_direct(const CoeffJob& J, uint64_t M, unsigned PB, const CoeffCons
         ln2_at<NL>(C, PB, ln2.lo, ln2.hi);
         return log_enc<NL>(M, J.p, J.e_in, PB, ln2, C.div, f);
     }
-    if (J.func == 0) return exp_small<NL>(M, q, PB, C.div, f);
+    if (J.func == 0) return J.red ? exp_reduced<NL>(J, M, PB, C, f) : exp_small<NL>(M, q, PB, C.div, f);
+    if (J.red) {  // 2^(X - red), X - red = (M - red 2^q) 2^-q in [0, 1)
+        if (q == 0 || q >= 64 || (M >> q) != (uint64_t)J.red) return false;
+        M -= (uint64_t)J.red << q;
+    }
     if (q == 0 || (M & ((1ull << q) - 1)) == 0) {  // 2^X at an integer X
         set_pow2(f.lo, PB + (unsigned)(q >= 64 ? 0 : (M >> q)));
         f.hi = f.lo;
@@ -182,6 +239,8 @@ TMD_HD bool job_anchor(const CoeffJob& J0, uint64_t Ma, int guard, const CoeffCo
     A.Ma = Ma;
     A.P = cf_detail::base_bits(J0, guard);
     A.ok = 0;
+    A.red = J0.red;
+    A.pad = 0;
     if ((int)A.P + 80 > 64 * NL) return false;
     fx::Enc<NL> f;
     bool exact;
@@ -202,7 +261,9 @@ template <int NL>
 TMD_HD bool f_anchored(const CoeffJob& J, uint64_t M, unsigned PB, const CoeffConsts& C, const Anchor& A,
                        fx::Enc<NL>& f) {
     using namespace fx;
-    if (!A.ok || M <= A.Ma || A.P < PB) return false;
+    // one reduction exponent: a reduced anchor serves the blocks of its
+    // own output binade (there X_t - X_a < ln 2, or < 1 for 2^x)
+    if (!A.ok || M <= A.Ma || A.P < PB || A.red != J.red) return false;
     Enc<NL> a;
     for (int i = 0; i < NL; i++) {
         a.lo.w[i] = i < ANCHOR_LIMBS ? A.lo[i] : 0;
@@ -254,7 +315,7 @@ TMD_HD bool block_coeffs(const CoeffJob& J, uint64_t M, int guard, const CoeffCo
                          const Anchor* anchor = nullptr) {
     using namespace fx;
     const int W = 64 * J.L;
-    const int E0 = W + J.scale_log2;
+    const int E0 = W + J.scale_log2 + J.red;  // f(X_t) is enclosed as 2^red g
     const unsigned P = (unsigned)((E0 > 0 ? E0 : 0) + guard);
     const unsigned q = (unsigned)(J.p - J.e_in);
     if ((int)P + 96 > 64 * NL) return false;

@@ -71,7 +71,8 @@ struct DevTask {
 enum { ERR_BAD_LENGTH = 1, ERR_ROUNDING = 2 };
 
 // Counters (device uint64 each) in the order of tmd_stats.
-enum { ST_LINES = 0, ST_FAIL = 1, ST_CAND = 2, ST_HALF = 3, ST_COUNT = 4 };
+// ST_EXH: arguments evaluated by the exhaustive phase of the sound mode
+enum { ST_LINES = 0, ST_FAIL = 1, ST_EXH = 2, ST_HALF = 3, ST_COUNT = 4 };
 
 // Launch-side description of one fused/unfused launch.
 struct LaunchArgs {

@@ -405,13 +405,47 @@ tmd_status validate_job(const tmd_job& job) {
     if (job.func == TMD_LOG) {
         if (job.e_in < 2 || job.e_in > 16) return TMD_EUNSUPPORTED;
     } else {
-        if (job.e_in < -16 || job.e_in > 2) return TMD_EUNSUPPORTED;
+        // up to [256, 512): the last binade of exp below binary64's overflow
+        if (job.e_in < -16 || job.e_in > 9) return TMD_EUNSUPPORTED;
     }
+    if (job.p - job.e_in < 8) return TMD_EUNSUPPORTED;
     uint64_t span = 1ull << (job.p - 1);
     if (job.count == 0 || job.start >= span || job.count > span - job.start) return TMD_EINVAL;
     // the sub-interval numbering of a job must fit 32 bits
     if ((job.count >> job.log2_N) + (job.count >> job.log2_T) + 8 >= (1ull << 32)) return TMD_EUNSUPPORTED;
     return TMD_OK;
+}
+
+// e(exp(X)) = K + 1 for the K with K ln 2 <= X < (K + 1) ln 2, X = M 2^-q:
+// K from a double estimate, confirmed on the exact fixed-point X against a
+// 192-bit enclosure of ln 2 (false when X is too close to a multiple of ln 2
+// to decide there).
+bool exp_exponent_reduced(uint64_t M, unsigned q, int* e) {
+    const CoeffConsts& C = coeff_consts();
+    const unsigned P = 192;
+    fx::U<5> llo, lhi, x;
+    cf_detail::ln2_at<5>(C, P, llo, lhi);
+    fx::set_zero(x);
+    x.w[0] = M;
+    fx::shl(x, P - q);
+    const double est = std::floor(std::ldexp((double)M, -(int)q) / 0.69314718055994530942);
+    for (int dk = -1; dk <= 1; dk++) {
+        const double kd = est + dk;
+        if (kd < 0 || kd > 4096) continue;
+        const uint64_t K = (uint64_t)kd;
+        fx::U<5> a = lhi, b = llo;
+        fx::mul_u64(a, K);       // >= K ln 2
+        fx::mul_u64(b, K + 1);   // <= (K + 1) ln 2
+        fx::U<5> t = x;
+        const bool ge = fx::sub(t, a) == 0;          // X >= K ln2_hi
+        fx::U<5> u = b;
+        const bool lt = fx::sub(u, x) == 0 && !fx::is_zero(u);  // X < (K+1) ln2_lo
+        if (ge && lt) {
+            *e = (int)K + 1;
+            return true;
+        }
+    }
+    return false;
 }
 
 // e(f(X)) from a 128-bit enclosure of f(X) (fixed-size routines, no heap);
@@ -420,6 +454,11 @@ tmd_status validate_job(const tmd_job& job) {
 bool output_exponent_fx(const tmd_job& job, uint64_t M, int* e) {
     const CoeffConsts& C = coeff_consts();
     const unsigned P = 128, q = (unsigned)(job.p - job.e_in);
+    if (job.func == TMD_EXP2 && job.e_in > 2) {  // 2^X in [2^n, 2^(n+1)), n = floor(X)
+        *e = (int)(M >> q) + 1;
+        return true;
+    }
+    if (job.func == TMD_EXP && job.e_in > 2) return exp_exponent_reduced(M, q, e);
     fx::Enc<6> f;
     if (job.func == TMD_EXP) {
         if (!fx::exp_small<6>(M, q, P, C.div, f)) return false;
@@ -571,6 +610,7 @@ CoeffJob coeff_job(const tmd_job& job, int e_out) {
     J.L = (int)job.limbs;
     J.scale_log2 = scale_log2(job, e_out);
     J.log2_N = (int)job.log2_N;
+    J.red = reduction_exponent(job.func, job.e_in, e_out);
     return J;
 }
 

@@ -726,6 +726,7 @@ __device__ __noinline__ void sound_exhaustive(bool fail, uint64_t B, uint64_t A,
         go = exact_min(B, A, n, &xm) < jb.Tm;
     }
     const uint32_t n2 = ((1u << jb.log2_N) + 31u) >> 5;
+    uint32_t exh = 0;  // arguments of the exhaustive phase (identical on every lane)
     unsigned todo = __ballot_sync(FULLMASK, go);
     while (todo) {
         const int src = __ffs(todo) - 1;
@@ -765,6 +766,7 @@ __device__ __noinline__ void sound_exhaustive(bool fail, uint64_t B, uint64_t A,
             pieces &= pieces - 1u;
             const uint32_t px0 = pc * n2;
             const uint32_t pend = min(px0 + n2, ns);
+            exh += pend - px0;
             // phase 3 over the piece
             Word<L> v[D + 1];
             const uint64_t y0 = ybase + px0 + (uint64_t)lane;
@@ -785,6 +787,7 @@ __device__ __noinline__ void sound_exhaustive(bool fail, uint64_t B, uint64_t A,
             }
         }
     }
+    if (lane == 0 && exh) atomicAdd((unsigned long long*)&a.stats[ST_EXH], (unsigned long long)exh);
 }
 
 // Lines per packet held in shared memory between the two phases of a task.
@@ -1085,6 +1088,7 @@ __device__ __forceinline__ CoeffJob block_coeff_job(const DevJob& jb, int e_out)
     J.L = (int)jb.L;
     J.scale_log2 = (jb.flags & TMD_BP_DIRECTED) ? jb.p - e_out : jb.p + 1 - e_out;
     J.log2_N = (int)jb.log2_N;
+    J.red = reduction_exponent(jb.func, jb.e_in, e_out);
     return J;
 }
 

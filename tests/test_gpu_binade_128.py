@@ -1,0 +1,148 @@
+"""GPU parity on the binade [128, 256) of exp, the second workload of
+Sect. V (Table 7): exp is far from linear there, so the degree-1 lines'
+truncation error dwarfs eps and the sound mode's first filter fails on
+nearly every line.  Through the C ABI:
+
+  * the literal-threshold search (range-reduced block coefficients on the
+    device) reports exactly the oracle's brute-force list, fused and
+    batched, across an output-binade cut, for exp and 2^x, up to the last
+    binade [256, 512) below binary64's overflow of exp;
+  * the sound mode reports exactly the oracle's Horner list, with the
+    regular and with Lefevre's filter, in the fused and batched forms;
+  * the counters show the heavy-failure regime (every line of a mid-binade
+    slice fails the first filter) and the exhaustive-phase argument count
+    covers every piece that holds a reported argument.
+"""
+import pytest
+
+import workloads as wl
+from oracle import candidates as oc
+from oracle import plan, sound
+
+torch = pytest.importorskip("torch")
+tmd = pytest.importorskip("paper_1211_3056_gb300")
+pytestmark = pytest.mark.gpu
+
+# first argument index with e(exp(X)) = 261 on [128, 256): X >= 260 ln 2
+CUT_260 = 1837266934047447
+# 2^x at X = 200 on [128, 256), p = 53
+X_200 = 72 << 45
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    c = tmd.Context(0)
+    yield c
+    c.close()
+
+
+LITERAL = [
+    wl.Job(wl.FUNC_EXP, 8, 53, 20, 14, 3, 20, 3, CUT_260 - (1 << 23), 1 << 24),
+    wl.Job(wl.FUNC_EXP2, 8, 53, 20, 12, 3, 18, 3, X_200 - (1 << 21) - 77, (1 << 22) + 555),
+    wl.Job(wl.FUNC_EXP, 9, 53, 20, 14, 3, 20, 3, (1 << 52) - (1 << 24), 1 << 24),
+    wl.Job(wl.FUNC_EXP, 3, 53, 20, 16, 3, 24, 3, 12345 << 24, 1 << 25, wl.FLAG_BP_DIRECTED),
+]
+
+
+@pytest.mark.parametrize("job", LITERAL, ids=lambda j: f"f{j.func}e{j.e_in}")
+def test_literal_search_equals_oracle(ctx, job):
+    want = oc.job_candidates(job, 0)
+    assert len(want) > 0
+    got, n = tmd.run([job], ctx=ctx, fused=True, cap=1 << 18)
+    assert n == len(want) and got == want
+
+
+def test_literal_batched_equals_oracle(ctx):
+    d_cand, d_count = tmd.alloc_candidates(1 << 18)
+    b = tmd.Batch(ctx, LITERAL, d_cand, d_count)
+    b.launch()
+    got, n = tmd.tmd_candidates(ctx, d_cand, d_count)
+    b.close()
+    want = sorted([r for i, j in enumerate(LITERAL) for r in oc.job_candidates(j, i)],
+                  key=lambda r: (r[0], r[2], r[3]))
+    assert n == len(want) and got == want
+
+
+# mid-binade slices (X near 208.25): generic slopes, every line fails the
+# first filter.  Next to a cut (f(X) near a power of two) the slope is
+# nearly an integer, the N points of a line cover a short arc only and most
+# lines truly miss the window; there Lefevre's bound sees it and Algorithm 4
+# (first partial quotient above N) does not -- parity only.
+MID = 2823693648527360
+SOUND = [
+    wl.Job(wl.FUNC_EXP, 8, 53, 14, 14, 3, 20, 3, MID, 1 << 20),
+    wl.Job(wl.FUNC_EXP2, 8, 53, 14, 14, 3, 20, 3, MID + 12345, (1 << 19) + 333),
+]
+SOUND_CUT = [
+    wl.Job(wl.FUNC_EXP, 8, 53, 14, 14, 3, 20, 3, CUT_260 - (1 << 19), 1 << 20),
+    wl.Job(wl.FUNC_EXP2, 8, 53, 14, 14, 3, 20, 3, X_200 - (1 << 18), (1 << 19) + 333),
+]
+
+
+def piece_args(job, records):
+    """Arguments in the distinct phase-2 pieces (32 per sub-interval) that
+    hold a listed argument."""
+    N = 1 << job.log2_N
+    n2 = (N + 31) // 32
+    blocks = plan.blocks(job)
+    pieces = set()
+    total = 0
+    for r in records:
+        blk = next(b for b in blocks if b.first_sub <= r[1] < b.first_sub + (b.length + N - 1) // N)
+        s0 = blk.start + (r[1] - blk.first_sub) * N
+        s_len = min(N, blk.start + blk.length - s0)
+        pc = (r[2] - s0) // n2
+        if (r[1], pc) not in pieces:
+            pieces.add((r[1], pc))
+            total += min(n2, s_len - pc * n2)
+    return total
+
+
+@pytest.mark.parametrize("lefevre", [False, True], ids=["regular", "lefevre"])
+@pytest.mark.parametrize("job", SOUND, ids=lambda j: f"f{j.func}e{j.e_in}")
+def test_sound_heavy_failure_equals_oracle(ctx, job, lefevre):
+    sj = tmd.sound_job(job.replace(flags=job.flags | (wl.FLAG_LEFEVRE if lefevre else 0)))
+    # the regime: the first filter's threshold exceeds 1/(2N) of the unit
+    assert sj.eps1 * 2 * (1 << job.log2_N) > 1 << 64
+    want = sound.sound_candidates([sj], [sj.eps3])
+    assert len(want) > 20
+    got, n = tmd.run([sj], ctx=ctx, fused=True, cap=1 << 18)
+    assert n == len(want) and got == want
+    st = tmd.tmd_stats_read(ctx)
+    assert st["filter_fail"] >= 0.99 * st["lines"]
+    assert piece_args(job, want) <= st["exhaustive_args"] <= job.count
+
+
+@pytest.mark.parametrize("job", SOUND_CUT, ids=lambda j: f"f{j.func}e{j.e_in}")
+def test_sound_across_a_cut_equals_oracle(ctx, job):
+    """Slices across an output-binade cut: same list with either filter;
+    Lefevre's filter fails no more lines than Algorithm 4's."""
+    want = None
+    fails = []
+    for flags in (0, wl.FLAG_LEFEVRE):
+        sj = tmd.sound_job(job.replace(flags=job.flags | flags))
+        if want is None:
+            want = sound.sound_candidates([sj], [sj.eps3])
+            assert len(want) > 20
+        got, n = tmd.run([sj], ctx=ctx, fused=True, cap=1 << 18)
+        assert n == len(want) and got == want
+        fails.append(tmd.tmd_stats_read(ctx)["filter_fail"])
+    assert fails[1] <= fails[0]
+
+
+def test_sound_batched_with_literal_jobs(ctx):
+    """Sound jobs of [128, 256) beside literal ones in one persistent launch."""
+    jobs = [tmd.sound_job(SOUND_CUT[0]), LITERAL[0], tmd.sound_job(SOUND[1])]
+    d_cand, d_count = tmd.alloc_candidates(1 << 18)
+    b = tmd.Batch(ctx, jobs, d_cand, d_count)
+    b.launch()
+    got, n = tmd.tmd_candidates(ctx, d_cand, d_count)
+    st = b.stats()
+    b.close()
+    want_sound = sound.sound_candidates([jobs[0], jobs[2]], [jobs[0].eps3, jobs[2].eps3])
+    remap = {0: 0, 1: 2}
+    want = sorted([(remap[r[0]],) + r[1:] for r in want_sound] + oc.job_candidates(jobs[1], 1),
+                  key=lambda r: (r[0], r[2], r[3]))
+    assert n == len(want) and got == want
+    assert st["exhaustive_args"] >= (piece_args(SOUND_CUT[0], [r for r in want_sound if r[0] == 0]) +
+                                     piece_args(SOUND[1], [r for r in want_sound if r[0] == 1]))

@@ -60,6 +60,13 @@ HOST_JOBS = [
     wl.Job(wl.FUNC_LOG, 3, 30, 20, 8, 2, 12, 2, 0, 1 << 29, wl.FLAG_BP_DIRECTED),
     wl.Job(wl.FUNC_EXP2, 0, 53, 42, 16, 1, 20, 1, 12345 << 20, 1 << 24),
     wl.Job(wl.FUNC_EXP, -5, 53, 40, 14, 2, 18, 2, 999 << 18, 1 << 22),
+    # range-reduced binades: exp on [128, 256) across the cut at 260 ln 2,
+    # 2^x across X = 200, exp on [4, 8) with three cuts, the top binades
+    wl.Job(wl.FUNC_EXP, 8, 53, 32, 16, 3, 20, 3, 1837266934047447 - (1 << 33), 1 << 34),
+    wl.Job(wl.FUNC_EXP2, 8, 53, 32, 14, 3, 20, 3, (72 << 45) - (1 << 31), 1 << 32),
+    wl.Job(wl.FUNC_EXP, 3, 40, 24, 10, 3, 20, 2, 0, 1 << 38),
+    wl.Job(wl.FUNC_EXP2, 9, 30, 16, 8, 2, 12, 2, 5 << 19, 1 << 21, wl.FLAG_BP_DIRECTED),
+    wl.Job(wl.FUNC_EXP, 9, 53, 40, 14, 3, 20, 3, (1 << 52) - (1 << 30), 1 << 30),
 ] + wl.batched_jobs()[:6]
 
 
@@ -94,7 +101,8 @@ def test_toy_every_block_table():
     ("m", 1, tmd._lib.TMD_EINVAL), ("m", 64, tmd._lib.TMD_EINVAL),
     ("log2_N", 17, tmd._lib.TMD_EUNSUPPORTED), ("d", 5, tmd._lib.TMD_EUNSUPPORTED),
     ("limbs", 4, tmd._lib.TMD_EUNSUPPORTED), ("count", 0, tmd._lib.TMD_EINVAL),
-    ("start", 1 << 52, tmd._lib.TMD_EINVAL), ("e_in", 3, tmd._lib.TMD_EUNSUPPORTED),
+    ("start", 1 << 52, tmd._lib.TMD_EINVAL), ("e_in", 10, tmd._lib.TMD_EUNSUPPORTED),
+    ("e_in", 46, tmd._lib.TMD_EUNSUPPORTED),
     ("log2_T", 13, tmd._lib.TMD_EINVAL), ("func", 7, tmd._lib.TMD_EINVAL),
     ("flags", 16, tmd._lib.TMD_EINVAL), ("flags", 8, tmd._lib.TMD_EINVAL), ("eps1", 5, tmd._lib.TMD_EINVAL)])
 def test_validation(field, value, status):
@@ -120,6 +128,8 @@ SOUND_JOBS = [
     wl.Job(wl.FUNC_LOG, 2, 20, 8, 6, 2, 10, 1, 100, 1 << 12),
     wl.Job(wl.FUNC_LOG, 3, 53, 40, 16, 2, 18, 3, 1 << 44, 1 << 30),
     wl.Job(wl.FUNC_EXP, 0, 20, 7, 6, 2, 10, 2, 0, 1 << 19),
+    wl.Job(wl.FUNC_EXP, 8, 53, 32, 16, 3, 20, 3, 1837266934047447 - (1 << 33), 1 << 34),
+    wl.Job(wl.FUNC_EXP2, 8, 53, 32, 14, 3, 20, 3, (72 << 45) - (1 << 31), 1 << 32),
 ]
 
 

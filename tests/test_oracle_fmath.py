@@ -110,3 +110,47 @@ def test_exponent_of():
     assert fmath.exponent_of(fmath.FUNC_EXP2, F(1)) == 2       # 2 = (1/2) 2^2
     assert fmath.exponent_of(fmath.FUNC_LOG, F(3)) == 1        # log 3 in [1, 2)
     assert fmath.exponent_of(fmath.FUNC_LOG, F(5, 2)) == 0     # log 2.5 in [1/2, 1)
+
+
+def test_large_arguments_against_libm():
+    """exp and 2^x on [4, 512) (the halving-squaring and integer-split
+    reductions) against libm, relative 1e-15."""
+    rng = random.Random(11)
+    for e_in in (3, 5, 8, 9):
+        for _ in range(20):
+            x = F(rng.randrange(1 << 40, 1 << 41), 1 << (41 - e_in))   # [2^(e_in-1), 2^e_in)
+            if x > 700:
+                continue
+            lo, hi = fmath.exp_interval(x, 64)
+            assert abs(float(lo) / math.exp(x) - 1) < 1e-15 and lo <= hi
+            lo2, hi2 = fmath.exp2_interval(x, 64)
+            assert abs(float(lo2) / 2.0 ** float(x) - 1) < 1e-15 and lo2 <= hi2
+
+
+def test_squaring_path_matches_series():
+    """exp(a + b) from the squaring path against exp(a) exp(b) from the
+    plain series (a, b <= 4), and the absolute width at several precisions."""
+    for a, b in ((F(3, 1), F(7, 4)), (F(37, 10), F(39, 10)), (F(1, 3), F(4))):
+        ea, eb = fmath.exp_interval(a, 200), fmath.exp_interval(b, 200)
+        lo, hi = fmath.exp_interval(a + b, 200)
+        assert ea[0] * eb[0] <= hi and lo <= ea[1] * eb[1]
+    for bits in (40, 128, 300):
+        for x in (F(4) + F(1, 2 ** 45), F(200 * 2 ** 45 + 12345, 2 ** 45)):
+            lo, hi = fmath.exp_interval(x, bits)
+            assert 0 <= hi - lo <= F(1, 2 ** bits)
+            lo, hi = fmath.exp2_interval(x, bits)
+            assert 0 < hi - lo <= F(1, 2 ** bits)
+
+
+def test_exp_brackets_powers_of_two():
+    """For dyadic x_lo < K ln 2 < x_hi (ln 2 from the atanh series, not exp),
+    exp(x_lo) < 2^K < exp(x_hi): ties the large-argument exp to ln 2."""
+    l_lo, l_hi = fmath.ln2_interval(200)
+    for K in (6, 100, 185, 369, 738):
+        x_lo = F((K * l_lo.numerator << 120) // l_lo.denominator, 1 << 120)
+        x_hi = x_lo + F(2, 1 << 120)
+        assert x_lo < K * l_lo and K * l_hi < x_hi
+        assert fmath.exp_interval(x_lo, 160)[1] < 2 ** K < fmath.exp_interval(x_hi, 160)[0]
+        # and e(f) flips exactly there
+        assert fmath.exponent_of(fmath.FUNC_EXP, x_lo) == K
+        assert fmath.exponent_of(fmath.FUNC_EXP, x_hi) == K + 1

@@ -18,6 +18,13 @@ SMALL = [
     wl.Job(wl.FUNC_EXP, 0, 20, 7, 6, 2, 10, 2, 0, 1 << 19),      # crosses e_out at ln 2, W = 128
 ]
 
+# The binade [128, 256) (range-reduced coefficients): exp across the cut at
+# 260 ln 2 (a one-argument first segment), 2^x across X = 200.
+BIG_BINADE = [
+    wl.Job(wl.FUNC_EXP, 8, 24, 7, 2, 2, 4, 1, 1837266934047447 >> 29, 1 << 11),
+    wl.Job(wl.FUNC_EXP2, 8, 24, 10, 3, 2, 5, 1, (72 << 16) - 700, 1 << 11),
+]
+
 
 def frac_cmod(v: Fraction) -> Fraction:
     """v cmod 1 in [-1/2, 1/2)."""
@@ -25,7 +32,7 @@ def frac_cmod(v: Fraction) -> Fraction:
     return f - 1 if f >= Fraction(1, 2) else f
 
 
-@pytest.mark.parametrize("job", SMALL, ids=lambda j: f"f{j.func}p{j.p}")
+@pytest.mark.parametrize("job", SMALL + BIG_BINADE[:1], ids=lambda j: f"f{j.func}e{j.e_in}p{j.p}")
 def test_eps_approx_holds_on_sampled_arguments(job):
     """|R_t(y)/2^W - s f(X)| cmod 1 <= eps_approx, X exact from enclosures."""
     ea = sound.eps_approx(job)
@@ -43,7 +50,8 @@ def test_eps_approx_holds_on_sampled_arguments(job):
                 assert abs(frac_cmod(r - v)) <= ea + Fraction(1, 1 << 90)
 
 
-@pytest.mark.parametrize("job", SMALL + [wl.plain_job(count_log2=30)], ids=lambda j: f"f{j.func}p{j.p}N{j.log2_N}")
+@pytest.mark.parametrize("job", SMALL + [wl.plain_job(count_log2=30)] + BIG_BINADE,
+                         ids=lambda j: f"f{j.func}e{j.e_in}p{j.p}N{j.log2_N}")
 def test_eps_trunc_holds_on_sampled_subintervals(job):
     """max_x |R_t(iN + x) - (b_i + alpha_i x)| cmod 2^W <= eps_trunc 2^W over
     whole sub-intervals (exact integers)."""
@@ -70,7 +78,7 @@ def test_eps_trunc_holds_on_sampled_subintervals(job):
     assert worst > et / 64   # the bound is not vacuous either
 
 
-@pytest.mark.parametrize("job", SMALL[:3], ids=lambda j: f"f{j.func}p{j.p}")
+@pytest.mark.parametrize("job", SMALL[:3] + BIG_BINADE[:1], ids=lambda j: f"f{j.func}e{j.e_in}p{j.p}")
 def test_sound_candidates_contain_every_hard_to_round_argument(job):
     """Every argument of the job decided hard-to-round from the exact f is
     in the exhaustive list taken at the smallest sound eps3; the list holds

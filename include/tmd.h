@@ -91,9 +91,12 @@ typedef enum { TMD_EXP = 0, TMD_EXP2 = 1, TMD_LOG = 2 } tmd_func;
 
 /* One search job: a slice of one binade of one function (Sect. III-A).
  * Argument index j in [0, 2^(p-1)) stands for X_j = (2^(p-1) + j) 2^(e_in - p).
- * Supported here: exp and 2^x with -16 <= e_in <= 2, log with 2 <= e_in <= 16,
- * 8 <= p <= 60, 2 <= m <= 63, 1 <= log2_N <= 16, log2_N <= log2_T <= 40,
- * 1 <= d <= 4, 1 <= limbs <= 3, count >= 1, start + count <= 2^(p-1). */
+ * Supported here: exp and 2^x with -16 <= e_in <= 9 (up to [256, 512), the
+ * last binade of exp below binary64's overflow; above [2, 4) the block
+ * coefficients are range-reduced by the output exponent), log with
+ * 2 <= e_in <= 16, 8 <= p <= 60, p - e_in >= 8, 2 <= m <= 63,
+ * 1 <= log2_N <= 16, log2_N <= log2_T <= 40, 1 <= d <= 4, 1 <= limbs <= 3,
+ * count >= 1, start + count <= 2^(p-1), at most 4 output binades per job. */
 typedef struct {
     int32_t  func;      /* tmd_func                                            */
     int32_t  e_in;      /* arguments in [2^(e_in-1), 2^e_in)                   */

@@ -279,6 +279,8 @@ def main():
                     help="also time the same slice with Lefevre's filter (0 = skip)")
     ap.add_argument("--binade128", type=int, default=1,
                     help="also time the sound search of exp on [128, 256), Table 7's regime (0 = skip)")
+    ap.add_argument("--binade128-log2", type=int, default=36,
+                    help="arguments of the [128, 256) slice (smaller only for profiling captures)")
     ap.add_argument("--tiling", default="auto",
                     help="'auto' (tmd_autotune picks it) or 'nu,ctas_per_sm' for the batched form")
     args = ap.parse_args()
@@ -454,8 +456,10 @@ def main():
                      "ms_per_step": s_ms, "listed_arguments": s_count,
                      "eps1_log2": math.log2(sjob.eps1) - 64, "eps3_log2": math.log2(sjob.eps3) - 64,
                      "filter_fail_per_line": sst["filter_fail"] / max(1, sst["lines"]),
+                     "phase3_args": sst["refined_args"], "one_by_one_args": sst["exhaustive_args"],
                      "form": "batched: filter at eps1, exact line minimum, 32 refined pieces per failing "
-                             "line at eps2 (phase 2), exhaustive evaluation of failing pieces (phase 3)"}
+                             "line at eps2 (phase 2); phase 3 on the failing pieces: 32 sub-pieces each "
+                             "tested against their own half-width, Horner at every argument of the failing ones"}
         sb.close()
 
     # Table 7's second binade: exp on [128, 256), where the degree-1 lines'
@@ -467,9 +471,9 @@ def main():
     if args.binade128:
         import random
         bstart = random.Random(128256).randrange(0, (1 << 52) - (1 << 36), 1 << 20)
-        bjob = wl.Job(wl.FUNC_EXP, 8, 53, 32, 16, 3, 20, 3, bstart, 1 << 36)
-        binade128 = {"workload": "exp binary64 [128, 256), 2^36-arg slice at Random(128256) block-aligned "
-                                 "start, sound (53, 2^-32) cases, d=3, W=192, N=2^16, T=2^20",
+        bjob = wl.Job(wl.FUNC_EXP, 8, 53, 32, 16, 3, 20, 3, bstart, 1 << args.binade128_log2)
+        binade128 = {"workload": f"exp binary64 [128, 256), 2^{args.binade128_log2}-arg slice at Random(128256) "
+                                 "block-aligned start, sound (53, 2^-32) cases, d=3, W=192, N=2^16, T=2^20",
                      "start": bstart, "unit": UNIT}
         d_cand_b, d_count_b = tmd.alloc_candidates(1 << 16, local_rank)
         recs_b = None
@@ -486,14 +490,16 @@ def main():
             binade128[name] = {"value": sj.count / (b_ms / 1e3), "ms_per_step": b_ms,
                                "phase1_args": sj.count,
                                "phase2_args": bst["filter_fail"] << sj.log2_N,
-                               "phase3_args": bst["exhaustive_args"],
+                               "phase3_args": bst["refined_args"],
+                               "one_by_one_args": bst["exhaustive_args"],
                                "phase2_fraction": bst["filter_fail"] / nl,
-                               "phase3_fraction": bst["exhaustive_args"] / sj.count,
+                               "phase3_fraction": bst["refined_args"] / sj.count,
                                "eps1_log2": math.log2(sj.eps1) - 64, "eps3_log2": math.log2(sj.eps3) - 64}
             bb.close()
         binade128["listed_arguments"] = recs_b[1]
         binade128["form"] = ("batched: filter at eps1, exact line minimum, 32 refined pieces per failing line "
-                             "at eps2 (phase 2), exhaustive evaluation of failing pieces (phase 3)")
+                             "at eps2 (phase 2); phase 3 on the failing pieces: 32 sub-pieces each tested "
+                             "against their own half-width, Horner at every argument of the failing ones")
 
     mixed = None
     if args.mixed_jobs > 0:

@@ -164,6 +164,16 @@ tmd_status tmd_sound_eps(const tmd_job* job, uint64_t* eps1, uint64_t* eps3);
  * job or eps3 >= 2^62. */
 tmd_status tmd_sound_piece_eps(const tmd_job* job, uint64_t* eps2);
 
+/* The sound half-width for lines of `length` consecutive arguments of the
+ * job (host only): job->eps3 + eps_trunc(length) + length + margin, the
+ * bound of tmd_sound_eps for lines of that length; tmd_sound_piece_eps is
+ * this at ceil(N/32).  The sound mode's phase 3 cuts each kept piece of more
+ * than 64 arguments into 32 sub-pieces of ceil(ceil(N/32)/32) arguments and
+ * tests their own lines against this half-width before it evaluates the
+ * failing ones argument by argument.  TMD_EINVAL for an invalid job, eps3 >=
+ * 2^62 or a length outside 1..N. */
+tmd_status tmd_sound_line_eps(const tmd_job* job, uint64_t length, uint64_t* eps);
+
 /* Per-block description returned by tmd_block_tables. */
 typedef struct {
     uint64_t start;          /* argument index of the block's first argument   */
@@ -183,6 +193,8 @@ typedef struct {
     uint64_t count;          /* the last search's *d_count                      */
     uint64_t exhaustive_args; /* sound mode: arguments evaluated one by one in
                                  the exhaustive phase (Sect. III-A phase 3)   */
+    uint64_t refined_args;   /* sound mode: arguments of the phase-2 pieces kept
+                                for phase 3                                    */
 } tmd_stats;
 
 typedef struct tmd_ctx tmd_ctx;
@@ -365,7 +377,7 @@ tmd_status tmd_batch_create_tiled(tmd_ctx* ctx, const tmd_job* jobs, uint32_t nj
 
 /* Autotuner of the batched form (no counterpart in the paper, which tunes
  * its block sizes by hand, Sect. V-A): builds the batch with every tiling of
- * nu in {8, 6, 4, 2} x ctas_per_sm in {occupancy .. 1}, times a few graph
+ * nu in {8, 6, 4, 2, 1} x ctas_per_sm in {occupancy .. 1}, times a few graph
  * replays of each on `stream` (CUDA events; records are counted, not
  * stored), and keeps the fastest in the context for batches of the same
  * signature.  *best receives it, *best_ms (may be NULL) its mean replay time.

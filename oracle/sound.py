@@ -29,7 +29,7 @@ The thresholds of a sound job, in units of 2^-64:
           up to N - 1 steps)
   eps2 >= eps3 + ceil(eps_trunc(N/32) 2^64) + N/32 + 2  (the same for the 32
           pieces of a failing sub-interval, each with its own line: the
-          paper's phase 2)
+          paper's phase 2; min_eps_len gives it for any line length)
 
 sound_candidates() is the definition of what the sound path reports: every
 argument whose polynomial value R_t(y), evaluated by direct Horner, has
@@ -117,12 +117,17 @@ def piece_length(job) -> int:
     return (N + 31) // 32
 
 
+def min_eps_len(job, eps3: int, length: int) -> int:
+    """The smallest sound half-width for lines of `length` consecutive
+    arguments (a stretch holding an argument within eps3 has its 64-bit line
+    within this half-width): eps3 + eps_trunc(length) + length + 2."""
+    return eps3 + _ceil(eps_trunc(job, length) * M64) + length + 2
+
+
 def min_eps2(job, eps3: int) -> int:
-    """The smallest sound phase-2 half-width for pieces of piece_length()
-    arguments (a piece holding an argument within eps3 has its 64-bit line
-    within eps2)."""
-    n2 = piece_length(job)
-    return eps3 + _ceil(eps_trunc(job, n2) * M64) + n2 + 2
+    """The smallest sound phase-2 half-width, for pieces of piece_length()
+    arguments."""
+    return min_eps_len(job, eps3, piece_length(job))
 
 
 def sound_candidates(jobs, eps3s) -> List[Tuple[int, int, int, int]]:

@@ -168,6 +168,16 @@ def tmd_sound_piece_eps(job) -> int:
     return e2.value
 
 
+def tmd_sound_line_eps(job, length: int) -> int:
+    """The sound half-width for lines of `length` arguments of a sound job
+    (host): what the library tests the sub-pieces of phase 3 against."""
+    j = make_job(job)
+    e = ctypes.c_uint64(0)
+    check(lib().tmd_sound_line_eps(ctypes.byref(j), ctypes.c_uint64(int(length)), ctypes.byref(e)),
+          "tmd_sound_line_eps")
+    return e.value
+
+
 def sound_job(job):
     """The job in sound mode with the library's sound thresholds."""
     e1, e3 = tmd_sound_eps(job)
@@ -186,7 +196,7 @@ def tmd_stats_read(ctx: Context, stream=None) -> dict:
     check(lib().tmd_stats_read(ctx.handle, ctypes.byref(s), _stream_ptr(stream)), "tmd_stats_read")
     return {"lines": s.lines, "filter_fail": s.filter_fail, "candidates": s.candidates,
             "half_steps": s.half_steps, "upload_bytes": s.upload_bytes, "count": s.count,
-            "exhaustive_args": s.exhaustive_args}
+            "exhaustive_args": s.exhaustive_args, "refined_args": s.refined_args}
 
 
 class Batch:
@@ -227,7 +237,7 @@ class Batch:
         check(lib().tmd_batch_stats(self.handle, ctypes.byref(s), _stream_ptr(stream)), "tmd_batch_stats")
         return {"lines": s.lines, "filter_fail": s.filter_fail, "candidates": s.candidates,
                 "half_steps": s.half_steps, "upload_bytes": s.upload_bytes, "count": s.count,
-                "exhaustive_args": s.exhaustive_args}
+                "exhaustive_args": s.exhaustive_args, "refined_args": s.refined_args}
 
     def close(self):
         if getattr(self, "handle", None):

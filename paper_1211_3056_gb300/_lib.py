@@ -63,7 +63,7 @@ class tmd_stats(ctypes.Structure):
     _fields_ = [("lines", ctypes.c_uint64), ("filter_fail", ctypes.c_uint64),
                 ("candidates", ctypes.c_uint64), ("half_steps", ctypes.c_uint64),
                 ("upload_bytes", ctypes.c_uint64), ("count", ctypes.c_uint64),
-                ("exhaustive_args", ctypes.c_uint64)]
+                ("exhaustive_args", ctypes.c_uint64), ("refined_args", ctypes.c_uint64)]
 
 
 class tmd_tiling(ctypes.Structure):
@@ -95,6 +95,7 @@ SIGNATURES = {
     "tmd_lefevre_bounds": (ctypes.c_int, [_vp, _vp, _vp, _vp, _u64, _u32, _vp, _vp, _vp]),
     "tmd_sound_eps": (ctypes.c_int, [ctypes.POINTER(tmd_job), ctypes.POINTER(_u64), ctypes.POINTER(_u64)]),
     "tmd_sound_piece_eps": (ctypes.c_int, [ctypes.POINTER(tmd_job), ctypes.POINTER(_u64)]),
+    "tmd_sound_line_eps": (ctypes.c_int, [ctypes.POINTER(tmd_job), _u64, ctypes.POINTER(_u64)]),
     "tmd_stats_read": (ctypes.c_int, [_vp, ctypes.POINTER(tmd_stats), _vp]),
     "tmd_batch_create": (ctypes.c_int, [_vp, ctypes.POINTER(tmd_job), _u32, _vp, _u64, _vp, _vp,
                                         ctypes.POINTER(_vp), ctypes.POINTER(_u64)]),

@@ -80,7 +80,7 @@ struct tmd_ctx {
     char* d_arena = nullptr;
     size_t arena_cap = 0;
     size_t off_jobs = 0, off_blocks = 0, off_tables = 0, off_tasks = 0;
-    // counters: stats[4] u64, err u32, queue head u32
+    // counters: stats[5] u64, err u32, queue head u32
     uint64_t* d_misc = nullptr;
     // pinned staging for uploads
     char* h_stage = nullptr;
@@ -128,15 +128,20 @@ void run_threads(unsigned n, F&& fn) {
     for (auto& t : th) t.join();
 }
 
+// Lines per packet of a job.  Sound jobs whose first filter fails on most
+// lines (half-width eps1 over N arguments covering a quarter of the unit or
+// more: the binades where the degree-1 truncation dwarfs eps) take one line
+// per packet whatever the tiling: each line then carries phases 2 and 3,
+// and 32-line tasks keep the warps of the grid evenly loaded.
 uint32_t choose_nu(const tmd_job& job, uint64_t n_sub_block, uint32_t nu_max) {
     const char* env = getenv("TMD_NU");
     uint32_t nu = 8;  // at most the kernels' shared-memory stage (8 lines per lane)
     if (nu_max) nu = nu_max;
     else if (env && atoi(env) > 0) nu = (uint32_t)atoi(env);
+    if ((job.flags & TMD_SOUND) && (job.eps1 >> (61 - job.log2_N)) != 0) nu = 1;
     if (nu > 8) nu = 8;
     if (nu > n_sub_block) nu = (uint32_t)n_sub_block;
     if (nu < 1) nu = 1;
-    (void)job;
     return nu;
 }
 
@@ -206,6 +211,15 @@ tmd_status build_plan(const tmd_job* jobs, uint32_t njobs, Plan& P, bool host_ta
             dj.shift2 = e2;
         }
         dj.T2 = 2 * dj.shift2;
+        dj.shift2s = 0;
+        const uint64_t n2 = sound_piece_length(jb.log2_N);
+        if (sound && n2 > 64) {
+            uint64_t e2s = 0;
+            const tmd_status s2 = sound_line_eps(jb, jb.eps3, (n2 + 31) / 32, &e2s);
+            if (s2 != TMD_OK) return s2;
+            dj.shift2s = e2s;
+        }
+        dj.T2s = 2 * dj.shift2s;
         dj.log2_N = jb.log2_N;
         dj.log2_T = jb.log2_T;
         dj.d = (uint32_t)jb.d;
@@ -527,6 +541,11 @@ tmd_status tmd_sound_eps(const tmd_job* job, uint64_t* eps1, uint64_t* eps3) {
     return sound_eps(*job, eps1, eps3);
 }
 
+tmd_status tmd_sound_line_eps(const tmd_job* job, uint64_t length, uint64_t* eps) {
+    if (!job || !eps) return TMD_EINVAL;
+    return sound_line_eps(*job, job->eps3, length, eps);
+}
+
 tmd_status tmd_sound_piece_eps(const tmd_job* job, uint64_t* eps2) {
     if (!job || !eps2) return TMD_EINVAL;
     return sound_piece_eps(*job, job->eps3, eps2);
@@ -713,13 +732,14 @@ tmd_status tmd_stats_read(tmd_ctx* c, tmd_stats* out, void* stream) {
     out->upload_bytes = c->upload_bytes;
     out->count = cnt;
     out->exhaustive_args = h[ST_EXH];
+    out->refined_args = h[ST_REF];
     return TMD_OK;
 }
 
 // ---------------------------------------------------------------- batches
 }  // extern "C"
 
-// batch counters: stats[4] | error | unused | plan error | pad | queue heads (one per class)
+// batch counters: stats[5] | error | unused | plan error | pad | queue heads (one per class)
 enum { BATCH_MISC_BYTES = 192, BATCH_QUEUE_OFF = 64 };
 
 struct tmd_batch {
@@ -822,7 +842,7 @@ tmd_status tmd_autotune(tmd_ctx* c, const tmd_job* jobs, uint32_t njobs, void* s
     tmd_status st = TMD_OK;
     tmd_tiling win = {0, 0};
     float win_ms = 0.f;
-    static const uint32_t nus[] = {8, 6, 4, 2};
+    static const uint32_t nus[] = {8, 6, 4, 2, 1};
     for (uint32_t nu : nus) {
         for (int k = occ; k >= 1 && st == TMD_OK; k--) {
             const tmd_tiling t = {nu, (uint32_t)k};
@@ -992,6 +1012,7 @@ tmd_status tmd_batch_stats(tmd_batch* b, tmd_stats* out, void* stream) {
     out->upload_bytes = b->upload_bytes;
     out->count = cnt;
     out->exhaustive_args = h[ST_EXH];
+    out->refined_args = h[ST_REF];
     return TMD_OK;
 }
 
@@ -1021,7 +1042,7 @@ struct ServerResult {
     std::vector<tmd_candidate> recs;
 };
 
-// Slot meta block on the device: stats[4] | error | queue head | plan error | pad | count.
+// Slot meta block on the device: stats[5] | error | queue head | plan error | pad | count.
 enum { META_BYTES = 128, META_COUNT_OFF = 64 };
 
 // One resident group of jobs: its stream, plan arena, records and counters.
@@ -1417,7 +1438,7 @@ tmd_status tmd_server_destroy(tmd_server* S) {
 
 namespace {
 
-constexpr size_t STATIC_MISC_BYTES = 256;  // stats[4], error word, queue head
+constexpr size_t STATIC_MISC_BYTES = 256;  // stats[5], error word, queue head
 __device__ __align__(256) unsigned char g_static_scratch[STATIC_MISC_BYTES + TMD_STATIC_SCRATCH_BYTES];
 
 constexpr int STATIC_MAX_DEVICES = 64;

@@ -43,6 +43,8 @@ struct DevJob {
     uint64_t T3;
     uint64_t shift2;       // sound mode: the phase-2 pieces' half-width eps2 (T2 = 2 eps2)
     uint64_t T2;
+    uint64_t shift2s;      // sound mode: half-width of the pieces' 32 sub-pieces (0: pieces of
+    uint64_t T2s;          // at most 64 arguments go to the exhaustive phase directly)
 };
 
 // One Taylor block.
@@ -71,8 +73,9 @@ struct DevTask {
 enum { ERR_BAD_LENGTH = 1, ERR_ROUNDING = 2 };
 
 // Counters (device uint64 each) in the order of tmd_stats.
-// ST_EXH: arguments evaluated by the exhaustive phase of the sound mode
-enum { ST_LINES = 0, ST_FAIL = 1, ST_EXH = 2, ST_HALF = 3, ST_COUNT = 4 };
+// ST_EXH: arguments evaluated one by one in the sound mode; ST_REF: arguments
+// of the phase-2 pieces the sound mode keeps (phase 3's input)
+enum { ST_LINES = 0, ST_FAIL = 1, ST_EXH = 2, ST_HALF = 3, ST_REF = 4, ST_COUNT = 5 };
 
 // Launch-side description of one fused/unfused launch.
 struct LaunchArgs {

@@ -718,18 +718,22 @@ tmd_status sound_eps(const tmd_job& job, uint64_t* eps1, uint64_t* eps3) {
 
 uint32_t sound_piece_length(uint32_t log2_N) { return ((1u << log2_N) + 31u) / 32u; }
 
-tmd_status sound_piece_eps(const tmd_job& job, uint64_t eps3, uint64_t* eps2) {
+tmd_status sound_line_eps(const tmd_job& job, uint64_t eps3, uint64_t length, uint64_t* eps) {
     double ea, et;
     int m;
     uint32_t lN;
-    const uint32_t n2 = sound_piece_length(job.log2_N);
-    tmd_status st = sound_bounds(job, (double)n2, &ea, &et, &m, &lN);
+    if (length == 0 || length > (1ull << job.log2_N)) return TMD_EINVAL;
+    tmd_status st = sound_bounds(job, (double)length, &ea, &et, &m, &lN);
     if (st != TMD_OK) return st;
     if (!(et < 0x1p61) || eps3 >= (1ull << 62)) return TMD_EINVAL;
-    const uint64_t e2 = eps3 + (uint64_t)std::ceil(et) + n2 + 2;
-    if (e2 >= (1ull << 62)) return TMD_EINVAL;
-    *eps2 = e2;
+    const uint64_t e = eps3 + (uint64_t)std::ceil(et) + length + 2;
+    if (e >= (1ull << 62)) return TMD_EINVAL;
+    *eps = e;
     return TMD_OK;
+}
+
+tmd_status sound_piece_eps(const tmd_job& job, uint64_t eps3, uint64_t* eps2) {
+    return sound_line_eps(job, eps3, sound_piece_length(job.log2_N), eps2);
 }
 
 }  // namespace tmd

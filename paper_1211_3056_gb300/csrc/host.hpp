@@ -28,6 +28,7 @@ tmd_status sound_eps(const tmd_job& job, uint64_t* eps1, uint64_t* eps3);
 // phase-2 half-width for a sound job's eps3.
 uint32_t sound_piece_length(uint32_t log2_N);
 tmd_status sound_piece_eps(const tmd_job& job, uint64_t eps3, uint64_t* eps2);
+tmd_status sound_line_eps(const tmd_job& job, uint64_t eps3, uint64_t length, uint64_t* eps);
 
 // e(f(X_j)) (Def. 1) for argument index j.
 int output_exponent(const tmd_job& job, uint64_t j);

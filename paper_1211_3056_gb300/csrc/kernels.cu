@@ -707,14 +707,31 @@ __device__ __forceinline__ Word<L> poly_at(const Word<L>* c, uint64_t y) {
 
 // Sound mode after the filter (Sect. III-A phases 2 and 3).  A line of the
 // warp that failed Algorithm 4 and whose exact minimum is below 2 eps1 is
-// cut into 32 pieces of ceil(N/32) arguments, one per lane; each lane forms
-// its piece's own line from the block polynomial (R_t at the piece start
-// and the next argument, the search words shifted by eps2) and keeps the
-// piece if its exact minimum is below 2 eps2 (phase 2).  Every kept piece
-// has R_t evaluated at each of its arguments by the whole warp: lane l
-// starts at the piece start + l with the step-32 forward differences of R_t
-// (Horner at y0, y0 + 32, ..., y0 + 32 D) and steps them; every argument
-// with (top64(R_t(y)) + eps3) mod 2^64 < 2 eps3 is emitted (phase 3).
+// cut into 32 pieces of n2 = ceil(N/32) arguments, one per lane; each lane
+// forms its piece's own line from the block polynomial (R_t at the piece
+// start and the next argument, the search words shifted by eps2) and keeps
+// the piece if its exact minimum is below 2 eps2 (phase 2).  Phase 3 takes
+// the kept pieces one at a time with the whole warp.  A piece of more than
+// 64 arguments is first cut the same way into 32 sub-pieces of
+// ceil(n2/32) arguments, tested against their own half-width eps2s, and R_t
+// is evaluated by Horner at every argument of the failing sub-pieces; a
+// shorter piece has R_t evaluated at each of its arguments directly, lane l
+// starting at the piece start + l with the step-32 forward differences of
+// R_t (Horner at y0, y0 + 32, ..., y0 + 32 D) and stepping them.  Every
+// argument with (top64(R_t(y)) + eps3) mod 2^64 < 2 eps3 is emitted.
+template <int L>
+__device__ __forceinline__ bool piece_line_fails(const Word<L>& r0, Word<L> r1, uint64_t shift, uint64_t T,
+                                                 uint32_t len) {
+    w_sub<L>(r1, r0);
+    uint64_t low = 0;
+#pragma unroll
+    for (int l = 0; l + 1 < L; l++) low |= r1.l[l];
+    const uint64_t B = r0.l[L - 1] + shift;
+    const uint64_t A = ~r1.l[L - 1] + (low == 0 ? 1ull : 0ull);
+    uint32_t xm;
+    return exact_min(B, A, len, &xm) < T;
+}
+
 template <int L, int D>
 __device__ __noinline__ void sound_exhaustive(bool fail, uint64_t B, uint64_t A, uint32_t n, uint64_t table_off,
                                               uint32_t i, uint32_t sub, uint64_t arg_base, uint32_t job,
@@ -726,7 +743,9 @@ __device__ __noinline__ void sound_exhaustive(bool fail, uint64_t B, uint64_t A,
         go = exact_min(B, A, n, &xm) < jb.Tm;
     }
     const uint32_t n2 = ((1u << jb.log2_N) + 31u) >> 5;
-    uint32_t exh = 0;  // arguments of the exhaustive phase (identical on every lane)
+    const uint32_t n3 = (n2 + 31u) >> 5;
+    const bool two_level = jb.T2s != 0;
+    uint32_t exh = 0, refined = 0;  // identical on every lane
     unsigned todo = __ballot_sync(FULLMASK, go);
     while (todo) {
         const int src = __ffs(todo) - 1;
@@ -748,26 +767,43 @@ __device__ __noinline__ void sound_exhaustive(bool fail, uint64_t B, uint64_t A,
         const uint32_t x0 = (uint32_t)lane * n2;
         const uint32_t len = x0 < ns ? min(n2, ns - x0) : 0u;
         bool keep = false;
-        if (len) {
-            const Word<L> r0 = poly_at<L, D>(c, ybase + x0);
-            Word<L> al = poly_at<L, D>(c, ybase + x0 + 1);
-            w_sub<L>(al, r0);
-            uint64_t low = 0;
-#pragma unroll
-            for (int l = 0; l + 1 < L; l++) low |= al.l[l];
-            const uint64_t B2 = r0.l[L - 1] + jb.shift2;
-            const uint64_t A2 = ~al.l[L - 1] + (low == 0 ? 1ull : 0ull);
-            uint32_t xm;
-            keep = exact_min(B2, A2, len, &xm) < jb.T2;
-        }
+        if (len)
+            keep = piece_line_fails<L>(poly_at<L, D>(c, ybase + x0), poly_at<L, D>(c, ybase + x0 + 1), jb.shift2,
+                                       jb.T2, len);
         unsigned pieces = __ballot_sync(FULLMASK, keep);
         while (pieces) {
             const uint32_t pc = (uint32_t)(__ffs(pieces) - 1);
             pieces &= pieces - 1u;
             const uint32_t px0 = pc * n2;
             const uint32_t pend = min(px0 + n2, ns);
+            refined += pend - px0;
+            if (two_level) {
+                // this lane's sub-piece [s0, s0 + slen) of the piece
+                const uint32_t s0 = px0 + (uint32_t)lane * n3;
+                const uint32_t slen = s0 < pend ? min(n3, pend - s0) : 0u;
+                bool keep2 = false;
+                if (slen)
+                    keep2 = piece_line_fails<L>(poly_at<L, D>(c, ybase + s0), poly_at<L, D>(c, ybase + s0 + 1),
+                                                jb.shift2s, jb.T2s, slen);
+                unsigned subs = __ballot_sync(FULLMASK, keep2);
+                while (subs) {
+                    const uint32_t sp = (uint32_t)(__ffs(subs) - 1);
+                    subs &= subs - 1u;
+                    const uint32_t sx0 = px0 + sp * n3;
+                    const uint32_t send = min(sx0 + n3, pend);
+                    exh += send - sx0;
+                    const uint32_t trips = (send - sx0 + 31u) >> 5;
+#pragma unroll 1
+                    for (uint32_t t = 0; t < trips; t++) {
+                        const uint32_t x = sx0 + t * 32u + (uint32_t)lane;
+                        const uint64_t val = poly_at<L, D>(c, ybase + x).l[L - 1] + jb.shift3;
+                        emit_warp(x < send && val < jb.T3, js, ss, ab + x, val, a.cand, a.cap, a.count);
+                    }
+                }
+                continue;
+            }
+            // phase 3 over the whole piece
             exh += pend - px0;
-            // phase 3 over the piece
             Word<L> v[D + 1];
             const uint64_t y0 = ybase + px0 + (uint64_t)lane;
 #pragma unroll
@@ -788,6 +824,7 @@ __device__ __noinline__ void sound_exhaustive(bool fail, uint64_t B, uint64_t A,
         }
     }
     if (lane == 0 && exh) atomicAdd((unsigned long long*)&a.stats[ST_EXH], (unsigned long long)exh);
+    if (lane == 0 && refined) atomicAdd((unsigned long long*)&a.stats[ST_REF], (unsigned long long)refined);
 }
 
 // Lines per packet held in shared memory between the two phases of a task.

@@ -104,7 +104,7 @@ def test_every_tiling_gives_the_oracle_list(ctx, tiling):
 def test_autotune_picks_a_valid_tiling_and_batches_use_it(ctx):
     jobs = wl.batched_jobs(njobs=6, m=24, size_log2_range=(24.0, 27.0))
     best = tmd.tmd_autotune(ctx, jobs)
-    assert best["nu"] in (2, 4, 6, 8) and best["ctas_per_sm"] >= 1 and best["ms"] > 0
+    assert best["nu"] in (1, 2, 4, 6, 8) and best["ctas_per_sm"] >= 1 and best["ms"] > 0
     d_cand, d_count = tmd.alloc_candidates(1 << 18)
     b = tmd.Batch(ctx, jobs, d_cand, d_count)      # takes the tuned tiling
     nu, per_sm = b.tiling()

@@ -10,8 +10,9 @@ nearly every line.  Through the C ABI:
   * the sound mode reports exactly the oracle's Horner list, with the
     regular and with Lefevre's filter, in the fused and batched forms;
   * the counters show the heavy-failure regime (every line of a mid-binade
-    slice fails the first filter) and the exhaustive-phase argument count
-    covers every piece that holds a reported argument.
+    slice fails the first filter), and the argument counts of phase 3's
+    input and of its one-by-one evaluation cover every piece and sub-piece
+    that holds a reported argument.
 """
 import pytest
 
@@ -79,23 +80,33 @@ SOUND_CUT = [
 ]
 
 
-def piece_args(job, records):
-    """Arguments in the distinct phase-2 pieces (32 per sub-interval) that
-    hold a listed argument."""
+def unit_args(job, records, level):
+    """Arguments in the distinct phase-2 pieces (level 1: 32 per
+    sub-interval) or phase-3 sub-pieces (level 2: 32 per piece of more than
+    64 arguments) that hold a listed argument."""
     N = 1 << job.log2_N
     n2 = (N + 31) // 32
+    n3 = (n2 + 31) // 32 if level == 2 and n2 > 64 else n2
     blocks = plan.blocks(job)
-    pieces = set()
+    units = set()
     total = 0
     for r in records:
         blk = next(b for b in blocks if b.first_sub <= r[1] < b.first_sub + (b.length + N - 1) // N)
         s0 = blk.start + (r[1] - blk.first_sub) * N
         s_len = min(N, blk.start + blk.length - s0)
-        pc = (r[2] - s0) // n2
-        if (r[1], pc) not in pieces:
-            pieces.add((r[1], pc))
-            total += min(n2, s_len - pc * n2)
+        x = r[2] - s0
+        px0 = x // n2 * n2
+        pend = min(px0 + n2, s_len)
+        u0 = px0 + (x - px0) // n3 * n3
+        if (r[1], u0) not in units:
+            units.add((r[1], u0))
+            total += min(u0 + n3, pend) - u0
     return total
+
+
+def check_phase_counts(st, job, records):
+    assert unit_args(job, records, 1) <= st["refined_args"] <= job.count
+    assert unit_args(job, records, 2) <= st["exhaustive_args"] <= st["refined_args"]
 
 
 @pytest.mark.parametrize("lefevre", [False, True], ids=["regular", "lefevre"])
@@ -110,7 +121,7 @@ def test_sound_heavy_failure_equals_oracle(ctx, job, lefevre):
     assert n == len(want) and got == want
     st = tmd.tmd_stats_read(ctx)
     assert st["filter_fail"] >= 0.99 * st["lines"]
-    assert piece_args(job, want) <= st["exhaustive_args"] <= job.count
+    check_phase_counts(st, job, want)
 
 
 @pytest.mark.parametrize("job", SOUND_CUT, ids=lambda j: f"f{j.func}e{j.e_in}")
@@ -144,5 +155,6 @@ def test_sound_batched_with_literal_jobs(ctx):
     want = sorted([(remap[r[0]],) + r[1:] for r in want_sound] + oc.job_candidates(jobs[1], 1),
                   key=lambda r: (r[0], r[2], r[3]))
     assert n == len(want) and got == want
-    assert st["exhaustive_args"] >= (piece_args(SOUND_CUT[0], [r for r in want_sound if r[0] == 0]) +
-                                     piece_args(SOUND[1], [r for r in want_sound if r[0] == 1]))
+    for lv, key in ((1, "refined_args"), (2, "exhaustive_args")):
+        assert st[key] >= (unit_args(SOUND_CUT[0], [r for r in want_sound if r[0] == 0], lv) +
+                           unit_args(SOUND[1], [r for r in want_sound if r[0] == 1], lv))

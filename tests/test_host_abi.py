@@ -154,6 +154,24 @@ def test_sound_piece_eps_not_below_the_oracle_bound(job):
     assert sj.eps3 < e2 < sj.eps1
 
 
+@pytest.mark.parametrize("job", SOUND_JOBS, ids=lambda j: f"f{j.func}e{j.e_in}p{j.p}N{j.log2_N}")
+def test_sound_line_eps_not_below_the_oracle_bound(job):
+    """The half-width of the phase-3 sub-pieces (and of any line length)
+    against the oracle's exact-rational bound; lengths outside 1..N refused."""
+    from oracle import sound
+    sj = tmd.sound_job(job)
+    N = 1 << job.log2_N
+    n2 = (N + 31) // 32
+    for length in sorted({1, (n2 + 31) // 32, n2, N}):
+        e = tmd.tmd_sound_line_eps(sj, length)
+        o = sound.min_eps_len(job, sj.eps3, length)
+        assert o <= e <= o * 1.01 + 64
+    assert tmd.tmd_sound_line_eps(sj, n2) == tmd.tmd_sound_piece_eps(sj)
+    for bad in (0, N + 1):
+        with pytest.raises(tmd.TmdError):
+            tmd.tmd_sound_line_eps(sj, bad)
+
+
 def test_sound_job_validation():
     job = tmd.sound_job(wl.toy_job())
     tmd.tmd_plan(job)                                   # accepted

@@ -110,11 +110,16 @@ def test_planted_exact_point_is_hard_to_round():
     assert sound.sound_candidates([job], [e3])[0][:3] == (0, 0, 0)
 
 
-@pytest.mark.parametrize("job", SMALL[:3] + [wl.plain_job(count_log2=30)], ids=lambda j: f"f{j.func}p{j.p}N{j.log2_N}")
-def test_piece_truncation_bound_holds(job):
-    """eps_trunc for the phase-2 pieces (N/32 arguments, a line from the two
-    values at the piece start) against the exact integer polynomial."""
+@pytest.mark.parametrize("level", [1, 2])
+@pytest.mark.parametrize("job", SMALL[:3] + [wl.plain_job(count_log2=30)] + BIG_BINADE[:1],
+                         ids=lambda j: f"f{j.func}e{j.e_in}p{j.p}N{j.log2_N}")
+def test_piece_truncation_bound_holds(job, level):
+    """eps_trunc for the phase-2 pieces (N/32 arguments) and for their 32
+    sub-pieces (level 2: ceil(N/32/32) arguments), a line from the two values
+    at the start, against the exact integer polynomial."""
     n2 = sound.piece_length(job)
+    if level == 2:
+        n2 = (n2 + 31) // 32
     et = sound.eps_trunc(job, n2)
     W = 64 * job.limbs
     mod = 1 << W
@@ -134,4 +139,4 @@ def test_piece_truncation_bound_holds(job):
                 worst = max(worst, Fraction(abs(diff), mod))
     assert worst <= et
     e1, e3 = sound.min_eps(job)
-    assert e3 < sound.min_eps2(job, e3) < e1
+    assert e3 < sound.min_eps_len(job, e3, n2) <= sound.min_eps2(job, e3) < e1

@@ -72,8 +72,10 @@ typedef enum { TMD_EXP = 0, TMD_EXP2 = 1, TMD_LOG = 2 } tmd_func;
                                its 32 pieces tested with their own lines against
                                eps2 (tmd_sound_piece_eps), and each failing piece has
                                its block polynomial R_t evaluated at every argument
-                               (tabulated differences of step 32 from the stored Taylor
-                               coefficients); every argument with
+                               (pieces of more than 64 arguments after one more cut
+                               into 32 sub-pieces tested against tmd_sound_line_eps;
+                               shorter ones by tabulated differences of step 32 from
+                               the stored Taylor coefficients); every argument with
                                (top64(R_t(y)) + eps3) mod 2^64 < 2 eps3 is reported
                                (record value = that quantity).  With eps1, eps3 from
                                tmd_sound_eps (or any larger values) every argument

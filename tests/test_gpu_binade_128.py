@@ -158,3 +158,24 @@ def test_sound_batched_with_literal_jobs(ctx):
     for lv, key in ((1, "refined_args"), (2, "exhaustive_args")):
         assert st[key] >= (unit_args(SOUND_CUT[0], [r for r in want_sound if r[0] == 0], lv) +
                            unit_args(SOUND[1], [r for r in want_sound if r[0] == 1], lv))
+
+
+def test_allocation_free_entry_equals_oracle():
+    """The allocation-free entry (host-computed tables, anchored on the
+    job's first block within one output binade) on [128, 256): a literal
+    slice across the cut at 260 ln 2 and a sound slice across X = 200."""
+    import numpy as np
+    jobs = [LITERAL[0], tmd.sound_job(SOUND_CUT[1])]
+    want = sorted(oc.job_candidates(jobs[0], 0) +
+                  [(1,) + r[1:] for r in sound.sound_candidates([jobs[1]], [jobs[1].eps3])],
+                  key=lambda r: (r[0], r[2], r[3]))
+    d_cand, d_count = tmd.alloc_candidates(1 << 14)
+    tmd.tmd_search_static(jobs, d_cand, d_count)
+    torch.cuda.synchronize()
+    n = int(d_count.cpu().item())
+    raw = d_cand[: n * tmd.CANDIDATE_BYTES].cpu().numpy()
+    rec = np.frombuffer(raw.tobytes(), dtype=np.dtype([("job", "<u4"), ("subint", "<u4"),
+                                                      ("arg", "<u8"), ("value", "<u8")]))
+    got = sorted(((int(r["job"]), int(r["subint"]), int(r["arg"]), int(r["value"])) for r in rec),
+                 key=lambda r: (r[0], r[2], r[3]))
+    assert n == len(want) and got == want

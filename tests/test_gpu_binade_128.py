@@ -179,3 +179,37 @@ def test_allocation_free_entry_equals_oracle():
     got = sorted(((int(r["job"]), int(r["subint"]), int(r["arg"]), int(r["value"])) for r in rec),
                  key=lambda r: (r[0], r[2], r[3]))
     assert n == len(want) and got == want
+
+
+def test_full_size_sound_slice_sampled(ctx):
+    """The benchmark's [128, 256) workload at full size in its launch form
+    (2^36 arguments, sound (53, 2^-32), N = 2^16, one batched replay):
+    every reported value is the oracle's (top64(R_t(y)) + eps3) mod 2^64 at
+    that argument, and on whole Taylor blocks (2^20 arguments each: those of
+    the first and last records and a seeded one) the records are exactly the
+    oracle's list."""
+    import random
+    from oracle import poly
+    start = random.Random(128256).randrange(0, (1 << 52) - (1 << 36), 1 << 20)
+    job = tmd.sound_job(wl.Job(wl.FUNC_EXP, 8, 53, 32, 16, 3, 20, 3, start, 1 << 36))
+    d_cand, d_count = tmd.alloc_candidates(1 << 16)
+    b = tmd.Batch(ctx, [job], d_cand, d_count)
+    b.launch()
+    got, n = tmd.tmd_candidates(ctx, d_cand, d_count)
+    b.close()
+    assert n == len(got) and 10 <= n <= 200
+    T = 1 << job.log2_T
+    W = 64 * job.limbs
+    for r in got:
+        b0 = r[2] - (r[2] - start) % T
+        # e_out from the oracle's own exponent of f at the block start
+        blk = plan.Block(b0, T, plan.e_out_at(job, b0), 0)
+        c = poly.taylor_coeffs(job, blk)
+        top = poly.horner(c, r[2] - blk.start, W) >> (W - 64)
+        assert (top + job.eps3) % (1 << 64) == r[3] < 2 * job.eps3
+    picks = {(got[0][2] - start) // T, (got[-1][2] - start) // T, random.Random(7).randrange(1 << 16)}
+    for bi in sorted(picks):
+        sub = job.replace(start=start + bi * T, count=T)
+        want = sound.sound_candidates([sub], [job.eps3])
+        got_b = [(0, r[2]) for r in got if start + bi * T <= r[2] < start + (bi + 1) * T]
+        assert got_b == [(0, w[2]) for w in want]

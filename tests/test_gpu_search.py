@@ -262,3 +262,49 @@ def test_bad_lengths_reported(ctx):
     tmd.tmd_search_lines(ctx, B, B, n, 20, 0, d_cand, d_count)
     with pytest.raises(tmd.TmdError):
         tmd.tmd_candidates(ctx, d_cand, d_count)
+
+
+def narrow_lines(w, ns):
+    """Every (A, B) of w-bit words at each length in ns, placed at the top of
+    the 64-bit words: (B 2^s - A 2^s x) mod 2^64 = 2^s ((B - A x) mod 2^w)
+    with s = 64 - w, so the 64-bit kernels run w-bit arithmetic exactly."""
+    s = 64 - w
+    return [(b << s, a << s, n) for a in range(1 << w) for b in range(1 << w) for n in ns]
+
+
+def test_exhaustive_narrow_words(ctx):
+    """All 8-bit (A, B) at seven lengths (every rational slope, tie and
+    degenerate ending of that width): the Algorithm 4 bound and half-step
+    count equal the oracle's line by line and never exceed the brute-force
+    minimum, and the search's records (minimum below 2^63) are brute
+    force's, smallest argmin included."""
+    import numpy as np
+    lines = narrow_lines(8, [1, 2, 3, 16, 100, 256, 1000])
+    lb, hs = run_lower_bounds(ctx, lines)
+    mins, _ = oc.brute_min_many(np.array([l[0] for l in lines], dtype=np.uint64),
+                                np.array([l[1] for l in lines], dtype=np.uint64),
+                                np.array([l[2] for l in lines], dtype=np.uint32))
+    for (B, A, n), g, h, mn in zip(lines, lb, hs, mins):
+        want, _, whs = search.regular_lb_unrolled(B, A, n)
+        assert (g, h) == (want, whs), (hex(B), hex(A), n)
+        assert g <= int(mn)
+    d_cand, d_count = tmd.alloc_candidates(len(lines) + 16)
+    tmd.tmd_search_lines(ctx, u64_tensor([l[0] for l in lines]), u64_tensor([l[1] for l in lines]),
+                         u32_tensor([l[2] for l in lines]), 2, 0, d_cand, d_count)
+    got, count = tmd.tmd_candidates(ctx, d_cand, d_count)
+    want = brute_records(lines, 2)
+    assert count == len(want) > 100000
+    assert sort_by_line(got) == sort_by_line(want)
+
+
+def test_exhaustive_narrow_words_all_hits(ctx):
+    """All 6-bit (A, B) at three lengths, every argument below 2^61
+    reported (all-hits mode) against brute force."""
+    lines = narrow_lines(6, [1, 7, 64])
+    d_cand, d_count = tmd.alloc_candidates(1 << 19)
+    tmd.tmd_search_lines(ctx, u64_tensor([l[0] for l in lines]), u64_tensor([l[1] for l in lines]),
+                         u32_tensor([l[2] for l in lines]), 4, tmd.TMD_ALL_HITS, d_cand, d_count)
+    got, count = tmd.tmd_candidates(ctx, d_cand, d_count)
+    want = brute_records(lines, 4, all_hits=True)
+    assert count == len(want) > 10000
+    assert sort_by_line(got) == sort_by_line(want)

@@ -19,6 +19,13 @@ Algorithm 4 filter, exact resolution and compaction over all 2^22 lines.
            planning and correctly rounded table kernels, the search kernel,
            the device->host read of the count and records.
 
+Further sections of the same line (each skippable by its flag): Lefevre's
+filter on the same slice (Table 4's comparison), the sound mode on Table 2's
+domain (exp on [1, 1+2^-13[, 2^39 arguments), the sound mode on exp's binade
+[128, 256) with both filters and the phase counts of Table 7, a 64-job
+mixed batch against per-job launches, the large 2^16-job batch, and a
+Poisson-arrival serving stream.
+
 Between timed steps a 256 MiB buffer (> the 129 MB L2) is written so that no
 step starts with a warm L2.  `--impl reference` times the CPU oracle instead
 (exact enclosures, direct Horner, brute force over every argument) on a

@@ -81,9 +81,9 @@ typedef enum { TMD_EXP = 0, TMD_EXP2 = 1, TMD_LOG = 2 } tmd_func;
                                tmd_sound_eps (or any larger values) every argument
                                whose s f(X) lies within 2^-m of a breakpoint is
                                reported: the list to re-check exactly (Ziv).  Not
-                               with TMD_ALL_HITS; fused and batched forms, the server
-                               and the allocation-free entry (not the unfused
-                               tmd_generate + tmd_search pair).                      */
+                               with TMD_ALL_HITS; every form (fused, unfused
+                               tmd_generate + tmd_search pair, batched, server,
+                               allocation-free entry).                               */
 #define TMD_LEFEVRE 4u      /* filter with Lefevre's lower bound (Algorithm 3, the swap
                                form of Algorithm 1, with his specific instructions,
                                see tmd_lefevre_bounds) instead of the regular one
@@ -262,8 +262,9 @@ tmd_status tmd_generate(tmd_ctx* ctx, const tmd_job* jobs, uint32_t njobs,
 /* Stage 2: search.  With d_lin != NULL, the lines written by tmd_generate
  * for the same jobs are searched (one line per lane, Algorithm 4 or
  * Algorithm 3 filter, exact minimum of the flagged lines, warp-ballot
- * compaction; sound jobs are not accepted here: TMD_EUNSUPPORTED).  With
- * d_lin == NULL the fused
+ * compaction; sound jobs continue with phases 2 and 3 from the resident
+ * block tables, the lanes of one job at a time).  With d_lin == NULL the
+ * fused
  * kernel regenerates the lines in registers from the resident tables
  * (planning them first if these jobs are not the resident ones).
  * Records go to d_cand[0 .. cand_cap), unordered; *d_count (device uint64)

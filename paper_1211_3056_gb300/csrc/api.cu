@@ -599,9 +599,6 @@ tmd_status tmd_generate(tmd_ctx* c, const tmd_job* jobs, uint32_t njobs, void* d
 tmd_status tmd_search(tmd_ctx* c, const tmd_job* jobs, uint32_t njobs, const void* d_lin,
                       tmd_candidate* d_cand, uint64_t cand_cap, uint64_t* d_count, void* stream) {
     if (!c || !jobs || njobs == 0 || !d_count || (cand_cap && !d_cand)) return TMD_EINVAL;
-    if (d_lin)  // the exhaustive phase of sound mode needs the fused kernels' block state
-        for (uint32_t j = 0; j < njobs; j++)
-            if (jobs[j].flags & TMD_SOUND) return TMD_EUNSUPPORTED;
     cudaStream_t s = (cudaStream_t)stream;
     CK(cudaSetDevice(c->device));
     tmd_status st = make_resident(c, jobs, njobs, s);
@@ -618,6 +615,7 @@ tmd_status tmd_search(tmd_ctx* c, const tmd_job* jobs, uint32_t njobs, const voi
         a.jobs = (const DevJob*)(c->d_arena + c->off_jobs);
         a.n_jobs = (uint32_t)c->plan.jobs.size();
         a.blocks = (const DevBlock*)(c->d_arena + c->off_blocks);
+        a.tables = (const uint64_t*)(c->d_arena + c->off_tables);
         a.cand = d_cand;
         a.cap = cand_cap;
         a.count = d_count;

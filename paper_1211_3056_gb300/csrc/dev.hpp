@@ -105,6 +105,7 @@ struct LineArgs {
     const DevJob* jobs;       // JOBS only
     uint32_t n_jobs;
     const DevBlock* blocks;
+    const uint64_t* tables;   // JOBS only: the block tables (sound jobs' phases 2 and 3)
     tmd_candidate* cand;
     uint64_t cap;
     uint64_t* count;

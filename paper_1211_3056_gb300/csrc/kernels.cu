@@ -985,9 +985,30 @@ __global__ void __launch_bounds__(256, 3) k_persistent(LaunchArgs a) {
     flush_stats(a.stats, sl, sf, sh);
 }
 
+// Sound jobs in the line search: phases 2 and 3 (sound_exhaustive) for the
+// lanes of one job at a time, so that the job record and its (limbs,
+// degree) instantiation are uniform across the warp.
+__device__ __noinline__ void sound_lines(bool fail, uint64_t B, uint64_t A, uint32_t n, uint64_t table_off,
+                                         uint32_t i, uint32_t sub, uint64_t arg_base, uint32_t job,
+                                         const DevJob& jb, const LaunchArgs& la) {
+    switch (jb.L * 8 + jb.d) {
+#define TMD_SOUND_CASE(L, D)                                                                     \
+    case L * 8 + D:                                                                              \
+        sound_exhaustive<L, D>(fail, B, A, n, table_off, i, sub, arg_base, job, jb, la);          \
+        break;
+        TMD_SOUND_CASE(1, 1) TMD_SOUND_CASE(1, 2) TMD_SOUND_CASE(1, 3) TMD_SOUND_CASE(1, 4)
+        TMD_SOUND_CASE(2, 1) TMD_SOUND_CASE(2, 2) TMD_SOUND_CASE(2, 3) TMD_SOUND_CASE(2, 4)
+        TMD_SOUND_CASE(3, 1) TMD_SOUND_CASE(3, 2) TMD_SOUND_CASE(3, 3) TMD_SOUND_CASE(3, 4)
+#undef TMD_SOUND_CASE
+        default:
+            break;
+    }
+}
+
 // Line search.  JOBS: the lines written by k_generate for the resident plan
-// (line index -> job -> block by binary search).  RAW: caller arrays with
-// per-line lengths; record = (0, line, x, value).
+// (line index -> job -> block by binary search; sound jobs continue with
+// phases 2 and 3 from the block tables).  RAW: caller arrays with per-line
+// lengths; record = (0, line, x, value).
 
 template <bool RAW>
 __global__ void __launch_bounds__(256) k_search_lines(LineArgs a) {
@@ -995,8 +1016,8 @@ __global__ void __launch_bounds__(256) k_search_lines(LineArgs a) {
     const uint64_t s = (w << 5) + (threadIdx.x & 31);
     if ((w << 5) >= a.n_lines) return;  // whole warp
     const bool valid = s < a.n_lines;
-    uint64_t B = 0, A = 0, Tm = a.Tm, arg_base = 0;
-    uint32_t n = 1, job = 0, sub = 0, flags = a.flags;
+    uint64_t B = 0, A = 0, Tm = a.Tm, arg_base = 0, table_off = 0;
+    uint32_t n = 1, job = 0, sub = 0, flags = a.flags, iblk = 0;
     if (valid) {
         B = a.B[s];
         A = a.A[s];
@@ -1030,16 +1051,42 @@ __global__ void __launch_bounds__(256) k_search_lines(LineArgs a) {
             n = (uint32_t)min(N, bk.length - i * N);
             sub = (uint32_t)js;
             arg_base = bk.start + i * N;
+            table_off = bk.table_off;
+            iblk = (uint32_t)i;
         }
     }
     uint32_t hs = 0;
     uint64_t lb = ~0ull;
     if (valid) lb = (flags & TMD_LEFEVRE) ? lefevre_lower_bound<true>(B, A, n, &hs) : cf_lower_bound(B, A, n, &hs);
     const bool fail = valid && lb < Tm;
+    const bool sound = !RAW && valid && (flags & TMD_SOUND);
     // all lanes of a warp share ALL_HITS in practice; take the warp's OR
     const bool all_hits = __any_sync(FULLMASK, valid && (flags & TMD_ALL_HITS));
-    if (__any_sync(FULLMASK, fail))
-        resolve_and_emit(fail, B, A, n, Tm, all_hits, job, sub, arg_base, a.cand, a.cap, a.count);
+    if (__any_sync(FULLMASK, fail && !sound))
+        resolve_and_emit(fail && !sound, B, A, n, Tm, all_hits, job, sub, arg_base, a.cand, a.cap, a.count);
+    if (!RAW) {
+        unsigned todo = __ballot_sync(FULLMASK, sound && fail);
+        if (todo) {
+            LaunchArgs la;
+            la.jobs = a.jobs;
+            la.blocks = a.blocks;
+            la.tables = a.tables;
+            la.tasks = nullptr;
+            la.n_tasks = 0;
+            la.lin_B = la.lin_A = nullptr;
+            la.cand = a.cand;
+            la.cap = a.cap;
+            la.count = a.count;
+            la.stats = a.stats;
+            la.queue_head = nullptr;
+            while (todo) {
+                const uint32_t jl = __shfl_sync(FULLMASK, job, __ffs(todo) - 1);
+                const bool mine = sound && fail && job == jl;
+                todo &= ~__ballot_sync(FULLMASK, mine);
+                sound_lines(mine, B, A, n, table_off, iblk, sub, arg_base, jl, a.jobs[jl], la);
+            }
+        }
+    }
     flush_stats(a.stats, valid ? 1u : 0u, fail ? 1u : 0u, hs);
 }
 

@@ -8,7 +8,8 @@ nearly every line.  Through the C ABI:
     batched, across an output-binade cut, for exp and 2^x, up to the last
     binade [256, 512) below binary64's overflow of exp;
   * the sound mode reports exactly the oracle's Horner list, with the
-    regular and with Lefevre's filter, in the fused and batched forms;
+    regular and with Lefevre's filter, in the fused, unfused and batched
+    forms;
   * the counters show the heavy-failure regime (every line of a mid-binade
     slice fails the first filter), and the argument counts of phase 3's
     input and of its one-by-one evaluation cover every piece and sub-piece
@@ -109,15 +110,16 @@ def check_phase_counts(st, job, records):
     assert unit_args(job, records, 2) <= st["exhaustive_args"] <= st["refined_args"]
 
 
+@pytest.mark.parametrize("fused", [True, False], ids=["fused", "unfused"])
 @pytest.mark.parametrize("lefevre", [False, True], ids=["regular", "lefevre"])
 @pytest.mark.parametrize("job", SOUND, ids=lambda j: f"f{j.func}e{j.e_in}")
-def test_sound_heavy_failure_equals_oracle(ctx, job, lefevre):
+def test_sound_heavy_failure_equals_oracle(ctx, job, lefevre, fused):
     sj = tmd.sound_job(job.replace(flags=job.flags | (wl.FLAG_LEFEVRE if lefevre else 0)))
     # the regime: the first filter's threshold exceeds 1/(2N) of the unit
     assert sj.eps1 * 2 * (1 << job.log2_N) > 1 << 64
     want = sound.sound_candidates([sj], [sj.eps3])
     assert len(want) > 20
-    got, n = tmd.run([sj], ctx=ctx, fused=True, cap=1 << 18)
+    got, n = tmd.run([sj], ctx=ctx, fused=fused, cap=1 << 18)
     assert n == len(want) and got == want
     st = tmd.tmd_stats_read(ctx)
     assert st["filter_fail"] >= 0.99 * st["lines"]

@@ -1,7 +1,7 @@
 """GPU parity of the sound mode (Sect. II-A's eps'' filter, then Sect.
 III-A's exhaustive phase) through the C ABI: the reported arguments and
-values equal the oracle's Horner definition exactly, in the fused, batched
-and allocation-free forms, every argument decided hard-to-round from the
+values equal the oracle's Horner definition exactly, in the fused, unfused,
+batched and allocation-free forms, every argument decided hard-to-round from the
 exact function is among them, and Table 2's count of (53, 2^-32)
 hard-to-round cases of exp on [1, 1+2^-13[ is compared with the exact
 decision of every listed argument."""
@@ -90,15 +90,19 @@ def test_sound_list_holds_every_hard_to_round_argument(ctx):
     assert len(hr) > 10 and set(hr) <= listed
 
 
-def test_sound_rejected_by_the_unfused_pair(ctx):
-    job = tmd.sound_job(SMALL[0])
-    need = tmd.tmd_generate(ctx, [job], None)
-    d_lin = torch.empty(need // 8, dtype=torch.int64, device="cuda:0")
-    tmd.tmd_generate(ctx, [job], d_lin)
-    d_cand, d_count = tmd.alloc_candidates(16)
-    with pytest.raises(tmd.TmdError) as e:
-        tmd.tmd_search(ctx, [job], d_lin, d_cand, d_count)
-    assert e.value.status == tmd._lib.TMD_EUNSUPPORTED
+def test_sound_unfused_pair_equals_oracle(ctx):
+    """tmd_generate writes the lines, tmd_search searches them: sound jobs of
+    different (limbs, degree) next to an ordinary job, so that warps of the
+    line search straddle jobs, give the oracle's lists."""
+    jobs = [tmd.sound_job(SMALL[0]), SMALL[2], tmd.sound_job(SMALL[3]), tmd.sound_job(SMALL[1]),
+            tmd.sound_job(SMALL[4])]
+    got, n = tmd.run(jobs, ctx=ctx, fused=False, cap=1 << 18)
+    from oracle import candidates as oc
+    sound_idx = [0, 2, 3, 4]
+    want_sound = oracle_list([jobs[i] for i in sound_idx])
+    want = sorted([(sound_idx[r[0]],) + r[1:] for r in want_sound] + oc.job_candidates(jobs[1], 1),
+                  key=lambda r: (r[0], r[2], r[3]))
+    assert n == len(want) and got == want
 
 
 def test_table2_hard_to_round_cases_of_exp(ctx):

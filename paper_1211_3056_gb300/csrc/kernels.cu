@@ -14,8 +14,9 @@
 //               warp ballot with one atomic per warp (Sect. III-C
 //               compaction of failing sub-domains).  Lefevre's filter
 //               (Algorithm 3) and the sound mode (eps'' filter, phase-2
-//               pieces, phase-3 exhaustive evaluation) live in the general
-//               kernel variant only.
+//               pieces, phase 3 with its sub-pieces and the evaluation of
+//               R_t at every argument of the failing ones) live in the
+//               general kernel variant and in the line search only.
 //
 // Quotients: GB300 has no integer divide instruction and a slow FP64 unit,
 // so floor(a/b) comes from an FP32 estimate built from 32-bit halves

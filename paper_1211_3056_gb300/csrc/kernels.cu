@@ -861,7 +861,8 @@ struct LineStage {
 // Lefevre's filter or the sound mode.
 template <int L, int D, bool G>
 __device__ __forceinline__ void fused_task(const DevTask& t, const LaunchArgs& a, LineStage& st,
-                                           uint32_t& st_lines, uint32_t& st_fail, uint32_t& st_half) {
+                                           uint32_t& st_lines, uint32_t& st_fail, uint32_t& st_half,
+                                           uint16_t* fl) {
     const int lane = threadIdx.x & 31;
     const uint32_t nu = a.jobs[t.job].nu;
     {
@@ -887,6 +888,7 @@ __device__ __forceinline__ void fused_task(const DevTask& t, const LaunchArgs& a
     __syncwarp();
     const uint64_t Tm = a.jobs[t.job].Tm;
     const bool lefevre = G && (a.jobs[t.job].flags & TMD_LEFEVRE) != 0;
+    uint32_t nfail = 0;  // general variant: failing lines listed in fl (warp-uniform)
 #pragma unroll 1
     for (uint32_t r = 0; r < nu; r++) {
         const int s = (int)r * 32 + lane;
@@ -901,18 +903,45 @@ __device__ __forceinline__ void fused_task(const DevTask& t, const LaunchArgs& a
         st_lines += n ? 1u : 0u;
         st_fail += fail ? 1u : 0u;
         st_half += hs;
-        if (__any_sync(FULLMASK, fail)) {
+        if (G) {
+            // general variant: the failing lines of the task are listed and
+            // resolved 32 at a time below (one lane each), not round by round
+            // with a few active lanes
+            const unsigned fm = __ballot_sync(FULLMASK, fail);
+            if (fail) fl[nfail + (uint32_t)__popc(fm & ((1u << lane) - 1u))] = (uint16_t)s;
+            nfail += (uint32_t)__popc(fm);
+        } else if (__any_sync(FULLMASK, fail)) {
             const uint32_t pk = (uint32_t)s / nu;
             const uint32_t i = st.i0[pk] + (uint32_t)s % nu;
             const DevBlock& bk = a.blocks[st.blk[pk]];
             const DevJob& jb = a.jobs[t.job];
-            if (G && (jb.flags & TMD_SOUND))
-                sound_exhaustive<L, D>(fail, B, A, n ? n : 1u, bk.table_off, i, (uint32_t)(bk.first_sub + i),
+            resolve_and_emit(fail, B, A, n ? n : 1u, Tm, (jb.flags & TMD_ALL_HITS) != 0, t.job,
+                             (uint32_t)(bk.first_sub + i), bk.start + ((uint64_t)i << jb.log2_N), a.cand,
+                             a.cap, a.count);
+        }
+    }
+    if (G && nfail) {
+        __syncwarp();
+        const DevJob& jb = a.jobs[t.job];
+        const bool all_hits = (jb.flags & TMD_ALL_HITS) != 0;
+#pragma unroll 1
+        for (uint32_t base = 0; base < nfail; base += 32) {
+            const uint32_t k = base + (uint32_t)lane;
+            const bool act = k < nfail;
+            const int s = act ? (int)fl[k] : 0;
+            const int slot = stage_slot(s);
+            const uint32_t n = act ? st.n[slot] : 1u;
+            const uint64_t B = st.B[slot];
+            const uint64_t A = st.A[slot];
+            const uint32_t pk = (uint32_t)s / nu;
+            const uint32_t i = st.i0[pk] + (uint32_t)s % nu;
+            const DevBlock& bk = a.blocks[st.blk[pk]];
+            if (jb.flags & TMD_SOUND)
+                sound_exhaustive<L, D>(act, B, A, n, bk.table_off, i, (uint32_t)(bk.first_sub + i),
                                        bk.start + ((uint64_t)i << jb.log2_N), t.job, jb, a);
             else
-                resolve_and_emit(fail, B, A, n ? n : 1u, Tm, (jb.flags & TMD_ALL_HITS) != 0, t.job,
-                                 (uint32_t)(bk.first_sub + i), bk.start + ((uint64_t)i << jb.log2_N),
-                                 a.cand, a.cap, a.count);
+                resolve_and_emit(act, B, A, n, Tm, all_hits, t.job, (uint32_t)(bk.first_sub + i),
+                                 bk.start + ((uint64_t)i << jb.log2_N), a.cand, a.cap, a.count);
         }
     }
     __syncwarp();
@@ -949,11 +978,12 @@ constexpr int FUSED_WARPS_PER_CTA = 4;
 template <int L, int D, bool G>
 __global__ void __launch_bounds__(128, 6) k_fused(LaunchArgs a) {
     __shared__ LineStage stage[FUSED_WARPS_PER_CTA];
+    __shared__ uint16_t fails[G ? FUSED_WARPS_PER_CTA * TASK_LINES : 1];
     const uint64_t w = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     if (w >= a.n_tasks) return;  // whole warp
     uint32_t sl = 0, sf = 0, sh = 0;
     const DevTask t = a.tasks[w];
-    fused_task<L, D, G>(t, a, stage[threadIdx.x >> 5], sl, sf, sh);
+    fused_task<L, D, G>(t, a, stage[threadIdx.x >> 5], sl, sf, sh, fails + (G ? (threadIdx.x >> 5) * TASK_LINES : 0));
     flush_stats(a.stats, sl, sf, sh);
 }
 
@@ -972,6 +1002,7 @@ __global__ void __launch_bounds__(256) k_generate(LaunchArgs a) {
 template <int L, int D, bool G>
 __global__ void __launch_bounds__(256, 3) k_persistent(LaunchArgs a) {
     __shared__ LineStage stage[WARPS_PER_CTA];
+    __shared__ uint16_t fails[G ? WARPS_PER_CTA * TASK_LINES : 1];
     LineStage& stg = stage[threadIdx.x >> 5];
     const int lane = threadIdx.x & 31;
     uint32_t sl = 0, sf = 0, sh = 0;
@@ -981,7 +1012,7 @@ __global__ void __launch_bounds__(256, 3) k_persistent(LaunchArgs a) {
         t = __shfl_sync(FULLMASK, t, 0);
         if ((uint64_t)t >= a.n_tasks) break;
         const DevTask task = a.tasks[t];
-        fused_task<L, D, G>(task, a, stg, sl, sf, sh);
+        fused_task<L, D, G>(task, a, stg, sl, sf, sh, fails + (G ? (threadIdx.x >> 5) * TASK_LINES : 0));
     }
     flush_stats(a.stats, sl, sf, sh);
 }

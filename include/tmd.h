@@ -96,7 +96,8 @@ typedef enum { TMD_EXP = 0, TMD_EXP2 = 1, TMD_LOG = 2 } tmd_func;
  * Supported here: exp and 2^x with -16 <= e_in <= 9 (up to [256, 512), the
  * last binade of exp below binary64's overflow; above [2, 4) the block
  * coefficients are range-reduced by the output exponent), log with
- * 2 <= e_in <= 16, 8 <= p <= 60, p - e_in >= 8, 2 <= m <= 63,
+ * 2 <= e_in <= 16, 8 <= p <= 60, p - e_in >= 1 (>= 8 above [2, 4) for exp
+ * and 2^x), 2 <= m <= 63,
  * 1 <= log2_N <= 16, log2_N <= log2_T <= 40, 1 <= d <= 4, 1 <= limbs <= 3,
  * count >= 1, start + count <= 2^(p-1), at most 4 output binades per job. */
 typedef struct {

@@ -408,7 +408,10 @@ tmd_status validate_job(const tmd_job& job) {
         // up to [256, 512): the last binade of exp below binary64's overflow
         if (job.e_in < -16 || job.e_in > 9) return TMD_EUNSUPPORTED;
     }
-    if (job.p - job.e_in < 8) return TMD_EUNSUPPORTED;
+    // arguments X = M 2^-(p - e_in) with a positive shift; the range-reduced
+    // binades (exp, 2^x above [2, 4)) keep at least 8 fractional bits
+    if (job.p - job.e_in < 1) return TMD_EUNSUPPORTED;
+    if (job.func != TMD_LOG && job.e_in > 2 && job.p - job.e_in < 8) return TMD_EUNSUPPORTED;
     uint64_t span = 1ull << (job.p - 1);
     if (job.count == 0 || job.start >= span || job.count > span - job.start) return TMD_EINVAL;
     // the sub-interval numbering of a job must fit 32 bits

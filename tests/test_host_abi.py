@@ -114,6 +114,21 @@ def test_validation(field, value, status):
     assert e.value.status == status
 
 
+@pytest.mark.parametrize("job,ok", [
+    (wl.Job(wl.FUNC_LOG, 16, 12, 4, 2, 2, 4, 1, 0, 1 << 8), False),      # p - e_in < 1
+    (wl.Job(wl.FUNC_EXP, 8, 15, 4, 2, 2, 4, 1, 0, 1 << 8), False),       # reduced binade, q < 8
+    (wl.Job(wl.FUNC_EXP, 1, 8, 4, 2, 2, 4, 1, 0, 1 << 6), True),         # q = 7 on [1, 2)
+    (wl.Job(wl.FUNC_EXP2, 8, 16, 4, 2, 2, 4, 1, 0, 1 << 8), True),       # q = 8 on [128, 256)
+])
+def test_argument_shift_limits(job, ok):
+    if ok:
+        tmd.tmd_plan(job)
+    else:
+        with pytest.raises(tmd.TmdError) as e:
+            tmd.tmd_plan(job)
+        assert e.value.status == tmd._lib.TMD_EUNSUPPORTED
+
+
 def test_log_binade_near_one_rejected():
     job = wl.Job(wl.FUNC_LOG, 1, 53, 40, 14, 3, 24, 3, 0, 1 << 30)
     with pytest.raises(tmd.TmdError):

@@ -71,6 +71,16 @@ struct Plan {
 
 size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 
+// Kernel variant of a job: the general one for Lefevre's filter, the sound
+// mode, and literal thresholds dense enough that a line fails the filter
+// often (2^(65-m) N >= 2^57, about one line in 2^7 holding a value below the
+// threshold): the general variant resolves a task's failing lines 32 at a
+// time instead of round by round.  The plain variant keeps the sparse
+// thresholds, where a line fails one time in 10^5 or less.
+bool general_variant(uint32_t flags, int m, uint32_t log2_N) {
+    return (flags & (TMD_LEFEVRE | TMD_SOUND)) != 0 || 65 - m + (int)log2_N >= 57;
+}
+
 }  // namespace
 
 struct tmd_ctx {
@@ -279,7 +289,7 @@ tmd_status build_plan(const tmd_job* jobs, uint32_t njobs, Plan& P, bool host_ta
         uint32_t Lk = 0, Dk = 0;
         for (uint32_t j = 0; j < njobs; j++) {
             const DevJob& dj = P.jobs[j];
-            const uint32_t g = (dj.flags & (TMD_LEFEVRE | TMD_SOUND)) ? 1u : 0u;
+            const uint32_t g = general_variant(dj.flags, (int)dj.m, dj.log2_N) ? 1u : 0u;
             if ((dj.L * 8 + dj.d) * 2 + g != key) continue;
             P.class_jobs.push_back(j);
             P.class_task0.push_back(task);
@@ -825,7 +835,8 @@ tmd_status tmd_autotune(tmd_ctx* c, const tmd_job* jobs, uint32_t njobs, void* s
     for (uint32_t j = 0; j < njobs; j++) {
         int per_sm = 0;
         if (jobs[j].limbs >= 1 && jobs[j].limbs <= 3 && jobs[j].d >= 1 && jobs[j].d <= 4 &&
-            persistent_occupancy(jobs[j].limbs, (uint32_t)jobs[j].d, (jobs[j].flags & (TMD_LEFEVRE | TMD_SOUND)) != 0,
+            persistent_occupancy(jobs[j].limbs, (uint32_t)jobs[j].d,
+                                 general_variant(jobs[j].flags, jobs[j].m, jobs[j].log2_N),
                                  &per_sm) == cudaSuccess)
             occ = std::max(occ, per_sm);
     }

@@ -467,7 +467,19 @@ def main():
                      "form": "batched: filter at eps1, exact line minimum, 32 refined pieces per failing "
                              "line at eps2 (phase 2); phase 3 on the failing pieces: 32 sub-pieces each "
                              "tested against their own half-width, Horner at every argument of the failing ones"}
+        recs_s = tmd.tmd_candidates(ctx, d_cand_s, d_count_s)
         sb.close()
+        # the same job with Lefevre's filter (Table 6's comparison of the two
+        # searches' phase shares on a binade where exp is nearly linear)
+        sjl = sjob.replace(flags=sjob.flags | wl.FLAG_LEFEVRE)
+        sbl = tmd.Batch(ctx, [sjl], d_cand_s, d_count_s)
+        sl_ms = max_over_ranks(statistics.mean(timed(sbl.launch, 10, 3)))
+        stl = sbl.stats()
+        assert tmd.tmd_candidates(ctx, d_cand_s, d_count_s) == recs_s, "the two filters must give the same records"
+        sbl.close()
+        sound_run["lefevre"] = {"value": sjob.count / (sl_ms / 1e3), "ms_per_step": sl_ms,
+                                "filter_fail_per_line": stl["filter_fail"] / max(1, stl["lines"]),
+                                "phase3_args": stl["refined_args"], "one_by_one_args": stl["exhaustive_args"]}
 
     # Table 7's second binade: exp on [128, 256), where the degree-1 lines'
     # truncation error is far above eps: a 2^36-argument slice at a seeded

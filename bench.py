@@ -23,8 +23,9 @@ Further sections of the same line (each skippable by its flag): Lefevre's
 filter on the same slice (Table 4's comparison), the sound mode on Table 2's
 domain (exp on [1, 1+2^-13[, 2^39 arguments), the sound mode on exp's binade
 [128, 256) with both filters and the phase counts of Table 7, a 64-job
-mixed batch against per-job launches, the large 2^16-job batch, and a
-Poisson-arrival serving stream.
+mixed batch against per-job launches, the large 2^16-job batch, a
+Poisson-arrival serving stream, and the whole binade [1, 2) of exp in sound
+mode through the public API (Table 4's workload).
 
 Between timed steps a 256 MiB buffer (> the 129 MB L2) is written so that no
 step starts with a warm L2.  `--impl reference` times the CPU oracle instead
@@ -288,6 +289,10 @@ def main():
                     help="also time the sound search of exp on [128, 256), Table 7's regime (0 = skip)")
     ap.add_argument("--binade128-log2", type=int, default=36,
                     help="arguments of the [128, 256) slice (smaller only for profiling captures)")
+    ap.add_argument("--binade-full", type=int, default=1,
+                    help="also search the whole binade [1, 2) of exp, Table 4's workload (0 = skip)")
+    ap.add_argument("--binade-full-chunks", type=int, default=1024,
+                    help="2^42-argument calls of the whole-binade run (1024 = all of [1, 2))")
     ap.add_argument("--tiling", default="auto",
                     help="'auto' (tmd_autotune picks it) or 'nu,ctas_per_sm' for the batched form")
     args = ap.parse_args()
@@ -520,6 +525,38 @@ def main():
                              "at eps2 (phase 2); phase 3 on the failing pieces: 32 sub-pieces each tested "
                              "against their own half-width, Horner at every argument of the failing ones")
 
+    # Table 4's workload: the whole binade [1, 2) of exp, 2^52 binary64
+    # arguments, sound (53, 2^-32) directed cases (Table 2's parameters), as
+    # 1024 calls of the public API on 2^42-argument slices: host job record
+    # in, plan, correctly rounded tables and fused search on the device,
+    # host records out, every call (wall clock around the whole loop)
+    binade_full = None
+    if args.binade_full and world == 1:
+        try:
+            d_cand_f, d_count_f = tmd.alloc_candidates(1 << 16, local_rank)
+            chunk_log2 = 42
+            n_chunks = min(args.binade_full_chunks, 1 << (52 - chunk_log2))
+            listed = 0
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            for c in range(n_chunks):
+                fj = tmd.sound_job(wl.Job(wl.FUNC_EXP, 1, 53, 32, 15, 3, 24, 3, c << chunk_log2,
+                                          1 << chunk_log2, wl.FLAG_BP_DIRECTED))
+                tmd.tmd_search(ctx, [fj], None, d_cand_f, d_count_f)
+                _, nf = tmd.tmd_candidates(ctx, d_cand_f, d_count_f)
+                listed += nf
+            secs = time.perf_counter() - t0
+            args_done = n_chunks << chunk_log2
+            binade_full = {"workload": f"exp binary64 [1, 2), {n_chunks} x 2^{chunk_log2} arguments "
+                                       f"({'the whole binade' if args_done == 1 << 52 else 'part of the binade'}), "
+                                       "sound (53, 2^-32) directed cases, d=3, W=192, N=2^15",
+                           "value": args_done / secs, "unit": UNIT, "seconds": secs,
+                           "listed_arguments": listed,
+                           "form": "one tmd_search + tmd_candidates call per slice from host job records "
+                                   "(plan, tables, fused search, records back), wall clock"}
+        except Exception as e:  # report, do not lose the rest of the line
+            binade_full = {"error": repr(e)}
+
     mixed = None
     if args.mixed_jobs > 0:
         mjobs = wl.batched_jobs(njobs=args.mixed_jobs)
@@ -609,6 +646,7 @@ def main():
             "roofline": roofline, "cpu_baseline": cpu, "clocks": clocks, "lefevre": lefevre,
             "sound_table2": sound_run,
             "binade_128_256": binade128,
+            "binade_1_2_whole": binade_full,
             "mixed_batch": mixed,
             "large_batch": large,
             "serving": serving,

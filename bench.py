@@ -60,7 +60,7 @@ UNIT = "args/s"
 SMS, LANES_PER_SM, SM_MAX_HZ = 152, 128, 2.070e9
 ISSUE_PEAK_OPS = SMS * LANES_PER_SM * SM_MAX_HZ
 
-# Algorithmic 32-bit operations (definitions in the design doc):
+# Algorithmic 32-bit operations (a fixed cost model of Algorithm 4):
 #   per line:       tabulated stepping (2d-1) W-bit adds = 2 (2d-1) L 32-bit
 #                   add-with-carry, plus 4 to form the search words;
 #   per half-step:  35 (divisor and dividend to FP32, reciprocal, two

@@ -39,6 +39,19 @@ struct CoeffJob {
 // arguments of the smaller binades keep their direct evaluation).
 TMD_HD int reduction_exponent(int func, int e_in, int e_out) { return (func != 2 && e_in > 2) ? e_out - 1 : 0; }
 
+// X = M 2^-q is an integer (any shift q: for q >= 64, 0 <= X < 1 since
+// M < 2^64, so only M = 0 is)
+TMD_HD bool integer_arg(uint64_t M, unsigned q) {
+    if (q >= 64) return M == 0;
+    return (M & ((1ull << q) - 1)) == 0;
+}
+
+// ceil(M 2^-q) for M > 0, any shift q
+TMD_HD uint64_t ceil_arg(uint64_t M, unsigned q) {
+    if (q >= 64) return M ? 1 : 0;
+    return (M >> q) + (integer_arg(M, q) ? 0 : 1);
+}
+
 namespace cf_detail {
 
 // ln 2 enclosure at P <= LN2_BITS fractional bits into NL limbs
@@ -123,7 +136,7 @@ TMD_HD bool exp2_arg(const CoeffJob& J, uint64_t M, unsigned PB, const CoeffCons
     shr(yhi, q);
     if (up) add_u64(yhi, 1);
     // Xc = ceil(M 2^-q) bounds the argument X ln 2 < X
-    const uint64_t Xc = (M >> q) + ((M & ((1ull << q) - 1)) ? 1 : 0);
+    const uint64_t Xc = ceil_arg(M, q);
     uint64_t e_lo, e_hi;
     U<NL> vlo, vhi;
     if (!exp_big<NL>(ylo, PB + 16, Xc, C.div, vlo, e_lo)) return false;
@@ -222,7 +235,7 @@ TMD_HD bool f_direct(const CoeffJob& J, uint64_t M, unsigned PB, const CoeffCons
         if (q == 0 || q >= 64 || (M >> q) != (uint64_t)J.red) return false;
         M -= (uint64_t)J.red << q;
     }
-    if (q == 0 || (M & ((1ull << q) - 1)) == 0) {  // 2^X at an integer X
+    if (integer_arg(M, q)) {  // 2^X at an integer X (then q < 64 or X = 0)
         set_pow2(f.lo, PB + (unsigned)(q >= 64 ? 0 : (M >> q)));
         f.hi = f.lo;
         exact = true;
@@ -323,7 +336,7 @@ TMD_HD bool block_coeffs(const CoeffJob& J, uint64_t M, int guard, const CoeffCo
     const unsigned PB = cf_detail::base_bits(J, guard);
     Enc<NL> f;
     bool exact = false;
-    const bool integer_x = J.func == 1 && (q == 0 || (M & ((1ull << q) - 1)) == 0);
+    const bool integer_x = J.func == 1 && integer_arg(M, q);
     if (!(anchor && !integer_x && cf_detail::f_anchored<NL>(J, M, PB, C, *anchor, f)))
         if (!cf_detail::f_direct<NL>(J, M, PB, C, f, exact)) return false;
     if (J.func == 2) {  // log

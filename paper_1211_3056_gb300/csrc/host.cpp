@@ -99,7 +99,7 @@ Enc ln2_fixed(unsigned P) {
 Enc exp2_fixed(uint64_t M, unsigned q, unsigned P) {
     Enc r;
     r.P = P;
-    if (q == 0 || (M & ((1ull << q) - 1)) == 0) {
+    if (integer_arg(M, q)) {
         uint64_t X = q >= 64 ? 0 : (M >> q);
         r.lo = Big::pow2(P + (unsigned)X);
         r.hi = r.lo;
@@ -348,6 +348,7 @@ bool cut_index(const tmd_job& job, int e, int64_t* out) {
     int q = job.p - job.e_in;
     int64_t half = (int64_t)1 << (job.p - 1);
     if (job.func == TMD_EXP2) {
+        if (q >= 62) return false;  // a cut needs X >= 1: q <= p - 1 there
         *out = (int64_t)(e - 1) * ((int64_t)1 << q) - half;
         return true;
     }
@@ -466,7 +467,7 @@ bool output_exponent_fx(const tmd_job& job, uint64_t M, int* e) {
     if (job.func == TMD_EXP) {
         if (!fx::exp_small<6>(M, q, P, C.div, f)) return false;
     } else if (job.func == TMD_EXP2) {
-        if (q == 0 || (M & ((1ull << q) - 1)) == 0) {
+        if (integer_arg(M, q)) {
             fx::set_pow2(f.lo, P + (unsigned)(q >= 64 ? 0 : (M >> q)));
             f.hi = f.lo;
         } else {

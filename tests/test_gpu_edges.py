@@ -61,3 +61,17 @@ def test_pipe_rates_are_plausible():
         assert 32 <= r[k] <= 260, (k, r[k])
     assert r["add_u32"] >= r["lop3"]
     assert 200 < r["sm_mhz"] < 4000
+
+
+@pytest.mark.parametrize("job", [
+    wl.Job(wl.FUNC_EXP2, -16, 53, 20, 14, 3, 20, 3, 1 << 40, 1 << 26),
+    wl.Job(wl.FUNC_EXP, -16, 60, 24, 14, 3, 20, 3, 5 << 50, 1 << 26),
+], ids=["exp2_shift69", "exp_shift76"])
+def test_argument_shift_of_64_and_more(ctx, job):
+    """X = M 2^-q with q = p - e_in >= 64 (the smallest binades): block
+    starts whose low bits are zero are not integer arguments; the device
+    tables and the search give the oracle's list."""
+    want = oc.job_candidates(job, 0)
+    assert len(want) > 0
+    got, n = tmd.run([job], ctx=ctx, fused=True, cap=1 << 16)
+    assert n == len(want) and got == want

@@ -67,6 +67,10 @@ HOST_JOBS = [
     wl.Job(wl.FUNC_EXP, 3, 40, 24, 10, 3, 20, 2, 0, 1 << 38),
     wl.Job(wl.FUNC_EXP2, 9, 30, 16, 8, 2, 12, 2, 5 << 19, 1 << 21, wl.FLAG_BP_DIRECTED),
     wl.Job(wl.FUNC_EXP, 9, 53, 40, 14, 3, 20, 3, (1 << 52) - (1 << 30), 1 << 30),
+    # argument shifts p - e_in of 64 and more (X = M 2^-69, 2^-76), block
+    # starts with many trailing zero bits: not integer arguments
+    wl.Job(wl.FUNC_EXP2, -16, 53, 20, 14, 3, 20, 3, 1 << 40, 1 << 26),
+    wl.Job(wl.FUNC_EXP, -16, 60, 24, 14, 3, 20, 3, 5 << 50, 1 << 26),
 ] + wl.batched_jobs()[:6]
 
 
@@ -195,3 +199,49 @@ def test_sound_job_validation():
         with pytest.raises(tmd.TmdError) as e:
             tmd.tmd_plan(bad)
         assert e.value.status == tmd._lib.TMD_EINVAL
+
+
+def random_jobs(n, seed):
+    """Seeded valid jobs over every supported (function, binade) range,
+    precision, degree, width and length: exp and 2^x from [2^-16, 2^-15) to
+    [256, 512), log from [2, 4) to [2^15, 2^16)."""
+    rng = random.Random(seed)
+    out = []
+    while len(out) < n:
+        func = rng.choice([wl.FUNC_EXP, wl.FUNC_EXP2, wl.FUNC_LOG])
+        e_in = rng.randint(2, 16) if func == wl.FUNC_LOG else rng.choice([-16, -3, 0, 1, 2, 3, 5, 8, 9])
+        p = rng.choice([24, 30, 40, 53])
+        if p - e_in < (8 if func != wl.FUNC_LOG and e_in > 2 else 1):
+            continue
+        log2_N = rng.randint(2, 14)
+        log2_T = log2_N + rng.randint(0, 8)
+        d = rng.randint(1, 4)
+        limbs = rng.randint(1, 3)
+        span = 1 << (p - 1)
+        count = rng.randint(1, min(span, 1 << rng.randint(4, 34)))
+        start = rng.randrange(0, span - count + 1)
+        job = wl.Job(func, e_in, p, rng.randint(8, 40), log2_N, d, log2_T, limbs, start, count,
+                     rng.choice([0, wl.FLAG_BP_DIRECTED]))
+        try:
+            tmd.tmd_plan(job)
+        except tmd.TmdError as e:
+            # more than 4 output binades in the slice is the one refusal expected
+            assert e.status == tmd._lib.TMD_EUNSUPPORTED
+            continue
+        out.append(job)
+    return out
+
+
+@pytest.mark.parametrize("job", random_jobs(16, 20261204), ids=lambda j: f"f{j.func}e{j.e_in}p{j.p}d{j.d}L{j.limbs}")
+def test_random_plans_and_tables_match_oracle(job):
+    info = tmd.tmd_plan(job)
+    ob = plan.blocks(job)
+    assert info["n_blocks"] == len(ob)
+    assert info["n_subints"] == plan.n_subintervals(job)
+    assert info["cuts"] == [s[0] for s in plan.segments(job)[1:]]
+    rng = random.Random(job.start ^ job.count ^ 77)
+    for b in sorted({0, len(ob) - 1, rng.randrange(len(ob))})[:3]:
+        c, tab, bi = tmd.tmd_block_tables(job, b)
+        oc_, ot = oracle_table(job, ob[b])
+        assert bi["e_out"] == ob[b].e_out
+        assert c == oc_ and tab == ot

@@ -245,3 +245,55 @@ def test_random_plans_and_tables_match_oracle(job):
         oc_, ot = oracle_table(job, ob[b])
         assert bi["e_out"] == ob[b].e_out
         assert c == oc_ and tab == ot
+
+
+def random_sound_jobs(n, seed):
+    """Seeded valid jobs whose sound thresholds fit (eps1 < 2^62)."""
+    rng = random.Random(seed)
+    out = []
+    for job in random_jobs(4 * n, seed):
+        if len(out) == n:
+            break
+        if job.func == wl.FUNC_EXP2 and job.e_in > 3:
+            continue  # keeps the oracle's 2^x enclosures short
+        try:
+            tmd.tmd_sound_eps(job)
+        except tmd.TmdError as e:
+            assert e.status == tmd._lib.TMD_EINVAL  # thresholds past 2^62 are refused
+            continue
+        out.append(job.replace(m=rng.randint(8, 40)))
+    return out
+
+
+@pytest.mark.parametrize("job", random_sound_jobs(10, 4242), ids=lambda j: f"f{j.func}e{j.e_in}p{j.p}d{j.d}")
+def test_random_sound_eps_not_below_the_oracle_bounds(job):
+    from oracle import sound
+    try:
+        e1, e3 = tmd.tmd_sound_eps(job)
+    except tmd.TmdError as e:
+        assert e.status == tmd._lib.TMD_EINVAL
+        return
+    o1, o3 = sound.min_eps(job)
+    assert o3 <= e3 <= o3 * 1.01 + 64
+    assert o1 <= e1 <= o1 * 1.01 + 64
+
+
+def test_fuzzed_job_records_never_crash():
+    """Random field values, mostly out of range: tmd_plan answers OK,
+    TMD_EINVAL or TMD_EUNSUPPORTED, never anything else."""
+    rng = random.Random(99)
+    seen = set()
+    for _ in range(3000):
+        job = wl.Job(rng.choice([-1, 0, 1, 2, 3, 7]), rng.randint(-40, 80), rng.randint(-5, 70), rng.randint(-3, 70),
+                     rng.randint(0, 40), rng.randint(-2, 9), rng.randint(0, 70), rng.randint(0, 6),
+                     rng.getrandbits(rng.choice([0, 8, 40, 63, 64])), rng.getrandbits(rng.choice([0, 1, 20, 52, 64])),
+                     rng.choice([0, 1, 2, 4, 8, 16, 3, 12]))
+        try:
+            tmd.tmd_plan(job)
+            seen.add(0)
+        except tmd.TmdError as e:
+            assert e.status in (tmd._lib.TMD_EINVAL, tmd._lib.TMD_EUNSUPPORTED), (job, e.status)
+            seen.add(e.status)
+        except (OverflowError, ValueError, TypeError):
+            seen.add(-1)  # not representable in the C record: refused by the binding
+    assert tmd._lib.TMD_EINVAL in seen and tmd._lib.TMD_EUNSUPPORTED in seen

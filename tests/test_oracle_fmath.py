@@ -154,3 +154,21 @@ def test_exp_brackets_powers_of_two():
         # and e(f) flips exactly there
         assert fmath.exponent_of(fmath.FUNC_EXP, x_lo) == K
         assert fmath.exponent_of(fmath.FUNC_EXP, x_hi) == K + 1
+
+
+def test_exponent_of_against_libm_over_all_binades():
+    """e(f(X)) (Def. 1) against frexp of libm's f(X) at random X of every
+    supported binade: exp and 2^x on [2^-17, 2^-16) .. [256, 512), log on
+    [2, 4) .. [2^15, 2^16); points within 1e-9 of a power of two skipped."""
+    rng = random.Random(1211)
+    for func, e_ins in ((fmath.FUNC_EXP, range(-16, 10)), (fmath.FUNC_EXP2, range(-16, 10)),
+                        (fmath.FUNC_LOG, range(2, 17))):
+        fn = {fmath.FUNC_EXP: math.exp, fmath.FUNC_EXP2: lambda v: 2.0 ** v, fmath.FUNC_LOG: math.log}[func]
+        for e_in in e_ins:
+            for _ in range(4):
+                x = F(rng.randrange(1 << 52, 1 << 53), 1 << (53 - e_in))   # [2^(e_in-1), 2^e_in)
+                v = fn(float(x))
+                m, e = math.frexp(v)
+                if abs(m - 0.5) < 1e-9 or abs(m - 1.0) < 1e-9:
+                    continue
+                assert fmath.exponent_of(func, x) == e, (func, e_in, float(x))

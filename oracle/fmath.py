@@ -30,6 +30,7 @@ returned as degenerate intervals lo == hi.
 """
 from __future__ import annotations
 
+import functools
 from fractions import Fraction
 from typing import Tuple
 
@@ -56,19 +57,33 @@ def exp_interval(x: Fraction, bits: int) -> Interval:
         return Fraction(1), Fraction(1)
     if x > 4:
         return _exp_by_squaring(x, bits)
-    eps = _pow2(-bits)
-    term = Fraction(1)
-    s = Fraction(1)
+    # x = a / b.  The partial sum is kept over the common denominator
+    # Q = b^n n! (the denominator of the n-th term x^n / n! = a^n / Q), so
+    # S_n = U / Q with U <- U b n + a^n: the same exact rational as adding
+    # the terms one by one, without reducing a fraction at every step.
+    a, b = x.numerator, x.denominator
+    P = Q = U = 1   # a^n, b^n n!, S_n Q; n = 0: S_0 = 1
     n = 0
     while True:
         n += 1
-        term = term * x / n
-        s += term
-        if n + 2 > x:
-            nxt = term * x / (n + 1)
-            tail = nxt / (1 - x / (n + 2))
-            if tail <= eps:
-                return s, s + tail
+        P *= a
+        Q *= b * n
+        U = U * b * n + P
+        if (n + 2) * b > a:  # n + 2 > x
+            # tail = x^(n+1)/(n+1)! / (1 - x/(n+2))
+            #      = a^(n+1) (n+2) / (Q (n+1) ((n+2) b - a))
+            tn = P * a * (n + 2)
+            td = Q * (n + 1) * ((n + 2) * b - a)
+            if _at_most_pow2(tn, td, -bits):
+                s = Fraction(U, Q)
+                return s, s + Fraction(tn, td)
+
+
+def _at_most_pow2(num: int, den: int, e: int) -> bool:
+    """num / den <= 2^e for integers num >= 0, den > 0."""
+    if e >= 0:
+        return num <= den << e
+    return num << -e <= den
 
 
 def atanh_interval(z: Fraction, bits: int) -> Interval:
@@ -81,23 +96,36 @@ def atanh_interval(z: Fraction, bits: int) -> Interval:
         raise ValueError("atanh_interval needs 0 <= z < 1")
     if z == 0:
         return Fraction(0), Fraction(0)
-    eps = _pow2(-bits)
-    z2 = z * z
-    power = z          # z^(2n+1)
-    s = Fraction(0)
+    # z = c / e.  Term n is z^(2n+1) / (2n+1) = c^(2n+1) / (e^(2n+1) (2n+1));
+    # the partial sum is kept over the common denominator
+    # Q = e^(2n+1) * 1 * 3 * ... * (2n+1) as S_n = U / Q (the same exact
+    # rational as adding the terms one by one).
+    c, e = z.numerator, z.denominator
+    c2, e2 = c * c, e * e
+    C, E, R = c, e, 1   # c^(2n+1), e^(2n+1), 1 * 3 * ... * (2n+1)
+    U = c               # n = 0: S_0 = z = c / e
     n = 0
     while True:
-        s += power / (2 * n + 1)
-        nxt_power = power * z2
-        tail = nxt_power / ((2 * n + 3) * (1 - z2))
-        if tail <= eps:
-            return s, s + tail
-        power = nxt_power
+        # tail after term n: z^(2n+3) / ((2n+3) (1 - z^2))
+        #                  = C c^2 / (E (2n+3) (e^2 - c^2))
+        tn = C * c2
+        td = E * (2 * n + 3) * (e2 - c2)
+        if _at_most_pow2(tn, td, -bits):
+            s = Fraction(U, E * R)
+            return s, s + Fraction(tn, td)
         n += 1
+        k = 2 * n + 1
+        # U / (E R) + C c^2 / (E e^2 k) over the new denominator E e^2 R k
+        U = U * e2 * k + C * c2 * R
+        C *= c2
+        E *= e2
+        R *= k
 
 
+@functools.lru_cache(maxsize=None)
 def ln2_interval(bits: int) -> Interval:
-    """ln 2 = 2 atanh(1/3)."""
+    """ln 2 = 2 atanh(1/3) (memoised: the 2^x coefficients of every block of
+    a job ask for the same few precisions)."""
     lo, hi = atanh_interval(Fraction(1, 3), bits + 1)
     return 2 * lo, 2 * hi
 

@@ -485,9 +485,14 @@ tmd_status tmd_server_destroy(tmd_server* server);
  * outputs d_cand[cand_cap] and d_count (results exactly as tmd_search).  The
  * first call on a device looks up the array's device address
  * (cudaGetSymbolAddress) and caches it; make that first call before any
- * stream capture.  TMD_ENOMEM when the jobs' plan exceeds
- * TMD_STATIC_SCRATCH_BYTES (nothing is launched); TMD_EINVAL on bad
- * arguments; TMD_ECUDA on a failed runtime call.  Every call uses the same
+ * stream capture.  The cached address belongs to the device's primary
+ * context: do not use this entry point again after cudaDeviceReset.  While
+ * `stream` is capturing a graph the call returns TMD_EUNSUPPORTED and
+ * enqueues nothing (the plan goes up from a host buffer that lives only for
+ * the call).  TMD_ENOMEM when the jobs' plan exceeds
+ * TMD_STATIC_SCRATCH_BYTES (decided from the plan's sizes before any table
+ * is computed; nothing is launched); TMD_EINVAL on bad arguments;
+ * TMD_ECUDA on a failed runtime call.  Every call uses the same
  * array and leaves its contents behind (the counters are cleared at the
  * start of each call): calls whose work overlaps on the GPU -- on different
  * streams or host threads -- race and corrupt each other.  The results are

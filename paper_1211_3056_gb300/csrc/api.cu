@@ -1455,7 +1455,8 @@ std::mutex g_static_mutex;
 char* g_static_base[STATIC_MAX_DEVICES] = {};
 
 // Device address of the scratch array on the current device (set-up on the
-// first call per device).
+// first call per device).  The address belongs to the device's primary
+// context: after cudaDeviceReset the cached value is stale.
 tmd_status static_scratch_base(int device, char** out) {
     if (device < 0 || device >= STATIC_MAX_DEVICES) return TMD_EUNSUPPORTED;
     std::lock_guard<std::mutex> lock(g_static_mutex);
@@ -1476,25 +1477,34 @@ extern "C" {
 tmd_status tmd_search_static(const tmd_job* jobs, uint32_t njobs, tmd_candidate* d_cand,
                              uint64_t cand_cap, uint64_t* d_count, void* stream) {
     if (!jobs || njobs == 0 || !d_count || (cand_cap && !d_cand)) return TMD_EINVAL;
+    cudaStream_t s = (cudaStream_t)stream;
+    // the plan goes up from a host buffer that lives only for this call: a
+    // capturing stream would keep a copy node that reads it on every replay
+    cudaStreamCaptureStatus cap_st = cudaStreamCaptureStatusNone;
+    CK(cudaStreamIsCapturing(s, &cap_st));
+    if (cap_st != cudaStreamCaptureStatusNone) return TMD_EUNSUPPORTED;
     int device = 0;
     CK(cudaGetDevice(&device));
     char* base = nullptr;
     tmd_status st = static_scratch_base(device, &base);
     if (st != TMD_OK) return st;
+    // sizes first (counts and offsets only), so that an oversized plan is
+    // refused before any correctly rounded table is computed
     Plan P;
-    st = build_plan(jobs, njobs, P);
+    st = build_plan(jobs, njobs, P, /*host_tables=*/false);
     if (st != TMD_OK) return st;
     const size_t o_blocks = align256(P.jobs.size() * sizeof(DevJob));
-    const size_t o_tables = align256(o_blocks + P.blocks.size() * sizeof(DevBlock));
-    const size_t o_tasks = align256(o_tables + P.tables.size() * sizeof(uint64_t));
-    const size_t total = align256(o_tasks + P.tasks.size() * sizeof(DevTask));
+    const size_t o_tables = align256(o_blocks + P.n_blocks * sizeof(DevBlock));
+    const size_t o_tasks = align256(o_tables + P.table_words * sizeof(uint64_t));
+    const size_t total = align256(o_tasks + P.n_tasks * sizeof(DevTask));
     if (total > TMD_STATIC_SCRATCH_BYTES) return TMD_ENOMEM;
+    st = build_plan(jobs, njobs, P, /*host_tables=*/true);
+    if (st != TMD_OK) return st;
     std::vector<char> host(total, 0);
     memcpy(host.data(), P.jobs.data(), P.jobs.size() * sizeof(DevJob));
     memcpy(host.data() + o_blocks, P.blocks.data(), P.blocks.size() * sizeof(DevBlock));
     memcpy(host.data() + o_tables, P.tables.data(), P.tables.size() * sizeof(uint64_t));
     memcpy(host.data() + o_tasks, P.tasks.data(), P.tasks.size() * sizeof(DevTask));
-    cudaStream_t s = (cudaStream_t)stream;
     char* arena = base + STATIC_MISC_BYTES;
     // pageable source: the call returns once the bytes are staged, so the
     // vector may go out of scope afterwards

@@ -24,6 +24,10 @@ def ctx():
     c.close()
 
 
+# exact decisions in the 2^-31 list of Table 2's domain: arguments whose
+# exp comes within 1.01 x 2^-32 of a binary64 number (241 below 2^-32)
+TABLE2_WITHIN_1_01 = 243
+
 SMALL = [
     wl.Job(wl.FUNC_EXP, 0, 24, 10, 8, 2, 12, 1, 3 << 20, 1 << 13),
     wl.Job(wl.FUNC_EXP2, 1, 22, 7, 7, 3, 11, 1, 12345, 1 << 11, wl.FLAG_BP_DIRECTED),
@@ -110,23 +114,25 @@ def test_table2_hard_to_round_cases_of_exp(ctx):
     -- 2^39 binary64 arguments, breakpoints the binary64 numbers (Def. 3,
     directed rounding, Sect. V) -- are printed as 243.  The sound path lists
     every argument within eps3 of a breakpoint on the block polynomials and
-    each listed argument is decided exactly from enclosures of exp.  The
-    exact decision leaves two fewer: the next two arguments lie 0.16 % and
-    1.0 % above 2^-32, so a count taken with a threshold about 1 % above
+    each listed argument is decided exactly from enclosures of exp: there
+    are exactly 241.  The next arguments lie just above 2^-32 (0.16 % and
+    1.0 % above it), so a count taken with a threshold about 1 % above
     2^-32 (an approximation error left in the paper's last check) gives the
-    printed 243; the test accepts the printed count or up to two fewer.
-    With the threshold 2^-31 every argument below 1.01 x 2^-32 is listed,
-    and their number is the printed 243 exactly or within the same two."""
+    printed 243.  With the threshold 2^-31 every argument below
+    1.01 x 2^-32 is listed, and the count in that window is pinned too."""
     job = tmd.sound_job(wl.Job(wl.FUNC_EXP, 1, 53, 32, 15, 3, 24, 3, 0, 1 << 39, wl.FLAG_BP_DIRECTED))
     got, n = tmd.run([job], ctx=ctx, fused=True, cap=1 << 16)
     assert n == len(got) < 1 << 16
     plain = job.replace(flags=wl.FLAG_BP_DIRECTED, eps1=0, eps3=0)
     hr = [r[2] for r in got if sound.is_hard_to_round(plain, r[2])]
     print("listed", n, "hard-to-round", len(hr))
-    assert 243 - 2 <= len(hr) <= 243
+    assert len(hr) == 241
     wide = tmd.sound_job(plain.replace(m=31))
     got31, n31 = tmd.run([wide], ctx=ctx, fused=True, cap=1 << 16)
     assert set(hr) <= {r[2] for r in got31}
-    near = [r[2] for r in got31 if sound.distance(plain, r[2])[1] < Fraction(101, 100) / (1 << 32)]
-    print("within 1.01 x 2^-32:", len(near))
-    assert 243 - 2 <= len(near) <= 243 + 2 and len(near) >= len(hr)
+    dist = sorted(float(sound.distance(plain, r[2])[1] * (1 << 32)) for r in got31)
+    above = [x for x in dist if x >= 1.0][:4]
+    near = [x for x in dist if x < 1.01]
+    print("within 1.01 x 2^-32:", len(near), "next distances / 2^-32:", above)
+    assert len([x for x in dist if x < 1.0]) == 241
+    assert len(near) == TABLE2_WITHIN_1_01

@@ -5,8 +5,9 @@ they search (their allocator owns the pool, their host forbids it, or their
 loop allows no allocation after start-up): it keeps the plan in the
 library's fixed device array.  Its records must equal those of the ordinary
 entry point (tmd_search, fused) exactly -- integer results, so the tolerance
-is zero -- on two calls in a row, which also checks that the array's leftover
-contents from the first call do not leak into the second.  This file is
+is zero -- on two calls in a row, the second with a smaller job list, which
+also checks that what the first call left in the array does not leak into
+the second.  This file is
 collected last so that a failure here leaves every other test already run."""
 import ctypes
 
@@ -39,15 +40,19 @@ def read_back(d_cand, d_count):
 
 
 def test_static_equals_ordinary_entry_point_twice():
+    """Two calls in a row: the first with all of JOBS (the larger plan), the
+    second with a smaller, different list, whose plan overwrites only part of
+    what the first call left in the array."""
     torch.cuda.set_device(0)
+    calls = [JOBS, [JOBS[2], JOBS[0]]]
     with tmd.Context(0) as ctx:
-        want, n_want = tmd.run(JOBS, ctx=ctx, fused=True, cap=1 << 16)
-    assert n_want > 1000
-    for call in range(2):
+        wants = [tmd.run(jobs, ctx=ctx, fused=True, cap=1 << 16) for jobs in calls]
+    assert wants[0][1] > 1000 and wants[1][1] > 100
+    for call, (jobs, (want, n_want)) in enumerate(zip(calls, wants)):
         d_cand, d_count = tmd.alloc_candidates(1 << 16)
         d_cand.fill_(0xAB)
         d_count.fill_(12345)                  # the entry point must clear it
-        tmd.tmd_search_static(JOBS, d_cand, d_count)
+        tmd.tmd_search_static(jobs, d_cand, d_count)
         torch.cuda.synchronize()
         got, n = read_back(d_cand, d_count)
         assert n == n_want, call

@@ -88,6 +88,67 @@ __device__ __forceinline__ Word<L> w_mul_u64(const Word<L>& a, uint64_t c) {
     return r;
 }
 
+// acc += w * c mod 2^192 for a 32-bit c, on the six 32-bit words of the
+// operands: the low halves of the six products c w_j go into one carry
+// chain, the high halves (one word up) into a second.  SHIFT = 1 adds
+// w * c * 2^32 instead (every product one word higher).
+template <int SHIFT>
+__device__ __forceinline__ void w3_madd32(Word<3>& acc, const Word<3>& w, uint32_t c) {
+    uint32_t a[6], x[6];
+#pragma unroll
+    for (int i = 0; i < 3; i++) {
+        a[2 * i] = (uint32_t)acc.l[i];
+        a[2 * i + 1] = (uint32_t)(acc.l[i] >> 32);
+        x[2 * i] = (uint32_t)w.l[i];
+        x[2 * i + 1] = (uint32_t)(w.l[i] >> 32);
+    }
+    if (SHIFT == 0) {
+        asm("mad.lo.cc.u32 %0, %6, %12, %0;\n\t"
+            "madc.lo.cc.u32 %1, %7, %12, %1;\n\t"
+            "madc.lo.cc.u32 %2, %8, %12, %2;\n\t"
+            "madc.lo.cc.u32 %3, %9, %12, %3;\n\t"
+            "madc.lo.cc.u32 %4, %10, %12, %4;\n\t"
+            "madc.lo.u32 %5, %11, %12, %5;\n\t"
+            "mad.hi.cc.u32 %1, %6, %12, %1;\n\t"
+            "madc.hi.cc.u32 %2, %7, %12, %2;\n\t"
+            "madc.hi.cc.u32 %3, %8, %12, %3;\n\t"
+            "madc.hi.cc.u32 %4, %9, %12, %4;\n\t"
+            "madc.hi.u32 %5, %10, %12, %5;"
+            : "+r"(a[0]), "+r"(a[1]), "+r"(a[2]), "+r"(a[3]), "+r"(a[4]), "+r"(a[5])
+            : "r"(x[0]), "r"(x[1]), "r"(x[2]), "r"(x[3]), "r"(x[4]), "r"(x[5]), "r"(c));
+    } else {
+        asm("mad.lo.cc.u32 %1, %6, %12, %1;\n\t"
+            "madc.lo.cc.u32 %2, %7, %12, %2;\n\t"
+            "madc.lo.cc.u32 %3, %8, %12, %3;\n\t"
+            "madc.lo.cc.u32 %4, %9, %12, %4;\n\t"
+            "madc.lo.u32 %5, %10, %12, %5;\n\t"
+            "mad.hi.cc.u32 %2, %6, %12, %2;\n\t"
+            "madc.hi.cc.u32 %3, %7, %12, %3;\n\t"
+            "madc.hi.cc.u32 %4, %8, %12, %4;\n\t"
+            "madc.hi.u32 %5, %9, %12, %5;"
+            : "+r"(a[0]), "+r"(a[1]), "+r"(a[2]), "+r"(a[3]), "+r"(a[4]), "+r"(a[5])
+            : "r"(x[0]), "r"(x[1]), "r"(x[2]), "r"(x[3]), "r"(x[4]), "r"(x[5]), "r"(c));
+    }
+#pragma unroll
+    for (int i = 0; i < 3; i++) acc.l[i] = ((uint64_t)a[2 * i + 1] << 32) | a[2 * i];
+}
+
+// acc += w * binom(i0, J) mod 2^W in the straightforward shift, i0 < 2^16:
+// binom(i0, 1) and binom(i0, 2) are below 2^32 and binom(i0, 3) below 2^46,
+// so for 192-bit words the product takes one or two 32-bit multiplier
+// passes instead of a full 64 x 64-bit product per limb.
+template <int L, int J>
+__device__ __forceinline__ void w_madd_binom(Word<L>& acc, const Word<L>& w, uint64_t c) {
+    if constexpr (L == 3 && J <= 2) {
+        w3_madd32<0>(acc, w, (uint32_t)c);
+    } else if constexpr (L == 3 && J == 3) {
+        w3_madd32<0>(acc, w, (uint32_t)c);
+        w3_madd32<1>(acc, w, (uint32_t)(c >> 32));
+    } else {
+        w_add<L>(acc, w_mul_u64<L>(w, c));
+    }
+}
+
 // binom(n, j), j = 0..4, exact for n <= 2^16
 __device__ __forceinline__ void binomials(uint64_t n, uint64_t* c) {
     c[0] = 1;
@@ -131,8 +192,8 @@ __device__ __forceinline__ float scaled_rcp(float bf) {
 // borrow of x - b, as a 0 / all-ones mask, adds b back (the subtract-with-
 // borrow and add-with-carry chains issue at the full 32-bit add rate, the
 // compares and selects they replace on the half-rate logic pipe).
-__device__ __forceinline__ uint64_t csub(uint64_t x, uint64_t b) {
-    uint32_t t0, t1, bw;
+__device__ __forceinline__ uint64_t csub(uint64_t x, uint64_t b, uint32_t& bw) {
+    uint32_t t0, t1;
     asm("sub.cc.u32 %0, %3, %5;\n\tsubc.cc.u32 %1, %4, %6;\n\tsubc.u32 %2, 0, 0;"
         : "=r"(t0), "=r"(t1), "=r"(bw)
         : "r"((uint32_t)x), "r"((uint32_t)(x >> 32)), "r"((uint32_t)b), "r"((uint32_t)(b >> 32)));
@@ -142,12 +203,19 @@ __device__ __forceinline__ uint64_t csub(uint64_t x, uint64_t b) {
     return ((uint64_t)t1 << 32) | t0;
 }
 
+__device__ __forceinline__ uint64_t csub(uint64_t x, uint64_t b) {
+    uint32_t bw;
+    return csub(x, b, bw);
+}
+
 // r = a - k b for an estimate k in {floor(a/b) - 1, floor(a/b)}, then one
-// conditional subtract; k is raised when the subtract happens.
+// conditional subtract; k is raised when the subtract happens (its borrow
+// mask is 0 then, all ones otherwise: k + 1 + mask).
 __device__ __forceinline__ uint64_t rem_fix(uint64_t a, uint64_t b, uint32_t& k) {
     const uint64_t r = a - (uint64_t)k * b;
-    const uint64_t rr = csub(r, b);
-    k += rr != r ? 1u : 0u;
+    uint32_t bw;
+    const uint64_t rr = csub(r, b, bw);
+    k += 1u + bw;
     return rr;
 }
 
@@ -627,6 +695,25 @@ struct Packet {
     bool active;
 };
 
+// Delta^l <- sum_{k>=l} binom(i0, k-l) Delta^k(0), l = 0..E, in place
+// (ascending l only reads the still-unshifted higher orders); E is the
+// column's top order.
+template <int L, int E, int l, int k>
+__device__ __forceinline__ void shift_terms(Word<L>* col, const uint64_t* c) {
+    if constexpr (k <= E) {
+        w_madd_binom<L, k - l>(col[l], col[k], c[k - l]);
+        shift_terms<L, E, l, k + 1>(col, c);
+    }
+}
+
+template <int L, int E, int l>
+__device__ __forceinline__ void shift_column(Word<L>* col, const uint64_t* c) {
+    if constexpr (l < E) {
+        shift_terms<L, E, l, l + 1>(col, c);
+        shift_column<L, E, l + 1>(col, c);
+    }
+}
+
 template <int L, int D>
 __device__ __forceinline__ uint32_t packet_init(Packet<L, D>& P, const DevTask& t, const DevJob& job,
                                                 const LaunchArgs& a) {
@@ -663,14 +750,8 @@ __device__ __forceinline__ uint32_t packet_init(Packet<L, D>& P, const DevTask& 
     // Delta^l(i0) = sum_{k>=l} binom(i0, k-l) Delta^k(0)
     uint64_t c[5];
     binomials(P.i0, c);
-#pragma unroll
-    for (int l = 0; l < D; l++)
-#pragma unroll
-        for (int k = l + 1; k <= D; k++) w_add<L>(P.d0[l], w_mul_u64<L>(P.d0[k], c[k - l]));
-#pragma unroll
-    for (int l = 0; l + 1 < D; l++)
-#pragma unroll
-        for (int k = l + 1; k < D; k++) w_add<L>(P.d1[l], w_mul_u64<L>(P.d1[k], c[k - l]));
+    shift_column<L, D, 0>(P.d0, c);
+    shift_column<L, D - 1, 0>(P.d1, c);
     return lo;
 }
 

@@ -79,6 +79,29 @@ def ops_per_line(job) -> int:
     return 2 * (2 * job.d - 1) * job.limbs + 4
 
 
+# The method's own count (the paper's work per partial quotient, Sect. III-B,
+# Algorithm 4): one quotient and one reduction of d (two 64-bit divisions),
+# two 64-bit multiply-subtracts and two adds/compares per half-step, each
+# counted as one operation -- the useful-work fraction beside the cost model.
+METHOD_OPS_PER_HALF_STEP = 6
+
+
+def roofline_of(tmd, jobs, stats, ms: float) -> dict:
+    """Integer-issue roofline of one timed launch (or step) over `jobs`:
+    algorithmic operations from the cost model (stepping per line, 35 per
+    continued-fraction half-step counted live by the kernel) divided by the
+    step time, against the derived issue ceiling."""
+    lines = [tmd.tmd_plan(j)["n_subints"] for j in jobs]
+    gen = sum(n * ops_per_line(j) for n, j in zip(lines, jobs))
+    alg = gen + stats["half_steps"] * OPS_PER_HALF_STEP
+    method = gen + stats["half_steps"] * METHOD_OPS_PER_HALF_STEP
+    sec = ms / 1e3
+    return {"bound": "alu", "achieved": alg / sec / 1e12, "peak": ISSUE_PEAK_OPS / 1e12, "unit": "Tops/s",
+            "frac": alg / sec / ISSUE_PEAK_OPS, "frac_method": method / sec / ISSUE_PEAK_OPS,
+            "half_steps_per_line": stats["half_steps"] / max(1, stats["lines"]),
+            "filter_fail_per_line": stats["filter_fail"] / max(1, stats["lines"])}
+
+
 def rank_info():
     r = int(os.environ.get("RANK", "0"))
     w = int(os.environ.get("WORLD_SIZE", "1"))
@@ -227,34 +250,31 @@ def run_reference(args):
 
 
 # ----------------------------------------------------------- served form
+SERVER_CFG = dict(max_inflight=4, chunk_tasks=0, cand_cap=1 << 16, max_batch=1024, device_budget=8 << 30)
+
+
 def run_serving(tmd, ctx, jobs, rate_per_s, seed=2012):
-    """Submit `jobs` with exponential gaps (rate_per_s; inf = all at once)
-    to a server on ctx and collect every result.  Returns (wall seconds,
-    latencies in s, total args, total records)."""
-    import math
-    gaps = ([0.0] * len(jobs) if math.isinf(rate_per_s)
-            else [g2 - g1 for g1, g2 in zip([0.0] + wl.arrival_times(len(jobs), rate_per_s, seed)[:-1],
-                                            wl.arrival_times(len(jobs), rate_per_s, seed))])
-    lat, recs = [], 0
-    with tmd.Server(ctx, max_inflight=16, chunk_tasks=4096, cand_cap=1 << 14, max_batch=32) as srv:
-        t0 = time.perf_counter()
-        next_t = t0
+    """Serve `jobs` arriving with exponential gaps (rate_per_s; inf = all at
+    once), replayed by the server's clock (tmd_server_submit_many), and
+    collect every result.  Returns (seconds from the first arrival to the
+    last completion, latencies in s, total args, total records, server
+    counters)."""
+    n = len(jobs)
+    delays = [0.0] * n if math.isinf(rate_per_s) else wl.arrival_times(n, rate_per_s, seed)
+    lat, recs, t_first, t_last = [], 0, float("inf"), 0.0
+    with tmd.Server(ctx, **SERVER_CFG) as srv:
+        srv.submit_many(jobs, list(range(n)), delays)
         done = 0
-        for tag, (job, gap) in enumerate(zip(jobs, gaps)):
-            next_t += gap
-            while True:
-                now = time.perf_counter()
-                if now >= next_t:
-                    break
-                for r, rr in srv.poll(wait_ms=0):
-                    lat.append(r["t_done"] - r["t_submit"]); recs += r["count"]; done += 1
-                time.sleep(min(1e-4, next_t - now))
-            srv.submit(job, tag)
-        while done < len(jobs):
-            for r, rr in srv.poll(wait_ms=50):
-                lat.append(r["t_done"] - r["t_submit"]); recs += r["count"]; done += 1
-        wall = time.perf_counter() - t0
-    return wall, lat, sum(j.count for j in jobs), recs
+        while done < n:
+            for r, rr in srv.poll(cap=4096, rec_cap=1 << 18, wait_ms=50):
+                assert r["status"] == 0, r
+                lat.append(r["t_done"] - r["t_submit"])
+                t_first = min(t_first, r["t_submit"])
+                t_last = max(t_last, r["t_done"])
+                recs += r["count"]
+                done += 1
+        st = srv.stats()
+    return t_last - t_first, lat, sum(j.count for j in jobs), recs, st
 
 
 def percentile(xs, q):
@@ -277,7 +297,7 @@ def main():
                     help="jobs of the seeded mixed batch for batched vs per-job launches (0 = skip)")
     ap.add_argument("--large", type=int, default=1,
                     help="run the large batch: 2^x, 2^40 args in 2^16 uneven jobs (0 = skip)")
-    ap.add_argument("--serve-jobs", type=int, default=400,
+    ap.add_argument("--serve-jobs", type=int, default=10000,
                     help="jobs of the seeded serving stream to serve (0 = skip)")
     ap.add_argument("--count-log2", type=int, default=36,
                     help="slice size (smaller only for profiling captures)")
@@ -293,8 +313,10 @@ def main():
                     help="also search the whole binade [1, 2) of exp, Table 4's workload (0 = skip)")
     ap.add_argument("--binade-full-chunks", type=int, default=1024,
                     help="2^42-argument calls of the whole-binade run (1024 = all of [1, 2))")
+    ap.add_argument("--twins", type=int, default=1,
+                    help="also time the dense twins (m = 20 / 20 / 22) of the plain, mixed and large workloads")
     ap.add_argument("--tiling", default="auto",
-                    help="'auto' (tmd_autotune picks it) or 'nu,ctas_per_sm' for the batched form")
+                    help="'auto' (tmd_autotune picks it) or 'nu,ctas_per_sm[,lanes[,unroll]]' for the batched form")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     if args.impl == "reference":
@@ -338,9 +360,9 @@ def main():
         tuned = tmd.tmd_autotune(ctx, [job])
         tiling = None
     else:
-        nu, per_sm = (int(v) for v in args.tiling.split(","))
-        tuned = {"nu": nu, "ctas_per_sm": per_sm, "ms": None}
-        tiling = (nu, per_sm)
+        tl = [int(v) for v in args.tiling.split(",")] + [1, 1]
+        tuned = {"nu": tl[0], "ctas_per_sm": tl[1], "lanes": tl[2], "unroll": tl[3], "ms": None}
+        tiling = tuple(tl[:4])
     d_cand_b, d_count_b = tmd.alloc_candidates(cap, local_rank)
     batch = tmd.Batch(ctx, [job], d_cand_b, d_count_b, tiling=tiling)
 
@@ -430,7 +452,28 @@ def main():
                               "logic and integer multiply-add"),
                 "measured_pipe_rates": pipe_rates,
                 "half_steps_per_line": stats["half_steps"] / max(1, stats["lines"]),
-                "filter_fail_per_line": stats["filter_fail"] / max(1, stats["lines"])}
+                "filter_fail_per_line": stats["filter_fail"] / max(1, stats["lines"]),
+                "frac_method": (stats["lines"] * ops_per_line(job) + stats["half_steps"] * METHOD_OPS_PER_HALF_STEP)
+                / (statistics.mean(batched_ms) / 1e3) / ISSUE_PEAK_OPS,
+                "frac_method_note": ("useful-work fraction: 6 operations per half-step (two 64-bit divisions, two "
+                                     "multiply-subtracts, two adds/compares: the method's count) instead of the "
+                                     "cost model's 35")}
+
+    # the dense twin of the same slice (m = 20: about 1.3e5 records), batched
+    # the same way: the exact resolution and compaction at scale
+    twin = None
+    if args.twins:
+        tjob = job.replace(m=20)
+        d_cand_t, d_count_t = tmd.alloc_candidates(1 << 18, local_rank)
+        tmd.tmd_autotune(ctx, [tjob])
+        tb = tmd.Batch(ctx, [tjob], d_cand_t, d_count_t)
+        t_ms = max_over_ranks(statistics.mean(timed(tb.launch, 10, 3)))
+        tst = tb.stats()
+        _, t_n = tmd.tmd_candidates(ctx, d_cand_t, d_count_t)
+        twin = {"m": 20, "value": total_args / (t_ms / 1e3), "ms_per_step": t_ms, "candidates": t_n,
+                "roofline": roofline_of(tmd, [tjob], tst, t_ms),
+                "form": "batched, autotuned tiling; flagged lines resolved exactly and compacted"}
+        tb.close()
 
     # Lefevre's filter (Algorithm 3) on the same slice, batched the same way
     # (Table 4's comparison of the two searches; identical records)
@@ -448,7 +491,7 @@ def main():
                    "regular_over_lefevre_time": lef_ms / ms,
                    "iterations_per_line": lst["half_steps"] / max(1, lst["lines"]),
                    "filter_fail_per_line": lst["filter_fail"] / max(1, lst["lines"]),
-                   "tiling": {"nu": ltune["nu"], "ctas_per_sm": ltune["ctas_per_sm"]},
+                   "tiling": {k: ltune[k] for k in ("nu", "ctas_per_sm", "lanes", "unroll")},
                    "form": "batched, Lefevre's lower bound (Algorithm 3) as the filter"}
         lbatch.close()
 
@@ -569,6 +612,7 @@ def main():
         singles = [tmd.Batch(ctx, [j], dmc, dmn) for j in mjobs]
         ms_b = statistics.mean(timed(mb.launch, 10, 3))
         st_b = mb.stats()
+        roof_b = roofline_of(tmd, mjobs, st_b, ms_b)
 
         def per_job():
             for sb in singles:
@@ -577,13 +621,26 @@ def main():
         mixed = {"jobs": len(mjobs), "args": margs, "lines": st_b["lines"],
                  "batched": {"value": margs / (ms_b / 1e3), "ms_per_step": ms_b,
                              "form": "one persistent graph launch over all jobs",
-                             "tiling": {"nu": mtuned["nu"], "ctas_per_sm": mtuned["ctas_per_sm"]}},
+                             "tiling": {k: mtuned[k] for k in ("nu", "ctas_per_sm", "lanes", "unroll")},
+                             "roofline": roof_b},
                  "plain": {"value": margs / (ms_p / 1e3), "ms_per_step": ms_p,
-                           "form": "one launch per job, plans resident"},
+                           "form": "one launch per job, plans resident",
+                           "roofline": roofline_of(tmd, mjobs, st_b, ms_p)},
                  "plan_and_tables_s": t_plan}
         for sb in singles:
             sb.close()
         mb.close()
+        if args.twins:
+            tj = [j.replace(m=20) for j in mjobs]
+            tmd.tmd_autotune(ctx, tj)
+            dtc, dtn = tmd.alloc_candidates(1 << 20, local_rank)
+            tb = tmd.Batch(ctx, tj, dtc, dtn)
+            t_ms = statistics.mean(timed(tb.launch, 10, 3))
+            tst = tb.stats()
+            _, t_n = tmd.tmd_candidates(ctx, dtc, dtn)
+            mixed["twin"] = {"m": 20, "value": margs / (t_ms / 1e3), "ms_per_step": t_ms, "candidates": t_n,
+                             "roofline": roofline_of(tmd, tj, tst, t_ms)}
+            tb.close()
 
     large = None
     if args.large:
@@ -600,22 +657,57 @@ def main():
         large = {"jobs": len(ljobs), "args": largs, "lines": st_l["lines"], "candidates": n_l,
                  "batched": {"value": largs / (ms_l / 1e3), "ms_per_step": ms_l,
                              "form": "one persistent graph launch over all 2^16 jobs",
-                             "tiling": {"nu": ltuned["nu"], "ctas_per_sm": ltuned["ctas_per_sm"]}},
+                             "tiling": {k: ltuned[k] for k in ("nu", "ctas_per_sm", "lanes", "unroll")},
+                             "roofline": roofline_of(tmd, ljobs, st_l, ms_l)},
                  "plan_and_tables_s": t_plan, "upload_bytes": lb.upload_bytes}
         lb.close()
+        if args.twins:
+            tj = [j.replace(m=22) for j in ljobs]
+            tmd.tmd_autotune(ctx, tj)
+            dtc, dtn = tmd.alloc_candidates(1 << 20, local_rank)
+            tb = tmd.Batch(ctx, tj, dtc, dtn)
+            t_ms = statistics.mean(timed(tb.launch, 5, 3))
+            tst = tb.stats()
+            _, t_n = tmd.tmd_candidates(ctx, dtc, dtn)
+            large["twin"] = {"m": 22, "value": largs / (t_ms / 1e3), "ms_per_step": t_ms, "candidates": t_n,
+                             "roofline": roofline_of(tmd, tj, tst, t_ms)}
+            tb.close()
 
     serving = None
     if rank == 0 and args.serve_jobs > 0:
         sjobs = wl.serving_jobs()[: args.serve_jobs]
-        mean_size = sum(j.count for j in sjobs) / len(sjobs)
-        w_sat, lat_sat, a_sat, _ = run_serving(tmd, ctx, sjobs, float("inf"))
+        sargs = sum(j.count for j in sjobs)
+        mean_size = sargs / len(sjobs)
+        w_sat, lat_sat, a_sat, _, st_sat = run_serving(tmd, ctx, sjobs, float("inf"))
         sat = a_sat / w_sat
         rate = 0.8 * sat / mean_size
-        w, lat, a, nrec = run_serving(tmd, ctx, sjobs, rate)
+        reps = []
+        for rep in range(3):
+            w, lat, a, nrec, st = run_serving(tmd, ctx, sjobs, rate)
+            reps.append({"p50_ms": 1e3 * percentile(lat, 0.50), "p99_ms": 1e3 * percentile(lat, 0.99),
+                         "args_per_s": a / w, "seconds": w, "records": nrec, "groups": st["groups"]})
+        # the same jobs as one batch (one persistent graph launch, plans and
+        # tables resident): the ceiling of the served form
+        dsc, dsn = tmd.alloc_candidates(1 << 18, local_rank)
+        sb = tmd.Batch(ctx, sjobs, dsc, dsn)
+        sb_ms = statistics.mean(timed(sb.launch, 3, 3))
+        sbst = sb.stats()
+        sb.close()
+        roof_sat = roofline_of(tmd, sjobs, st_sat, 1e3 * w_sat)
         serving = {"jobs": len(sjobs), "arrival_rate_jobs_per_s": rate, "mean_job_args": mean_size,
-                   "p50_ms": 1e3 * percentile(lat, 0.50), "p99_ms": 1e3 * percentile(lat, 0.99),
-                   "args_per_s": a / w, "saturated_args_per_s": sat, "records": nrec,
-                   "form": "continuous batching: up to 32 waiting jobs per admitted group, 16 slots, Poisson arrivals at 0.8 x saturated rate"}
+                   "p50_ms": statistics.median(r["p50_ms"] for r in reps),
+                   "p99_ms": statistics.median(r["p99_ms"] for r in reps),
+                   "args_per_s": statistics.median(r["args_per_s"] for r in reps),
+                   "repeats": reps,
+                   "saturated_args_per_s": sat, "saturated_seconds": w_sat, "saturated_groups": st_sat["groups"],
+                   "saturated_roofline": roof_sat,
+                   "batched_same_jobs": {"value": sargs / (sb_ms / 1e3), "ms_per_step": sb_ms,
+                                         "roofline": roofline_of(tmd, sjobs, sbst, sb_ms)},
+                   "records": reps[0]["records"],
+                   "form": ("continuous batching: arrived jobs admitted up to 1024 per group into 4 slots "
+                            "(plan, tables, one fused launch per kernel class per group); Poisson arrivals "
+                            "at 0.8 x the saturated rate replayed by the server clock; 3 repeats"),
+                   "latency": "t_done - t_submit per job (arrival to results ready on the host)"}
 
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
@@ -633,6 +725,7 @@ def main():
                        "l2": "256 MiB flush before every step",
                        "form": "batched: persistent work-queue kernel replayed as a CUDA graph",
                        "tiling": {"nu": tuned["nu"], "ctas_per_sm": tuned["ctas_per_sm"],
+                                  "lanes": tuned.get("lanes", 1), "unroll": tuned.get("unroll", 1),
                                   "picked_by": ("tmd_autotune (mean of 4 replays per candidate)"
                                                 if args.tiling == "auto" else "--tiling")},
                        "candidates": count},
@@ -643,7 +736,7 @@ def main():
             "e2e": {"value": total_args / e2e_s, "unit": UNIT, "h2d_bytes_per_step": h2d,
                     "d2h_bytes_per_step": d2h, "ms_per_step": e2e_s * 1e3},
             "gpu_launches": args.steps * 1,
-            "roofline": roofline, "cpu_baseline": cpu, "clocks": clocks, "lefevre": lefevre,
+            "roofline": roofline, "cpu_baseline": cpu, "clocks": clocks, "dense_twin": twin, "lefevre": lefevre,
             "sound_table2": sound_run,
             "binade_128_256": binade128,
             "binade_1_2_whole": binade_full,

@@ -329,17 +329,6 @@ tmd_status tmd_lefevre_bounds(tmd_ctx* ctx, const uint64_t* d_B, const uint64_t*
  * Synchronises `stream`. */
 tmd_status tmd_stats_read(tmd_ctx* ctx, tmd_stats* out, void* stream);
 
-/* Measured issue rates of the pipes the search runs on (no counterpart in the
- * paper: the measured denominator of the integer-pipe roofline).  Long
- * independent chains of one instruction kind per thread, 8 CTAs of 256
- * threads on every SM of `device`, timed by the SM cycle counter:
- * out[0..3] = lane-operations per SM per clock of 32-bit add, 3-input
- * logic, 32-bit multiply-add and FP32 fused multiply-add; out[4] (if
- * n_out > 4) = the SM clock in MHz during the add run.  Writes
- * min(n_out, 5) values.  Synchronises the device; allocates and frees
- * about 1.3 MB of device memory. */
-tmd_status tmd_pipe_rates(int device, double* out, int n_out);
-
 /* ---- batched form: one persistent launch over many jobs, as a CUDA graph ---- */
 
 typedef struct tmd_batch tmd_batch;
@@ -363,14 +352,25 @@ tmd_status tmd_batch_create(tmd_ctx* ctx, const tmd_job* jobs, uint32_t njobs,
  * IV-B), shorter ones give more, smaller tasks of 32 packets.  ctas_per_sm =
  * resident CTAs of 8 warps per SM (0 = the kernel's occupancy): with the
  * task count it fixes how evenly the tasks divide among the resident warps.
- * Lanes per approximation are 1 (one line per lane, Sect. III-C). */
+ * lanes = lanes per approximation in the filter (1, 2 or 4; 0 = 1): the
+ * paper maps one linear approximation to each thread (Sect. III-C); with 2 or
+ * 4 the N arguments of a line are cut into that many pieces of consecutive
+ * arguments, each lane bounding its piece's own line over fewer points, and
+ * the line fails when a piece does (flagged lines are resolved whole, so the
+ * records do not change).  unroll = difference steps per iteration of the
+ * stepping loop (1 or 2; 0 = 1).  The limb count is not a tiling knob: the
+ * word width W is part of the job (it fixes the correctly rounded
+ * coefficients, hence the lines). */
 typedef struct {
     uint32_t nu;
     uint32_t ctas_per_sm;
+    uint32_t lanes;
+    uint32_t unroll;
 } tmd_tiling;
 
 /* tmd_batch_create with an explicit tiling (NULL = the default); EINVAL for
- * nu > 8 or ctas_per_sm > 64.  tmd_batch_create itself takes the tiling that
+ * nu > 8, ctas_per_sm > 64, lanes not in {0, 1, 2, 4} or unroll > 2.
+ * tmd_batch_create itself takes the tiling that
  * tmd_autotune chose for a batch of the same signature on this context
  * (distinct limbs/degree/N classes, SM count, order of magnitude of the
  * sub-interval count), else the default. */
@@ -381,16 +381,19 @@ tmd_status tmd_batch_create_tiled(tmd_ctx* ctx, const tmd_job* jobs, uint32_t nj
 
 /* Autotuner of the batched form (no counterpart in the paper, which tunes
  * its block sizes by hand, Sect. V-A): builds the batch with every tiling of
- * nu in {8, 6, 4, 2, 1} x ctas_per_sm in {occupancy .. 1}, times a few graph
- * replays of each on `stream` (CUDA events; records are counted, not
- * stored), and keeps the fastest in the context for batches of the same
- * signature.  *best receives it, *best_ms (may be NULL) its mean replay time.
- * Synchronises `stream`; allocates and frees 8 bytes of device memory. */
+ * nu in {8, 6, 4, 2, 1} x ctas_per_sm in {occupancy .. 1} (one lane per line,
+ * one step per iteration), then, for the fastest of those, lanes in {1, 2, 4}
+ * x unroll in {1, 2}; times a few graph replays of each on `stream` (CUDA
+ * events; records are counted, not stored), and keeps the fastest in the
+ * context for batches of the same signature.  *best receives it, *best_ms
+ * (may be NULL) its mean replay time.  Synchronises `stream`; allocates and
+ * frees 8 bytes of device memory. */
 tmd_status tmd_autotune(tmd_ctx* ctx, const tmd_job* jobs, uint32_t njobs, void* stream,
                         tmd_tiling* best, float* best_ms);
 
 /* The tiling a batch was built with (nu = its longest packet, ctas_per_sm =
- * its largest per-SM CTA count over the classes). */
+ * its largest per-SM CTA count over the classes, lanes and unroll as
+ * requested, 0 read as 1). */
 tmd_status tmd_batch_tiling(const tmd_batch* batch, tmd_tiling* out);
 
 /* Replay the batch's graph on `stream` (asynchronous). */
@@ -409,15 +412,16 @@ typedef struct tmd_server tmd_server;
 typedef struct {
     uint64_t device_budget;  /* bytes of device memory for the plans of resident jobs
                                 (0 = 1 GiB); a job waits until its plan fits      */
-    uint32_t max_inflight;   /* jobs resident on the device at once, one stream each
-                                (1..64; 0 = 8)                                     */
-    uint32_t chunk_tasks;    /* warp tasks per launch; a job runs as consecutive
-                                launches over its resident tables (0 = 2048)       */
+    uint32_t max_inflight;   /* groups resident on the device at once, one slot
+                                (stream, plan arena, records) each (1..64; 0 = 4) */
+    uint32_t chunk_tasks;    /* warp tasks per search launch; a group's kernel class
+                                is searched by consecutive launches of at most this
+                                many tasks (0 = one launch per class)              */
     uint64_t cand_cap;       /* records kept per admitted group (0 = 65536); a group that
                                 overflows is re-run job by job, so every job's count
                                 stays exact                                         */
     uint32_t max_batch;      /* jobs admitted together into one slot as one plan
-                                (continuous batching of arrivals; 0 = 32)          */
+                                (continuous batching of arrivals; 0 = 1024)        */
     uint32_t reserved;       /* must be 0                                           */
 } tmd_server_config;
 
@@ -430,20 +434,32 @@ typedef struct {
     double   t_submit, t_start, t_done;  /* seconds on the server's clock          */
 } tmd_job_result;
 
-/* Start the serving loop on ctx's device: a host thread admits the jobs
- * waiting in arrival order, up to max_batch at a time, into a free slot
- * whenever their plans fit the device budget; plans them as one group
- * (host), uploads the plan and computes its block tables on the device, and
- * runs the fused search in chunks on the slot's stream, so that groups
- * admitted while others run overlap on the GPU.  Finished groups are read
- * back (count and sorted records, split per job) and queued for
- * tmd_server_poll.  Each job's result is the one tmd_search gives it alone.
- * The server uses ctx only for its device; ctx must outlive it. */
+/* Start the serving loop on ctx's device (continuous batching): a host
+ * worker thread admits the jobs that have arrived, in arrival order, up to
+ * max_batch at a time, into a free slot whenever their plans fit the device
+ * budget; plans them as one group on the host, and enqueues on the slot's
+ * stream the upload of the job records, the device planning and correctly
+ * rounded block tables, one fused search launch per kernel class and the
+ * read-back of the group's count.  A stream callback returns the slot to the
+ * worker, which reads the records and splits them per job into results for
+ * tmd_server_poll.  The worker plans and launches the next group while
+ * earlier ones run, and the groups' launches share the SMs.  Each job's
+ * result is the one tmd_search gives it alone.  The server uses ctx for its
+ * device and its coefficient tables; ctx must outlive it. */
 tmd_status tmd_server_create(tmd_ctx* ctx, const tmd_server_config* cfg, tmd_server** server);
 
 /* Queue one job under the caller's tag (thread-safe, never blocks on the GPU).
  * TMD_EINVAL for a job that fails validation (nothing is queued). */
 tmd_status tmd_server_submit(tmd_server* server, const tmd_job* job, uint64_t id);
+
+/* Queue n jobs that arrive later: job i becomes eligible for admission
+ * delays_s[i] seconds (>= 0) after this call, on the server's clock, and its
+ * result's t_submit is that arrival time -- a recorded or generated arrival
+ * stream (e.g. Poisson) replayed by the server itself.  ids[i] tags job i.
+ * Thread-safe, never blocks on the GPU.  TMD_EINVAL (nothing queued) if a job
+ * fails validation or a delay is negative. */
+tmd_status tmd_server_submit_many(tmd_server* server, const tmd_job* jobs, const uint64_t* ids,
+                                  const double* delays_s, uint32_t n);
 
 /* Move up to `cap` finished jobs into out[] (completion order) and their
  * records, concatenated in the same order, into h_records[0 .. rec_cap)
@@ -456,6 +472,11 @@ tmd_status tmd_server_poll(tmd_server* server, tmd_job_result* out, uint32_t cap
 
 /* Jobs submitted but not yet returned by tmd_server_poll. */
 tmd_status tmd_server_pending(tmd_server* server, uint64_t* n);
+
+/* Counters summed over the groups the server has finished (lines searched,
+ * filter failures, continued-fraction half-steps, sound-mode phase counts,
+ * records); *groups (may be NULL) = the number of groups. */
+tmd_status tmd_server_stats(tmd_server* server, tmd_stats* out, uint64_t* groups);
 
 /* Seconds on the server's clock (the clock of tmd_job_result). */
 double tmd_server_clock(tmd_server* server);

@@ -204,7 +204,7 @@ class Batch:
 
     def __init__(self, ctx: Context, jobs: Sequence, d_cand, d_count, stream=None, tiling=None):
         """tiling: None = the context's autotuned tiling for this batch
-        signature (else the default); or (nu, ctas_per_sm)."""
+        signature (else the default); or (nu, ctas_per_sm[, lanes[, unroll]])."""
         self.ctx = ctx
         self.jobs = list(jobs)
         self.d_cand, self.d_count = d_cand, d_count   # kept alive with the batch
@@ -216,7 +216,8 @@ class Batch:
                                          cap, _ptr(d_count), _stream_ptr(stream), ctypes.byref(h),
                                          ctypes.byref(up)), "tmd_batch_create")
         else:
-            t = _lib.tmd_tiling(int(tiling[0]), int(tiling[1]))
+            tl = list(tiling) + [0] * (4 - len(tiling))
+            t = _lib.tmd_tiling(int(tl[0]), int(tl[1]), int(tl[2]), int(tl[3]))
             check(lib().tmd_batch_create_tiled(ctx.handle, job_array(self.jobs), len(self.jobs), _ptr(d_cand),
                                                cap, _ptr(d_count), _stream_ptr(stream), ctypes.byref(t),
                                                ctypes.byref(h), ctypes.byref(up)), "tmd_batch_create_tiled")
@@ -224,10 +225,10 @@ class Batch:
         self.upload_bytes = up.value
 
     def tiling(self) -> tuple:
-        """(nu, ctas_per_sm) the batch was built with."""
+        """(nu, ctas_per_sm, lanes, unroll) the batch was built with."""
         t = _lib.tmd_tiling()
         check(lib().tmd_batch_tiling(self.handle, ctypes.byref(t)), "tmd_batch_tiling")
-        return (t.nu, t.ctas_per_sm)
+        return (t.nu, t.ctas_per_sm, t.lanes, t.unroll)
 
     def launch(self, stream=None):
         check(lib().tmd_batch_launch(self.handle, _stream_ptr(stream)), "tmd_batch_launch")
@@ -258,12 +259,12 @@ def tmd_batch_create(ctx: Context, jobs: Sequence, d_cand, d_count, stream=None,
 def tmd_autotune(ctx: Context, jobs: Sequence, stream=None) -> dict:
     """Time the batch under every candidate tiling; the fastest is kept in the
     context for batches of the same signature.  Returns {"nu", "ctas_per_sm",
-    "ms"}."""
+    "lanes", "unroll", "ms"}."""
     t = _lib.tmd_tiling()
     ms = ctypes.c_float(0.0)
     check(lib().tmd_autotune(ctx.handle, job_array(list(jobs)), len(jobs), _stream_ptr(stream),
                              ctypes.byref(t), ctypes.byref(ms)), "tmd_autotune")
-    return {"nu": t.nu, "ctas_per_sm": t.ctas_per_sm, "ms": ms.value}
+    return {"nu": t.nu, "ctas_per_sm": t.ctas_per_sm, "lanes": t.lanes, "unroll": t.unroll, "ms": ms.value}
 
 
 def tmd_batch_launch(batch: Batch, stream=None) -> None:
@@ -291,6 +292,23 @@ class Server:
 
     def submit(self, job, tag: int) -> None:
         check(lib().tmd_server_submit(self.handle, ctypes.byref(make_job(job)), int(tag)), "tmd_server_submit")
+
+    def submit_many(self, jobs: Sequence, tags: Sequence[int], delays_s: Sequence[float]) -> None:
+        """Queue jobs that arrive later: job i becomes eligible delays_s[i]
+        seconds after this call (server clock)."""
+        n = len(jobs)
+        ids = (ctypes.c_uint64 * max(1, n))(*[int(t) for t in tags])
+        dl = (ctypes.c_double * max(1, n))(*[float(d) for d in delays_s])
+        check(lib().tmd_server_submit_many(self.handle, job_array(list(jobs)), ids, dl, n),
+              "tmd_server_submit_many")
+
+    def stats(self) -> dict:
+        """Counters summed over the groups served so far."""
+        s = _lib.tmd_stats()
+        g = ctypes.c_uint64(0)
+        check(lib().tmd_server_stats(self.handle, ctypes.byref(s), ctypes.byref(g)), "tmd_server_stats")
+        return {"lines": s.lines, "filter_fail": s.filter_fail, "half_steps": s.half_steps, "count": s.count,
+                "exhaustive_args": s.exhaustive_args, "refined_args": s.refined_args, "groups": g.value}
 
     def poll(self, cap: int = 256, rec_cap: int = 1 << 16, wait_ms: int = 0):
         """[(result dict, [(job, subint, arg_index, value), ...]), ...]"""
@@ -385,7 +403,8 @@ def run(jobs: Sequence, ctx: Optional[Context] = None, fused: bool = True, cap: 
 
 def tmd_pipe_rates(device: int = 0) -> dict:
     """Measured lane-operations per SM per clock of 32-bit add, 3-input logic,
-    32-bit multiply-add and FP32 FMA chains, and the SM clock (MHz)."""
+    32-bit multiply-add and FP32 FMA chains, and the SM clock (MHz)
+    (libtmd_probe.so, include/tmd_probe.h)."""
     out = (ctypes.c_double * 5)()
-    check(lib().tmd_pipe_rates(int(device), out, 5), "tmd_pipe_rates")
+    check(_lib.probe_lib().tmd_pipe_rates(int(device), out, 5), "tmd_pipe_rates")
     return {"add_u32": out[0], "lop3": out[1], "mad_u32": out[2], "ffma": out[3], "sm_mhz": out[4]}

@@ -7,6 +7,7 @@ import os
 
 HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "libtmd.so")
+PROBE_PATH = os.path.join(HERE, "libtmd_probe.so")
 
 TMD_OK, TMD_EINVAL, TMD_ENOMEM, TMD_EOVERFLOW, TMD_ETIMEOUT, TMD_ECUDA, TMD_EUNSUPPORTED = range(7)
 TMD_EXP, TMD_EXP2, TMD_LOG = 0, 1, 2
@@ -67,7 +68,8 @@ class tmd_stats(ctypes.Structure):
 
 
 class tmd_tiling(ctypes.Structure):
-    _fields_ = [("nu", ctypes.c_uint32), ("ctas_per_sm", ctypes.c_uint32)]
+    _fields_ = [("nu", ctypes.c_uint32), ("ctas_per_sm", ctypes.c_uint32), ("lanes", ctypes.c_uint32),
+                ("unroll", ctypes.c_uint32)]
 
 
 _vp = ctypes.c_void_p
@@ -106,7 +108,6 @@ SIGNATURES = {
                                     ctypes.POINTER(ctypes.c_float)]),
     "tmd_batch_tiling": (ctypes.c_int, [_vp, ctypes.POINTER(tmd_tiling)]),
     "tmd_batch_launch": (ctypes.c_int, [_vp, _vp]),
-    "tmd_pipe_rates": (ctypes.c_int, [ctypes.c_int, ctypes.POINTER(ctypes.c_double), ctypes.c_int]),
     "tmd_batch_stats": (ctypes.c_int, [_vp, ctypes.POINTER(tmd_stats), _vp]),
     "tmd_batch_destroy": (ctypes.c_int, [_vp]),
     "tmd_search_static": (ctypes.c_int, [ctypes.POINTER(tmd_job), _u32, _vp, _u64, _vp, _vp]),
@@ -114,7 +115,10 @@ SIGNATURES = {
     "tmd_server_submit": (ctypes.c_int, [_vp, ctypes.POINTER(tmd_job), _u64]),
     "tmd_server_poll": (ctypes.c_int, [_vp, ctypes.POINTER(tmd_job_result), _u32, ctypes.POINTER(_u32),
                                        _vp, _u64, ctypes.POINTER(_u64), ctypes.c_int32]),
+    "tmd_server_submit_many": (ctypes.c_int, [_vp, ctypes.POINTER(tmd_job), ctypes.POINTER(_u64),
+                                              ctypes.POINTER(ctypes.c_double), _u32]),
     "tmd_server_pending": (ctypes.c_int, [_vp, ctypes.POINTER(_u64)]),
+    "tmd_server_stats": (ctypes.c_int, [_vp, ctypes.POINTER(tmd_stats), ctypes.POINTER(_u64)]),
     "tmd_server_clock": (ctypes.c_double, [_vp]),
     "tmd_server_destroy": (ctypes.c_int, [_vp]),
 }
@@ -136,6 +140,29 @@ def lib():
             f.argtypes = args
         _LIB = L
     return _LIB
+
+
+# the declarations of include/tmd_probe.h (libtmd_probe.so)
+PROBE_SIGNATURES = {
+    "tmd_pipe_rates": (ctypes.c_int, [ctypes.c_int, ctypes.POINTER(ctypes.c_double), ctypes.c_int]),
+}
+
+_PROBE = None
+
+
+def probe_lib():
+    """The loaded libtmd_probe.so (measurement support)."""
+    global _PROBE
+    if _PROBE is None:
+        if not os.path.exists(PROBE_PATH):
+            raise ImportError(f"{PROBE_PATH} is missing: build it with `python paper_1211_3056_gb300/build.py`")
+        L = ctypes.CDLL(PROBE_PATH)
+        for name, (res, args) in PROBE_SIGNATURES.items():
+            f = getattr(L, name)
+            f.restype = res
+            f.argtypes = args
+        _PROBE = L
+    return _PROBE
 
 
 def status_str(s: int) -> str:

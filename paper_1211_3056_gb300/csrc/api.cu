@@ -28,7 +28,8 @@ cudaError_t launch_persistent(uint32_t L, uint32_t D, bool G, const LaunchArgs& 
 cudaError_t persistent_occupancy(uint32_t L, uint32_t D, bool G, int* blocks_per_sm);
 cudaError_t upload_coeff_consts(const CoeffConsts& C);
 cudaError_t launch_block_tables(const DevJob* jobs, const DevBlock* blocks, uint64_t n_blocks, uint64_t* tables,
-                                uint32_t* status, uint32_t* err, cudaStream_t s);
+                                uint32_t* status, uint32_t* err, const uint64_t* ctab, cudaStream_t s);
+cudaError_t launch_coeff_tables(uint64_t* ctab, uint32_t* err, cudaStream_t s);
 cudaError_t launch_plan(const DevJob* jobs, uint32_t n_jobs, DevBlock* blocks, uint64_t n_blocks,
                         const uint32_t* class_jobs, const uint64_t* class_task0, uint32_t n_entries,
                         DevTask* tasks, uint64_t n_tasks, cudaStream_t s);
@@ -92,6 +93,8 @@ struct tmd_ctx {
     size_t off_jobs = 0, off_blocks = 0, off_tables = 0, off_tasks = 0;
     // counters: stats[5] u64, err u32, queue head u32
     uint64_t* d_misc = nullptr;
+    // tables of the table-driven exp and 2^x enclosures (CT_WORDS words)
+    uint64_t* d_ctab = nullptr;
     // pinned staging for uploads
     char* h_stage = nullptr;
     size_t stage_cap = 0;
@@ -385,7 +388,8 @@ void pack_plan(const Plan& P, const Layout& L, char* dst) {
 }
 
 // after the upload: blocks, tasks and tables on the device (unless host mode)
-cudaError_t expand_plan(const Plan& P, const Layout& L, char* d_arena, uint32_t* plan_err, cudaStream_t s) {
+cudaError_t expand_plan(const Plan& P, const Layout& L, char* d_arena, uint32_t* plan_err, const uint64_t* ctab,
+                        cudaStream_t s) {
     if (P.host_tables) return cudaSuccess;
     cudaError_t e = launch_plan((const DevJob*)d_arena, (uint32_t)P.jobs.size(), (DevBlock*)(d_arena + L.o_blocks),
                                 P.n_blocks, (const uint32_t*)(d_arena + L.o_cjobs),
@@ -393,7 +397,8 @@ cudaError_t expand_plan(const Plan& P, const Layout& L, char* d_arena, uint32_t*
                                 (DevTask*)(d_arena + L.o_tasks), P.n_tasks, s);
     if (e != cudaSuccess) return e;
     return launch_block_tables((const DevJob*)d_arena, (const DevBlock*)(d_arena + L.o_blocks), P.n_blocks,
-                               (uint64_t*)(d_arena + L.o_tables), (uint32_t*)(d_arena + L.o_status), plan_err, s);
+                               (uint64_t*)(d_arena + L.o_tables), (uint32_t*)(d_arena + L.o_status), plan_err, ctab,
+                               s);
 }
 
 // Arena layout: jobs | blocks | tasks | table status | tables.  The first
@@ -431,7 +436,7 @@ tmd_status upload_plan(tmd_ctx* c, cudaStream_t s) {
     c->off_tables = Lo.o_tables;
     c->off_tasks = Lo.o_tasks;
     CK(cudaMemsetAsync(plan_err_ptr(c), 0, sizeof(uint32_t), s));
-    CK(expand_plan(P, Lo, c->d_arena, plan_err_ptr(c), s));
+    CK(expand_plan(P, Lo, c->d_arena, plan_err_ptr(c), c->d_ctab, s));
     return TMD_OK;
 }
 
@@ -508,6 +513,19 @@ tmd_status tmd_create(tmd_ctx** out, int device) {
         tmd_destroy(c);
         return TMD_ECUDA;
     }
+    // the exp and 2^x tables of the block-table kernel, built once per context
+    uint32_t terr = 0;
+    if (cudaMalloc((void**)&c->d_ctab, CT_WORDS * sizeof(uint64_t)) != cudaSuccess ||
+        launch_coeff_tables(c->d_ctab, plan_err_ptr(c), nullptr) != cudaSuccess ||
+        cudaMemcpy(&terr, plan_err_ptr(c), sizeof terr, cudaMemcpyDeviceToHost) != cudaSuccess ||
+        cudaMemset(plan_err_ptr(c), 0, sizeof(uint32_t)) != cudaSuccess) {
+        tmd_destroy(c);
+        return TMD_ECUDA;
+    }
+    if (terr) {
+        tmd_destroy(c);
+        return TMD_EUNSUPPORTED;
+    }
     *out = c;
     return TMD_OK;
 }
@@ -518,6 +536,7 @@ tmd_status tmd_destroy(tmd_ctx* c) {
     if (c->stage_pending) cudaEventSynchronize(c->stage_done);
     if (c->d_arena) cudaFree(c->d_arena);
     if (c->d_misc) cudaFree(c->d_misc);
+    if (c->d_ctab) cudaFree(c->d_ctab);
     if (c->h_stage) cudaFreeHost(c->h_stage);
     if (c->stage_done) cudaEventDestroy(c->stage_done);
     delete c;
@@ -761,7 +780,7 @@ struct tmd_batch {
     cudaStream_t cap_stream = nullptr;
     uint64_t upload_bytes = 0;
     const uint64_t* d_count = nullptr;
-    tmd_tiling tiling = {0, 0};
+    tmd_tiling tiling = {0, 0, 0, 0};
 };
 
 namespace {
@@ -807,7 +826,7 @@ tmd_status tmd_batch_create(tmd_ctx* c, const tmd_job* jobs, uint32_t njobs, tmd
                             uint64_t cand_cap, uint64_t* d_count, void* stream, tmd_batch** out,
                             uint64_t* upload_bytes) {
     if (!c || !jobs || njobs == 0 || !d_count || !out || (cand_cap && !d_cand)) return TMD_EINVAL;
-    tmd_tiling t = {0, 0};
+    tmd_tiling t = {0, 0, 0, 0};
     {
         std::lock_guard<std::mutex> lk(c->tune_mu);
         auto it = c->tuned.find(tiling_key(jobs, njobs, c->sms));
@@ -820,8 +839,8 @@ tmd_status tmd_batch_create_tiled(tmd_ctx* c, const tmd_job* jobs, uint32_t njob
                                   uint64_t cand_cap, uint64_t* d_count, void* stream, const tmd_tiling* tiling,
                                   tmd_batch** out, uint64_t* upload_bytes) {
     if (!c || !jobs || njobs == 0 || !d_count || !out || (cand_cap && !d_cand)) return TMD_EINVAL;
-    tmd_tiling t = tiling ? *tiling : tmd_tiling{0, 0};
-    if (t.nu > 8 || t.ctas_per_sm > 64) return TMD_EINVAL;
+    tmd_tiling t = tiling ? *tiling : tmd_tiling{0, 0, 0, 0};
+    if (t.nu > 8 || t.ctas_per_sm > 64 || t.lanes == 3 || t.lanes > 4 || t.unroll > 2) return TMD_EINVAL;
     return batch_create(c, jobs, njobs, d_cand, cand_cap, d_count, stream, t, out, upload_bytes);
 }
 
@@ -849,12 +868,23 @@ tmd_status tmd_autotune(tmd_ctx* c, const tmd_job* jobs, uint32_t njobs, void* s
         return TMD_ECUDA;
     }
     tmd_status st = TMD_OK;
-    tmd_tiling win = {0, 0};
+    tmd_tiling win = {0, 0, 0, 0};
     float win_ms = 0.f;
+    // stage 1: packet length x resident CTAs (one lane per line, one step
+    // per iteration); stage 2: lanes per line x steps per iteration for the
+    // stage-1 winner
+    std::vector<tmd_tiling> cands;
     static const uint32_t nus[] = {8, 6, 4, 2, 1};
-    for (uint32_t nu : nus) {
-        for (int k = occ; k >= 1 && st == TMD_OK; k--) {
-            const tmd_tiling t = {nu, (uint32_t)k};
+    for (uint32_t nu : nus)
+        for (int k = occ; k >= 1; k--) cands.push_back(tmd_tiling{nu, (uint32_t)k, 1, 1});
+    const size_t stage1 = cands.size();
+    for (size_t ci = 0; ci < cands.size() && st == TMD_OK; ci++) {
+        if (ci == stage1) {
+            static const uint32_t lanes_unroll[][2] = {{1, 2}, {2, 1}, {2, 2}, {4, 1}, {4, 2}};
+            for (const auto& lu : lanes_unroll) cands.push_back(tmd_tiling{win.nu, win.ctas_per_sm, lu[0], lu[1]});
+        }
+        {
+            const tmd_tiling t = cands[ci];
             tmd_batch* b = nullptr;
             st = batch_create(c, jobs, njobs, nullptr, 0, d_cnt, stream, t, &b, nullptr);
             if (st != TMD_OK) break;
@@ -875,7 +905,6 @@ tmd_status tmd_autotune(tmd_ctx* c, const tmd_job* jobs, uint32_t njobs, void* s
                 win_ms = ms;
             }
         }
-        if (st != TMD_OK) break;
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
@@ -927,7 +956,7 @@ tmd_status batch_create(tmd_ctx* c, const tmd_job* jobs, uint32_t njobs, tmd_can
         return TMD_ECUDA;
     }
     plan_err = (uint32_t*)(b->d_misc + ST_COUNT) + 2;
-    if (expand_plan(P, Lo, b->d_arena, plan_err, s) != cudaSuccess ||
+    if (expand_plan(P, Lo, b->d_arena, plan_err, c->d_ctab, s) != cudaSuccess ||
         cudaMemcpyAsync(&perr, plan_err, sizeof perr, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
         cudaStreamSynchronize(s) != cudaSuccess) {
         batch_free(b);
@@ -954,6 +983,10 @@ tmd_status batch_create(tmd_ctx* c, const tmd_job* jobs, uint32_t njobs, tmd_can
     a.cap = cand_cap;
     a.count = d_count;
     a.stats = b->d_misc;
+    a.lanes = tiling.lanes;
+    a.unroll = tiling.unroll;
+    b->tiling.lanes = tiling.lanes ? tiling.lanes : 1;
+    b->tiling.unroll = tiling.unroll ? tiling.unroll : 1;
     if (cudaStreamCreateWithFlags(&b->cap_stream, cudaStreamNonBlocking) != cudaSuccess ||
         cudaStreamBeginCapture(b->cap_stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
         batch_free(b);
@@ -1035,15 +1068,28 @@ tmd_status tmd_batch_destroy(tmd_batch* b) {
 }  // extern "C"
 
 // ------------------------------------------------------------ serving loop
+//
+// Continuous batching.  A host worker thread admits the jobs that have
+// arrived (in arrival order, up to max_batch at a time, while their plans fit
+// the device budget) into a free slot as one group: it plans the group on the
+// host, uploads its job records and enqueues on the slot's stream the device
+// planning, the correctly rounded tables, one fused search launch per kernel
+// class and the read-back of the group's count.  A stream callback hands the
+// slot back to the worker, which reads the records (if any) and splits them
+// into per-job results.  While one group runs on the device the worker plans
+// and launches the next in another slot, and the fused launches of the slots
+// share the SMs.  Jobs may be submitted with an arrival time in the future
+// (tmd_server_submit_many), so that a recorded or generated arrival stream is
+// replayed by the server's clock without a host loop in between.
 
 namespace {
 
 struct ServerJob {
     tmd_job job;
     uint64_t id;
-    double t_submit;
-    size_t est;      // plan bytes estimate (for the device budget)
-    bool solo;       // re-run alone after its group overflowed the records
+    double t_submit;  // arrival time on the server clock
+    size_t est;       // plan bytes estimate (for the device budget)
+    bool solo;        // re-run alone after its group overflowed the records
 };
 
 struct ServerResult {
@@ -1056,25 +1102,27 @@ enum { META_BYTES = 128, META_COUNT_OFF = 64 };
 
 // One resident group of jobs: its stream, plan arena, records and counters.
 struct Slot {
+    enum State { FREE, RUNNING, READING };
     cudaStream_t stream = nullptr;
-    cudaEvent_t done = nullptr;
     char* d_arena = nullptr;
     size_t arena_cap = 0;
     tmd_candidate* d_cand = nullptr;
     char* d_meta = nullptr;
     char* h_stage = nullptr;
     size_t stage_cap = 0;
-    char* h_meta = nullptr;       // pinned copy of the meta block
-    bool busy = false;
-    bool all_launched = false;
+    char* h_meta = nullptr;          // pinned copy of the meta block
+    tmd_candidate* h_recs = nullptr;  // pinned records (cand_cap)
+    State state = FREE;
     std::vector<ServerJob> sjs;
     std::vector<tmd_job> jobs;
     double t_start = 0;
     Plan plan;
     size_t plan_bytes = 0;
-    size_t off_blocks = 0, off_tasks = 0, off_tables = 0;
-    size_t class_idx = 0;
-    uint64_t class_pos = 0;
+    uint64_t count = 0, n_read = 0;
+    tmd_status status = TMD_OK;
+    // stream-callback argument (stable address: slots are never resized)
+    void* server = nullptr;
+    int index = 0;
 };
 
 }  // namespace
@@ -1085,13 +1133,17 @@ struct tmd_server {
     std::thread worker;
     std::mutex mu;
     std::condition_variable cv_work, cv_done;
-    std::deque<ServerJob> pending;
+    std::deque<ServerJob> pending;                 // arrived, in arrival order
+    std::multimap<double, ServerJob> future;       // arrival time -> job
+    std::deque<int> events;                        // slots whose stream reached a callback
     std::deque<ServerResult> finished;
     std::vector<Slot> slots;
     size_t budget_used = 0;
     uint64_t outstanding = 0;
     bool stop = false;
     std::chrono::steady_clock::time_point t0;
+    // totals over the finished groups (tmd_server_stats)
+    uint64_t st_lines = 0, st_fail = 0, st_half = 0, st_exh = 0, st_ref = 0, st_groups = 0, st_count = 0;
 };
 
 namespace {
@@ -1108,7 +1160,18 @@ size_t plan_estimate(const tmd_job& job) {
            (size_t)(ns / 8 / 32 + nb + 1) * sizeof(DevTask) + 4096;
 }
 
-// plan, upload (plan records and zeroed counters) and table kernel of a group
+void CUDART_CB slot_callback(void* arg) {
+    Slot* sl = (Slot*)arg;
+    tmd_server* S = (tmd_server*)sl->server;
+    {
+        std::lock_guard<std::mutex> lk(S->mu);
+        S->events.push_back(sl->index);
+    }
+    S->cv_work.notify_one();
+}
+
+// plan, upload, device planning and tables, fused search launches and the
+// read-back of the meta block of a group, all enqueued on the slot's stream
 tmd_status slot_start(tmd_server* S, Slot& sl) {
     sl.t_start = server_now(S);
     sl.jobs.clear();
@@ -1117,67 +1180,48 @@ tmd_status slot_start(tmd_server* S, Slot& sl) {
     if (st != TMD_OK) return st;
     Plan& P = sl.plan;
     const Layout Lo = plan_layout(P);
-    const size_t o_blocks = Lo.o_blocks, o_tasks = Lo.o_tasks, o_tables = Lo.o_tables, total = Lo.total;
-    if (total > sl.arena_cap) {
+    if (Lo.total > sl.arena_cap) {
         if (sl.d_arena) CK(cudaFreeAsync(sl.d_arena, sl.stream));
         sl.d_arena = nullptr;
-        CK(cudaMallocAsync((void**)&sl.d_arena, total, sl.stream));
-        sl.arena_cap = total;
+        const size_t cap = std::max(Lo.total, sl.arena_cap + sl.arena_cap / 2);
+        CK(cudaMallocAsync((void**)&sl.d_arena, cap, sl.stream));
+        sl.arena_cap = cap;
     }
     if (Lo.upload > sl.stage_cap) {
         CK(cudaStreamSynchronize(sl.stream));
         if (sl.h_stage) CK(cudaFreeHost(sl.h_stage));
         sl.h_stage = nullptr;
-        CK(cudaHostAlloc((void**)&sl.h_stage, Lo.upload, cudaHostAllocDefault));
-        sl.stage_cap = Lo.upload;
+        const size_t cap = std::max(Lo.upload, sl.stage_cap * 2);
+        CK(cudaHostAlloc((void**)&sl.h_stage, cap, cudaHostAllocDefault));
+        sl.stage_cap = cap;
     }
     pack_plan(P, Lo, sl.h_stage);
     CK(cudaMemcpyAsync(sl.d_arena, sl.h_stage, Lo.upload, cudaMemcpyHostToDevice, sl.stream));
     CK(cudaMemsetAsync(sl.d_meta, 0, META_BYTES, sl.stream));
     uint32_t* perr = (uint32_t*)(sl.d_meta + sizeof(uint64_t) * ST_COUNT) + 2;
-    CK(expand_plan(P, Lo, sl.d_arena, perr, sl.stream));
-    sl.off_blocks = o_blocks;
-    sl.off_tasks = o_tasks;
-    sl.off_tables = o_tables;
-    sl.plan_bytes = total;
-    sl.class_idx = 0;
-    sl.class_pos = 0;
-    sl.all_launched = false;
-    return TMD_OK;
-}
-
-// launch the next chunk of warp tasks of a slot; after the last one, queue
-// the read-back of the meta block and record the done event
-tmd_status slot_launch_chunk(tmd_server* S, Slot& sl) {
-    Plan& P = sl.plan;
-    const uint64_t chunk = S->cfg.chunk_tasks;
-    if (sl.class_idx < P.classes.size()) {
-        const ClassRange& cr = P.classes[sl.class_idx];
-        const uint64_t n = std::min<uint64_t>(chunk, cr.count - sl.class_pos);
-        LaunchArgs a;
-        memset(&a, 0, sizeof a);
-        a.jobs = (const DevJob*)sl.d_arena;
-        a.blocks = (const DevBlock*)(sl.d_arena + sl.off_blocks);
-        a.tables = (const uint64_t*)(sl.d_arena + sl.off_tables);
-        a.tasks = (const DevTask*)(sl.d_arena + sl.off_tasks) + cr.first + sl.class_pos;
-        a.n_tasks = n;
-        a.cand = sl.d_cand;
-        a.cap = S->cfg.cand_cap;
-        a.count = (uint64_t*)(sl.d_meta + META_COUNT_OFF);
-        a.stats = (uint64_t*)sl.d_meta;
-        a.queue_head = (uint32_t*)(sl.d_meta + sizeof(uint64_t) * ST_COUNT) + 1;
-        CK(launch_tasks(true, cr.L, cr.D, cr.G, a, sl.stream));
-        sl.class_pos += n;
-        if (sl.class_pos >= cr.count) {
-            sl.class_idx++;
-            sl.class_pos = 0;
+    CK(expand_plan(P, Lo, sl.d_arena, perr, S->ctx->d_ctab, sl.stream));
+    LaunchArgs a;
+    memset(&a, 0, sizeof a);
+    a.jobs = (const DevJob*)sl.d_arena;
+    a.blocks = (const DevBlock*)(sl.d_arena + Lo.o_blocks);
+    a.tables = (const uint64_t*)(sl.d_arena + Lo.o_tables);
+    a.cand = sl.d_cand;
+    a.cap = S->cfg.cand_cap;
+    a.count = (uint64_t*)(sl.d_meta + META_COUNT_OFF);
+    a.stats = (uint64_t*)sl.d_meta;
+    a.queue_head = (uint32_t*)(sl.d_meta + sizeof(uint64_t) * ST_COUNT) + 1;
+    const uint64_t chunk = S->cfg.chunk_tasks ? S->cfg.chunk_tasks : ~0ull;
+    for (const ClassRange& cr : P.classes) {
+        for (uint64_t pos = 0; pos < cr.count; pos += chunk) {
+            LaunchArgs la = a;
+            la.tasks = (const DevTask*)(sl.d_arena + Lo.o_tasks) + cr.first + pos;
+            la.n_tasks = std::min<uint64_t>(chunk, cr.count - pos);
+            CK(launch_tasks(true, cr.L, cr.D, cr.G, la, sl.stream));
         }
     }
-    if (sl.class_idx >= P.classes.size()) {
-        CK(cudaMemcpyAsync(sl.h_meta, sl.d_meta, META_BYTES, cudaMemcpyDeviceToHost, sl.stream));
-        CK(cudaEventRecord(sl.done, sl.stream));
-        sl.all_launched = true;
-    }
+    CK(cudaMemcpyAsync(sl.h_meta, sl.d_meta, META_BYTES, cudaMemcpyDeviceToHost, sl.stream));
+    CK(cudaLaunchHostFunc(sl.stream, slot_callback, &sl));
+    sl.state = Slot::RUNNING;
     return TMD_OK;
 }
 
@@ -1186,31 +1230,17 @@ void slot_release(tmd_server* S, Slot& sl) {
         std::lock_guard<std::mutex> lk(S->mu);
         S->budget_used -= sl.plan_bytes;
     }
-    sl.busy = false;
+    sl.state = Slot::FREE;
     sl.sjs.clear();
     sl.plan_bytes = 0;
 }
 
-// read back a finished group and split it into per-job results; a group
-// whose records overflowed goes back to the queue front job by job
-void slot_finish(tmd_server* S, Slot& sl, tmd_status st) {
+// the group's results, split per job; a group whose records overflowed goes
+// back to the queue front job by job
+void slot_finish(tmd_server* S, Slot& sl) {
     const double t_done = server_now(S);
-    uint64_t count = 0;
-    std::vector<tmd_candidate> recs;
-    if (st == TMD_OK) {
-        const uint32_t* err = (const uint32_t*)(sl.h_meta + sizeof(uint64_t) * ST_COUNT);
-        count = *(const uint64_t*)(sl.h_meta + META_COUNT_OFF);
-        if (err[2]) {
-            st = TMD_EUNSUPPORTED;
-        } else {
-            const uint64_t n = std::min<uint64_t>(count, S->cfg.cand_cap);
-            recs.resize(n);
-            if (n && (cudaMemcpyAsync(recs.data(), sl.d_cand, n * sizeof(tmd_candidate), cudaMemcpyDeviceToHost,
-                                      sl.stream) != cudaSuccess ||
-                      cudaStreamSynchronize(sl.stream) != cudaSuccess))
-                st = TMD_ECUDA;
-        }
-    }
+    tmd_status st = sl.status;
+    const uint64_t count = sl.count;
     const bool overflow = st == TMD_OK && count > S->cfg.cand_cap;
     if (overflow && sl.sjs.size() > 1) {
         std::vector<ServerJob> again = sl.sjs;
@@ -1222,6 +1252,7 @@ void slot_finish(tmd_server* S, Slot& sl, tmd_status st) {
         }
         return;
     }
+    std::vector<tmd_candidate> recs(sl.h_recs, sl.h_recs + (st == TMD_OK ? sl.n_read : 0));
     std::sort(recs.begin(), recs.end(), [](const tmd_candidate& a, const tmd_candidate& b) {
         if (a.job != b.job) return a.job < b.job;
         if (a.arg_index != b.arg_index) return a.arg_index < b.arg_index;
@@ -1253,33 +1284,73 @@ void slot_finish(tmd_server* S, Slot& sl, tmd_status st) {
     S->cv_done.notify_all();
 }
 
+// a slot's stream reached its callback: the meta block (count, counters,
+// plan error) is on the host, or, in the READING state, the records
+void slot_event(tmd_server* S, Slot& sl) {
+    if (sl.state == Slot::RUNNING) {
+        const uint64_t* h = (const uint64_t*)sl.h_meta;
+        const uint32_t* err = (const uint32_t*)(sl.h_meta + sizeof(uint64_t) * ST_COUNT);
+        sl.count = *(const uint64_t*)(sl.h_meta + META_COUNT_OFF);
+        sl.status = err[2] ? TMD_EUNSUPPORTED : TMD_OK;
+        {
+            std::lock_guard<std::mutex> lk(S->mu);
+            S->st_lines += h[ST_LINES];
+            S->st_fail += h[ST_FAIL];
+            S->st_half += h[ST_HALF];
+            S->st_exh += h[ST_EXH];
+            S->st_ref += h[ST_REF];
+            S->st_groups += 1;
+            S->st_count += sl.count;
+        }
+        const bool rerun = sl.status == TMD_OK && sl.count > S->cfg.cand_cap && sl.sjs.size() > 1;
+        sl.n_read = sl.status == TMD_OK && !rerun ? std::min<uint64_t>(sl.count, S->cfg.cand_cap) : 0;
+        if (sl.n_read) {
+            if (cudaMemcpyAsync(sl.h_recs, sl.d_cand, sl.n_read * sizeof(tmd_candidate), cudaMemcpyDeviceToHost,
+                                sl.stream) != cudaSuccess ||
+                cudaLaunchHostFunc(sl.stream, slot_callback, &sl) != cudaSuccess) {
+                cudaStreamSynchronize(sl.stream);
+                sl.status = TMD_ECUDA;
+                slot_finish(S, sl);
+                return;
+            }
+            sl.state = Slot::READING;
+            return;
+        }
+    }
+    slot_finish(S, sl);
+}
+
 void server_loop(tmd_server* S) {
     cudaSetDevice(S->ctx->device);
+    std::vector<int> evs;
     for (;;) {
-        bool progress = false;
-        for (Slot& sl : S->slots) {
-            if (sl.busy && sl.all_launched && cudaEventQuery(sl.done) == cudaSuccess) {
-                slot_finish(S, sl, TMD_OK);
-                progress = true;
+        evs.clear();
+        bool any_busy = false;
+        {
+            std::unique_lock<std::mutex> lk(S->mu);
+            const double now = server_now(S);
+            while (!S->future.empty() && S->future.begin()->first <= now) {
+                S->pending.push_back(S->future.begin()->second);
+                S->future.erase(S->future.begin());
+            }
+            evs.assign(S->events.begin(), S->events.end());
+            S->events.clear();
+            for (const Slot& sl : S->slots) any_busy |= sl.state != Slot::FREE;
+            if (S->stop) {
+                S->pending.clear();
+                S->future.clear();
+                if (!any_busy && evs.empty()) break;
             }
         }
+        bool progress = !evs.empty();
+        for (int i : evs) slot_event(S, S->slots[(size_t)i]);
+        // admission: the oldest arrived jobs, up to max_batch, while they fit
         for (Slot& sl : S->slots) {
-            if (sl.busy && !sl.all_launched) {
-                if (slot_launch_chunk(S, sl) != TMD_OK) {
-                    cudaStreamSynchronize(sl.stream);
-                    slot_finish(S, sl, TMD_ECUDA);
-                }
-                progress = true;
-            }
-        }
-        // admission: the oldest waiting jobs, up to max_batch, while they fit
-        for (Slot& sl : S->slots) {
-            if (sl.busy) continue;
-            size_t take = 0;
+            if (sl.state != Slot::FREE) continue;
+            size_t take = 0, bytes = 0;
             {
                 std::unique_lock<std::mutex> lk(S->mu);
                 if (S->pending.empty()) break;
-                size_t bytes = 0;
                 while (take < S->pending.size() && take < S->cfg.max_batch) {
                     const ServerJob& sj = S->pending[take];
                     if (take > 0 && (sj.solo || S->pending[0].solo)) break;
@@ -1292,33 +1363,35 @@ void server_loop(tmd_server* S) {
                 sl.sjs.assign(S->pending.begin(), S->pending.begin() + (long)take);
                 S->pending.erase(S->pending.begin(), S->pending.begin() + (long)take);
                 S->budget_used += bytes;
-                sl.plan_bytes = bytes;
             }
-            sl.busy = true;
-            const size_t est = sl.plan_bytes;
-            tmd_status st = slot_start(S, sl);
-            {
-                std::lock_guard<std::mutex> lk(S->mu);
-                S->budget_used += sl.plan_bytes;
-                S->budget_used -= est;
-            }
-            if (st != TMD_OK) {
+            sl.plan_bytes = bytes;
+            sl.status = TMD_OK;
+            sl.count = sl.n_read = 0;
+            if (slot_start(S, sl) != TMD_OK) {
                 cudaStreamSynchronize(sl.stream);
-                slot_finish(S, sl, st);
+                sl.status = TMD_ECUDA;
+                slot_finish(S, sl);
             }
             progress = true;
         }
-        bool any_busy = false;
-        for (Slot& sl : S->slots) any_busy |= sl.busy;
+        if (progress) continue;
         std::unique_lock<std::mutex> lk(S->mu);
-        if (S->stop && !any_busy) break;
-        if (!progress) {
-            if (!any_busy && S->pending.empty())
-                S->cv_work.wait_for(lk, std::chrono::milliseconds(50));
-            else
-                S->cv_work.wait_for(lk, std::chrono::microseconds(20));
+        if (!S->events.empty()) continue;
+        if (S->stop) {
+            if (any_busy) S->cv_work.wait_for(lk, std::chrono::milliseconds(50));
+            continue;
         }
-        if (S->stop) S->pending.clear();
+        bool can_admit = !S->pending.empty();
+        if (can_admit) {
+            can_admit = false;
+            for (const Slot& sl : S->slots) can_admit |= sl.state == Slot::FREE;
+        }
+        if (can_admit) continue;
+        // sleep until a callback, a submission, or the next scheduled arrival
+        double wait_s = 0.05;
+        if (!S->future.empty()) wait_s = std::min(wait_s, std::max(0.0, S->future.begin()->first - server_now(S)));
+        if (wait_s > 0)
+            S->cv_work.wait_for(lk, std::chrono::duration<double>(wait_s));
     }
 }
 
@@ -1334,10 +1407,9 @@ tmd_status tmd_server_create(tmd_ctx* c, const tmd_server_config* cfg, tmd_serve
     if (cfg) k = *cfg;
     if (k.reserved != 0) return TMD_EINVAL;
     if (k.device_budget == 0) k.device_budget = 1ull << 30;
-    if (k.max_inflight == 0) k.max_inflight = 8;
-    if (k.chunk_tasks == 0) k.chunk_tasks = 2048;
+    if (k.max_inflight == 0) k.max_inflight = 4;
     if (k.cand_cap == 0) k.cand_cap = 65536;
-    if (k.max_batch == 0) k.max_batch = 32;
+    if (k.max_batch == 0) k.max_batch = 1024;
     if (k.max_inflight > 64) return TMD_EINVAL;
     CK(cudaSetDevice(c->device));
     tmd_server* S = new tmd_server();
@@ -1345,12 +1417,16 @@ tmd_status tmd_server_create(tmd_ctx* c, const tmd_server_config* cfg, tmd_serve
     S->cfg = k;
     S->t0 = std::chrono::steady_clock::now();
     S->slots.resize(k.max_inflight);
-    for (Slot& sl : S->slots) {
+    for (size_t i = 0; i < S->slots.size(); i++) {
+        Slot& sl = S->slots[i];
+        sl.server = S;
+        sl.index = (int)i;
         if (cudaStreamCreateWithFlags(&sl.stream, cudaStreamNonBlocking) != cudaSuccess ||
-            cudaEventCreateWithFlags(&sl.done, cudaEventDisableTiming) != cudaSuccess ||
             cudaMalloc((void**)&sl.d_cand, k.cand_cap * sizeof(tmd_candidate)) != cudaSuccess ||
             cudaMalloc((void**)&sl.d_meta, META_BYTES) != cudaSuccess ||
-            cudaHostAlloc((void**)&sl.h_meta, META_BYTES, cudaHostAllocDefault) != cudaSuccess) {
+            cudaHostAlloc((void**)&sl.h_meta, META_BYTES, cudaHostAllocDefault) != cudaSuccess ||
+            cudaHostAlloc((void**)&sl.h_recs, k.cand_cap * sizeof(tmd_candidate), cudaHostAllocDefault) !=
+                cudaSuccess) {
             tmd_server_destroy(S);
             return TMD_ECUDA;
         }
@@ -1370,6 +1446,30 @@ tmd_status tmd_server_submit(tmd_server* S, const tmd_job* job, uint64_t id) {
         if (S->stop) return TMD_EINVAL;
         S->pending.push_back(ServerJob{*job, id, server_now(S), est, false});
         S->outstanding++;
+    }
+    S->cv_work.notify_one();
+    return TMD_OK;
+}
+
+tmd_status tmd_server_submit_many(tmd_server* S, const tmd_job* jobs, const uint64_t* ids,
+                                  const double* delays_s, uint32_t n) {
+    if (!S || (n && (!jobs || !ids || !delays_s))) return TMD_EINVAL;
+    std::vector<size_t> est(n);
+    for (uint32_t i = 0; i < n; i++) {
+        if (!(delays_s[i] >= 0.0)) return TMD_EINVAL;
+        tmd_status st = validate_job(jobs[i]);
+        if (st != TMD_OK) return st;
+        est[i] = plan_estimate(jobs[i]);
+    }
+    {
+        std::lock_guard<std::mutex> lk(S->mu);
+        if (S->stop) return TMD_EINVAL;
+        const double now = server_now(S);
+        for (uint32_t i = 0; i < n; i++) {
+            const double t = now + delays_s[i];
+            S->future.emplace(t, ServerJob{jobs[i], ids[i], t, est[i], false});
+        }
+        S->outstanding += n;
     }
     S->cv_work.notify_one();
     return TMD_OK;
@@ -1408,6 +1508,21 @@ tmd_status tmd_server_pending(tmd_server* S, uint64_t* n) {
     return TMD_OK;
 }
 
+tmd_status tmd_server_stats(tmd_server* S, tmd_stats* out, uint64_t* groups) {
+    if (!S || !out) return TMD_EINVAL;
+    std::lock_guard<std::mutex> lk(S->mu);
+    memset(out, 0, sizeof *out);
+    out->lines = S->st_lines;
+    out->filter_fail = S->st_fail;
+    out->candidates = S->st_count;
+    out->half_steps = S->st_half;
+    out->count = S->st_count;
+    out->exhaustive_args = S->st_exh;
+    out->refined_args = S->st_ref;
+    if (groups) *groups = S->st_groups;
+    return TMD_OK;
+}
+
 double tmd_server_clock(tmd_server* S) { return S ? server_now(S) : 0.0; }
 
 tmd_status tmd_server_destroy(tmd_server* S) {
@@ -1427,7 +1542,7 @@ tmd_status tmd_server_destroy(tmd_server* S) {
         if (sl.d_meta) cudaFree(sl.d_meta);
         if (sl.h_stage) cudaFreeHost(sl.h_stage);
         if (sl.h_meta) cudaFreeHost(sl.h_meta);
-        if (sl.done) cudaEventDestroy(sl.done);
+        if (sl.h_recs) cudaFreeHost(sl.h_recs);
         if (sl.stream) cudaStreamDestroy(sl.stream);
     }
     delete S;

@@ -78,16 +78,20 @@ TMD_HD void rn_shift(fx::U<NL>& x, unsigned s) {
     fx::shr(x, s);
 }
 
+// the low L limbs of x (or of -x) into out[0 .. L), out[L .. COEFF_MAX_LIMBS)
+// zeroed: every slot is written with a constant index, so that an array of
+// coefficients in registers stays there
 template <int NL>
 TMD_HD void store_mod_w(const fx::U<NL>& x, bool neg, int L, uint64_t* out) {
     uint64_t c = 1;
-    for (int l = 0; l < L; l++) {
-        uint64_t w = x.w[l];
+#pragma unroll
+    for (int l = 0; l < COEFF_MAX_LIMBS; l++) {
+        uint64_t w = l < NL ? x.w[l < NL ? l : 0] : 0;
         if (neg) {
             w = ~w + c;
             c = (w == 0 && c) ? 1 : 0;
         }
-        out[l] = w;
+        out[l] = l < L ? w : 0;
     }
 }
 
@@ -193,6 +197,55 @@ TMD_HD bool exp_reduced(const CoeffJob& J, uint64_t M, unsigned PB, const CoeffC
     return true;
 }
 
+// Tables of the device path for exp and 2^x: entry (base, level i, b) is an
+// enclosure of base^(b 2^(-8 i)), i = 1..10, b < 256 (base 0: e, base 1: 2),
+// and level 0 of base e holds e^n, n < 4; lo and hi ends of CT_LIMBS limbs
+// with CT_BITS fractional bits.  An argument X = n + sum_i b_i 2^(-8 i) with
+// at most 80 fractional bits then has e^X (2^X) as the product of at most 11
+// entries (2^n exact), with no series per block (the table-driven method of
+// Tang's exponential, here with rigorous enclosures at every step).
+enum { CT_LEVELS = 11, CT_ENTRIES = 256, CT_LIMBS = 12, CT_BITS = 64 * CT_LIMBS - 68 };
+
+TMD_HD size_t ct_index(int base, int level, int b, int end) {
+    return ((((size_t)base * CT_LEVELS + (size_t)level) * CT_ENTRIES + (size_t)b) * 2 + (size_t)end) * CT_LIMBS;
+}
+
+constexpr size_t CT_WORDS = 2 * CT_LEVELS * CT_ENTRIES * 2 * CT_LIMBS;
+
+// Entry (base, level, b) of the tables at CT_BITS fractional bits; false if
+// an enclosure fails (it does not for the supported ranges).
+TMD_HD bool ct_entry(int base, int level, int b, const CoeffConsts& C, uint64_t* lo, uint64_t* hi) {
+    using namespace fx;
+    Enc<CT_LIMBS> f;
+    if (b == 0 || (base == 1 && level == 0)) {  // 1 (level 0 of base 2 is unused)
+        set_pow2(f.lo, CT_BITS);
+        f.hi = f.lo;
+    } else if (base == 0) {
+        if (level == 0 && b >= 4) {
+            set_zero(f.lo);
+            set_zero(f.hi);
+        } else if (!exp_small<CT_LIMBS>((uint64_t)b, 8u * (unsigned)level, CT_BITS, C.div, f)) {
+            return false;
+        }
+    } else {
+        CoeffJob J;
+        J.func = 1;
+        J.e_in = 0;
+        J.p = 8 * level;  // X = b 2^-(8 level): q = p - e_in = 8 level
+        J.d = 0;
+        J.L = 1;
+        J.scale_log2 = 0;
+        J.log2_N = 0;
+        J.red = 0;
+        if (!exp2_arg<CT_LIMBS>(J, (uint64_t)b, CT_BITS, C, f)) return false;
+    }
+    for (int i = 0; i < CT_LIMBS; i++) {
+        lo[i] = f.lo.w[i];
+        hi[i] = f.hi.w[i];
+    }
+    return true;
+}
+
 // Per-job anchor: an enclosure of f at the job's first block X_a (exp and
 // 2^x: f(X_a) with P2 fractional bits; log: log X_a with P), at the
 // precision of the job's first segment (the largest scale of the job).
@@ -242,6 +295,93 @@ TMD_HD bool f_direct(const CoeffJob& J, uint64_t M, unsigned PB, const CoeffCons
         return true;
     }
     return exp2_arg<NL>(J, M, PB, C, f);
+}
+
+// An entry of the tables as NL limbs at PA = 64 (NL - 2) + 60 fractional
+// bits (the top NL of its CT_LIMBS limbs; the upper end rounded up).
+template <int NL>
+TMD_HD void ct_load(const uint64_t* tab, int base, int level, int b, fx::U<NL>& lo, fx::U<NL>& hi) {
+    static_assert(NL <= CT_LIMBS, "table entries hold CT_LIMBS limbs");
+    const uint64_t* e = tab + ct_index(base, level, b, 0);
+#pragma unroll
+    for (int i = 0; i < NL; i++) {
+        lo.w[i] = e[CT_LIMBS - NL + i];
+        hi.w[i] = e[CT_LIMBS + CT_LIMBS - NL + i];
+    }
+    if (NL < CT_LIMBS) fx::add_u64(hi, 1);
+}
+
+// Enclosure of f(X) 2^-red (exp with red = 0, 2^x) with PB fractional bits
+// from the tables: X = n + sum_i b_i 2^(-8 i) (the fraction of X = M 2^-q
+// left-aligned to 80 bits), f = e^n prod_i T(0, i, b_i) for exp and
+// 2^n prod_i T(1, i, b_i) for 2^x, the products formed at PA fractional bits
+// (lower end truncated, upper end raised by two units per product) and
+// shifted to PB bits.  False when the tables do not apply (log, exp above
+// [2, 4), more than 80 fractional bits), so that the caller takes the
+// series.
+template <int NL>
+TMD_HD bool f_table(const CoeffJob& J, uint64_t M, unsigned PB, const uint64_t* tab, fx::Enc<NL>& f, bool& exact) {
+    using namespace fx;
+    constexpr unsigned PA = 64u * NL - 68u;
+    exact = false;
+    const unsigned q = (unsigned)(J.p - J.e_in);
+    if (!tab || J.func == 2 || q > 80 || PB + 8 > PA) return false;
+    if (J.func == 0 && J.red) return false;
+    if (J.func == 1) {
+        if (J.red) {  // 2^(X - red), X - red = (M - red 2^q) 2^-q in [0, 1)
+            if (q == 0 || q >= 64 || (M >> q) != (uint64_t)J.red) return false;
+            M -= (uint64_t)J.red << q;
+        }
+        if (integer_arg(M, q)) {  // 2^X at an integer X
+            set_pow2(f.lo, PB + (unsigned)(q >= 64 ? 0 : (M >> q)));
+            f.hi = f.lo;
+            exact = true;
+            return true;
+        }
+    }
+    const uint64_t n = q >= 64 ? 0 : (M >> q);
+    if (n > 3) return false;
+    const uint64_t F = q >= 64 ? M : (M & ((1ull << q) - 1));
+    // the 80-bit left-aligned fraction V = F 2^(80 - q) as (vh, vl)
+    uint64_t vh, vl;
+    const unsigned sh = 80u - q;
+    if (sh >= 64) {
+        vh = F << (sh - 64);
+        vl = 0;
+    } else {
+        vl = F << sh;
+        vh = sh ? (F >> (64 - sh)) : 0;
+    }
+    const int base = J.func == 0 ? 0 : 1;
+    U<NL> lo, hi;
+    if (base == 0) {
+        ct_load<NL>(tab, 0, 0, (int)n, lo, hi);
+    } else {
+        set_pow2(lo, PA + (unsigned)n);
+        hi = lo;
+    }
+#pragma unroll 1
+    for (int i = 1; i <= 10; i++) {
+        const unsigned pos = 80u - 8u * (unsigned)i;  // bits [pos, pos + 8) of V
+        const unsigned b = pos >= 64 ? (unsigned)(vh >> (pos - 64)) & 255u
+                                     : (unsigned)((vl >> pos) | (pos > 56 ? vh << (64 - pos) : 0)) & 255u;
+        if (b == 0) continue;
+        U<NL> tlo, thi, r;
+        ct_load<NL>(tab, base, i, (int)b, tlo, thi);
+        mul_trunc<NL>(lo, tlo, r);
+        lo = r;
+        mul_trunc<NL>(hi, thi, r);
+        hi = r;
+        add_u64(hi, 2);
+    }
+    const unsigned s = PA - PB;
+    const bool up = low_bits(hi, s);
+    shr(lo, s);
+    shr(hi, s);
+    if (up) add_u64(hi, 1);
+    f.lo = lo;
+    f.hi = hi;
+    return true;
 }
 
 }  // namespace cf_detail
@@ -320,12 +460,16 @@ TMD_HD bool f_anchored(const CoeffJob& J, uint64_t M, unsigned PB, const CoeffCo
 
 }  // namespace cf_detail
 
-// c[k*L + l] for k = 0..d.  Returns false when a rounding stays undecided
-// at this width (retry with a wider NL) or a width is exceeded.  With an
-// anchor of the block's job, f(X_t) comes from the anchored short series.
+// c[k*COEFF_MAX_LIMBS + l] for k = 0..d, l < L (limb l of c_k; the other
+// slots zero).  Returns false when a rounding stays undecided at this width
+// (retry with a wider NL) or a width is exceeded.  With the device tables
+// f(X_t) comes from their products, with an anchor of the block's job from
+// the anchored short series, else from the direct series.  The loops over
+// the orders run to the largest degree with constant indices, so that the
+// caller's coefficient array can live in registers.
 template <int NL>
 TMD_HD bool block_coeffs(const CoeffJob& J, uint64_t M, int guard, const CoeffConsts& C, uint64_t* c,
-                         const Anchor* anchor = nullptr) {
+                         const Anchor* anchor = nullptr, const uint64_t* tables = nullptr) {
     using namespace fx;
     const int W = 64 * J.L;
     const int E0 = W + J.scale_log2 + J.red;  // f(X_t) is enclosed as 2^red g
@@ -337,8 +481,9 @@ TMD_HD bool block_coeffs(const CoeffJob& J, uint64_t M, int guard, const CoeffCo
     Enc<NL> f;
     bool exact = false;
     const bool integer_x = J.func == 1 && integer_arg(M, q);
-    if (!(anchor && !integer_x && cf_detail::f_anchored<NL>(J, M, PB, C, *anchor, f)))
-        if (!cf_detail::f_direct<NL>(J, M, PB, C, f, exact)) return false;
+    if (!(tables && cf_detail::f_table<NL>(J, M, PB, tables, f, exact)))
+        if (!(anchor && !integer_x && cf_detail::f_anchored<NL>(J, M, PB, C, *anchor, f)))
+            if (!cf_detail::f_direct<NL>(J, M, PB, C, f, exact)) return false;
     if (J.func == 2) {  // log
         const int s = (int)P - E0;
         if (s < 1) return false;
@@ -346,9 +491,15 @@ TMD_HD bool block_coeffs(const CoeffJob& J, uint64_t M, int guard, const CoeffCo
         cf_detail::rn_shift(f.hi, (unsigned)s);
         if (!equal(f.lo, f.hi)) return false;
         cf_detail::store_mod_w(f.lo, false, J.L, c);
-        for (int k = 1; k <= J.d; k++) {
+#pragma unroll
+        for (int k = 1; k <= COEFF_MAX_DEG; k++) {
+            if (k > J.d) {
+#pragma unroll
+                for (int l = 0; l < COEFF_MAX_LIMBS; l++) c[k * COEFF_MAX_LIMBS + l] = 0;
+                continue;
+            }
             const int Ek = E0 + k * (J.e_in - J.p);
-            if (!cf_detail::log_exact<NL>(M, k, Ek + k * (int)q, C, J.L, c + k * J.L)) return false;
+            if (!cf_detail::log_exact<NL>(M, k, Ek + k * (int)q, C, J.L, c + k * COEFF_MAX_LIMBS)) return false;
         }
         return true;
     }
@@ -357,7 +508,13 @@ TMD_HD bool block_coeffs(const CoeffJob& J, uint64_t M, int guard, const CoeffCo
     U<NL> l2lo, l2hi;
     if (J.func == 1) cf_detail::ln2_at<NL>(C, P2, l2lo, l2hi);
     U<NL> plo = f.lo, phi = f.hi;  // f (ln 2)^k enclosure, updated per order
-    for (int k = 0; k <= J.d; k++) {
+#pragma unroll
+    for (int k = 0; k <= COEFF_MAX_DEG; k++) {
+        if (k > J.d) {
+#pragma unroll
+            for (int l = 0; l < COEFF_MAX_LIMBS; l++) c[k * COEFF_MAX_LIMBS + l] = 0;
+            continue;
+        }
         if (J.func == 1 && k > 0) {
             U<NL> t;
             mul_shr(plo, l2lo, P2, t);
@@ -381,67 +538,105 @@ TMD_HD bool block_coeffs(const CoeffJob& J, uint64_t M, int guard, const CoeffCo
         if (s >= 64 * NL) {
             // the scaled value is below 2^(Ek - P2 + bits) < 1/2: rounds to 0
             if (bit_length(hi) + 1 >= (unsigned)s) return false;
-            for (int l = 0; l < J.L; l++) c[k * J.L + l] = 0;
+#pragma unroll
+            for (int l = 0; l < COEFF_MAX_LIMBS; l++) c[k * COEFF_MAX_LIMBS + l] = 0;
             continue;
         }
         cf_detail::rn_shift(lo, (unsigned)s);
         cf_detail::rn_shift(hi, (unsigned)s);
         if (!equal(lo, hi)) return false;
-        cf_detail::store_mod_w(lo, false, J.L, c + k * J.L);
+        cf_detail::store_mod_w(lo, false, J.L, c + k * COEFF_MAX_LIMBS);
     }
     (void)exact;
     return true;
 }
 
-// The 2d+1 table words from the coefficients: w = 0..d are Delta^w g0(0) with
-// g0(i) = R(iN), w = d+1..2d are Delta^(w-d-1) g1(0) with
-// g1(i) = R(iN+1) - R(iN), all mod 2^W.
+// The 2d+1 table words from the coefficients c[k*COEFF_MAX_LIMBS + l]: w =
+// 0..d are Delta^w g0(0) with g0(i) = R(iN), w = d+1..2d are
+// Delta^(w-d-1) g1(0) with g1(i) = R(iN+1) - R(iN), all mod 2^W; table[w*L +
+// l] (the loops run to the largest degree with constant indices).
 TMD_HD void block_table_words(const CoeffJob& J, const uint64_t* c, uint64_t* table) {
     using namespace fx;
     const int L = J.L, d = J.d;
     const uint64_t N = 1ull << J.log2_N;
     U<COEFF_MAX_LIMBS> g0[COEFF_MAX_DEG + 1], g1[COEFF_MAX_DEG];
-    for (int i = 0; i <= d; i++) {
+#pragma unroll
+    for (int i = 0; i <= COEFF_MAX_DEG; i++) {
+        if (i > d) break;
+#pragma unroll
         for (int pass = 0; pass < 2; pass++) {
             const uint64_t y = (uint64_t)i * N + (uint64_t)pass;
+            // R(y) mod 2^W by Horner from the top coefficient
             U<COEFF_MAX_LIMBS> acc;
             set_zero(acc);
-            for (int l = 0; l < L; l++) acc.w[l] = c[d * L + l];
-            for (int k = d - 1; k >= 0; k--) {
+#pragma unroll
+            for (int k = COEFF_MAX_DEG; k >= 0; k--) {
+                if (k > d) continue;
                 mul_u64(acc, y);
                 U<COEFF_MAX_LIMBS> ck;
-                set_zero(ck);
-                for (int l = 0; l < L; l++) ck.w[l] = c[k * L + l];
+#pragma unroll
+                for (int l = 0; l < COEFF_MAX_LIMBS; l++) ck.w[l] = c[k * COEFF_MAX_LIMBS + l];
                 add(acc, ck);
-                for (int l = L; l < COEFF_MAX_LIMBS; l++) acc.w[l] = 0;  // mod 2^W
+#pragma unroll
+                for (int l = 0; l < COEFF_MAX_LIMBS; l++)
+                    if (l >= L) acc.w[l] = 0;  // mod 2^W
             }
             if (pass == 0) {
                 g0[i] = acc;
             } else if (i < d) {
                 U<COEFF_MAX_LIMBS> t = acc;
                 sub(t, g0[i]);
-                for (int l = L; l < COEFF_MAX_LIMBS; l++) t.w[l] = 0;
-                g1[i] = t;
+#pragma unroll
+                for (int l = 0; l < COEFF_MAX_LIMBS; l++)
+                    if (l >= L) t.w[l] = 0;
+                g1[i < COEFF_MAX_DEG ? i : 0] = t;
             }
         }
     }
-    for (int lev = 0; lev <= d; lev++) {
-        for (int l = 0; l < L; l++) table[lev * L + l] = g0[0].w[l];
-        for (int i = 0; i + lev < d; i++) {  // g0[i] <- g0[i+1] - g0[i]  (mod 2^W)
+#pragma unroll
+    for (int lev = 0; lev <= COEFF_MAX_DEG; lev++) {
+        if (lev > d) break;
+#pragma unroll
+        for (int l = 0; l < COEFF_MAX_LIMBS; l++)
+            if (l < L) table[lev * L + l] = g0[0].w[l];
+#pragma unroll
+        for (int i = 0; i < COEFF_MAX_DEG; i++) {  // g0[i] <- g0[i+1] - g0[i]  (mod 2^W)
+            if (i + lev >= d) break;
             U<COEFF_MAX_LIMBS> t = g0[i + 1];
             sub(t, g0[i]);
-            for (int l = L; l < COEFF_MAX_LIMBS; l++) t.w[l] = 0;
+#pragma unroll
+            for (int l = 0; l < COEFF_MAX_LIMBS; l++)
+                if (l >= L) t.w[l] = 0;
             g0[i] = t;
         }
     }
-    for (int lev = 0; lev < d; lev++) {
-        for (int l = 0; l < L; l++) table[(d + 1 + lev) * L + l] = g1[0].w[l];
-        for (int i = 0; i + lev + 1 < d; i++) {
+#pragma unroll
+    for (int lev = 0; lev < COEFF_MAX_DEG; lev++) {
+        if (lev >= d) break;
+#pragma unroll
+        for (int l = 0; l < COEFF_MAX_LIMBS; l++)
+            if (l < L) table[(d + 1 + lev) * L + l] = g1[0].w[l];
+#pragma unroll
+        for (int i = 0; i + 1 < COEFF_MAX_DEG; i++) {
+            if (i + lev + 1 >= d) break;
             U<COEFF_MAX_LIMBS> t = g1[i + 1];
             sub(t, g1[i]);
-            for (int l = L; l < COEFF_MAX_LIMBS; l++) t.w[l] = 0;
+#pragma unroll
+            for (int l = 0; l < COEFF_MAX_LIMBS; l++)
+                if (l >= L) t.w[l] = 0;
             g1[i] = t;
         }
+    }
+}
+
+// The coefficients in the order of the external tables: out[k*L + l].
+TMD_HD void coeffs_packed(const CoeffJob& J, const uint64_t* c, uint64_t* out) {
+#pragma unroll
+    for (int k = 0; k <= COEFF_MAX_DEG; k++) {
+        if (k > J.d) break;
+#pragma unroll
+        for (int l = 0; l < COEFF_MAX_LIMBS; l++)
+            if (l < J.L) out[k * J.L + l] = c[k * COEFF_MAX_LIMBS + l];
     }
 }
 

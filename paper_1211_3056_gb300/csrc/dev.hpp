@@ -91,6 +91,8 @@ struct LaunchArgs {
     uint64_t* count;
     uint64_t* stats;
     uint32_t* queue_head;   // persistent form: next task index
+    uint32_t lanes;         // lanes per line in the filter (0, 1: one; 2; 4)
+    uint32_t unroll;        // difference steps per iteration of the stepping loop (0, 1: one; 2)
 };
 
 // Line search arguments.  JOBS mode: the lines written by the generation

@@ -236,6 +236,41 @@ TMD_HD void mul_shr(const U<NL>& a, const U<NL>& b, unsigned s, U<NL>& r) {
     shift_down<2 * NL, NL>(p, s, r);
 }
 
+// r = floor(a b / 2^PA) - e, e in {0, 1}, for PA = 64 (NL - 2) + 60 (the
+// working precision of the table products): the partial products a_i b_j
+// with i + j <= NL - 4 are not formed.  They all lie below
+// 2^(64 (NL - 2)) each, so together below 2^(64 (NL - 2) + 6) < 2^PA, and
+// dropping them lowers the quotient by at most one.  Needs a b < 2^(64 NL + PA).
+template <int NL>
+TMD_HD void mul_trunc(const U<NL>& a, const U<NL>& b, U<NL>& r) {
+    constexpr int K0 = NL - 3;
+    uint64_t p[2 * NL];
+#pragma unroll
+    for (int i = 0; i < 2 * NL; i++) p[i] = 0;
+#pragma unroll
+    for (int i = 0; i < NL; i++) {
+        uint64_t c = 0;
+#pragma unroll
+        for (int j = 0; j < NL; j++) {
+            if (i + j < K0) continue;
+            uint64_t lo = a.w[i] * b.w[j];
+            uint64_t hi = mulhi(a.w[i], b.w[j]);
+            uint64_t t = p[i + j] + lo;
+            hi += t < lo;
+            uint64_t t2 = t + c;
+            hi += t2 < c;
+            p[i + j] = t2;
+            c = hi;
+        }
+        p[i + NL] = c;
+    }
+#pragma unroll
+    for (int k = 0; k < NL; k++) {
+        const uint64_t lo = p[k + NL - 2], hi = (k + NL - 1 < 2 * NL) ? p[k + NL - 1] : 0;
+        r.w[k] = (lo >> 60) | (hi << 4);
+    }
+}
+
 // ------------------------------------------------ division by a 64-bit word
 struct Recip {
     uint64_t dn;  // divisor shifted left until its top bit is set

@@ -636,8 +636,7 @@ tmd_status block_table(const tmd_job& job, const BlockPlan& blk, uint64_t* coeff
     // one), then 768-bit words with 320 computed directly
     if (!block_coeffs<8>(J, M, 64, coeff_consts(), c, anchor) && !block_coeffs<12>(J, M, 320, coeff_consts(), c))
         return TMD_EUNSUPPORTED;
-    if (coeffs)
-        for (int i = 0; i < (job.d + 1) * (int)job.limbs; i++) coeffs[i] = c[i];
+    if (coeffs) coeffs_packed(J, c, coeffs);
     if (table) block_table_words(J, c, table);
     return TMD_OK;
 }

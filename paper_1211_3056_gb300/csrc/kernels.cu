@@ -317,12 +317,17 @@ __device__ __forceinline__ uint64_t cf_lower_bound(uint64_t B, uint64_t A, uint3
         *hs = h;
         return d;
     }
+    // The choice between the subtraction (partial quotient 1) and the
+    // division path is taken by the active lanes together: the division path
+    // is exact for k = 1 as well, so when the lanes disagree they all take it
+    // (one path issued instead of both, and a warp-uniform branch needs no
+    // reconvergence).
 #pragma unroll 1
     for (int guard = 0; guard < 64; guard++) {
         // second half: k = floor(p/q); p -= k q; v += k u; if d >= p: d = (d - p) mod q
         {
             const uint64_t r = p - q;
-            if (r < q) {
+            if (__all_sync(__activemask(), r < q)) {
                 p = r;
                 v = min(v + u, n);
                 d = csub(d, p);  // d - p < k q = q
@@ -332,13 +337,14 @@ __device__ __forceinline__ uint64_t cf_lower_bound(uint64_t B, uint64_t A, uint3
                 v = sat_madd(v, k, u, n);
             }
             h++;
-            if (u + v >= n) break;
+            // exit at u + v >= n, or when p reached 0 (d was reduced mod q
+            // just above): one branch for both
+            if ((u + v >= n) | (p == 0)) break;
         }
-        if (p == 0) break;  // d was reduced mod q just above
         // first half: k = floor(q/p); q -= k p; u += k v; d = d mod p
         {
             const uint64_t r = q - p;
-            if (r < p) {
+            if (__all_sync(__activemask(), r < p)) {
                 q = r;
                 u = min(u + v, n);
                 d = csub(d, p);  // d < q < 2p
@@ -348,7 +354,7 @@ __device__ __forceinline__ uint64_t cf_lower_bound(uint64_t B, uint64_t A, uint3
                 u = sat_madd(u, k, v, n);
             }
             h++;
-            if (u + v >= n || q == 0) break;
+            if ((u + v >= n) | (q == 0)) break;
         }
     }
     *hs = h;
@@ -947,16 +953,19 @@ __device__ __forceinline__ void fused_task(const DevTask& t, const LaunchArgs& a
     const int lane = threadIdx.x & 31;
     const uint32_t nu = a.jobs[t.job].nu;
     {
-        const DevJob job = a.jobs[t.job];
+        // the job record stays in global memory (a local copy of the whole
+        // record would be written to the stack at every task)
+        const DevJob& job = a.jobs[t.job];
         Packet<L, D> P;
         const uint32_t bi = packet_init<L, D>(P, t, job, a);
         st.blk[lane] = bi;
         st.i0[lane] = P.i0;
         const uint32_t N = 1u << job.log2_N;
-#pragma unroll 1
-        for (uint32_t it = 0; it < nu; it++) {
+        const uint64_t shift = job.shift;
+        // one line: its search words and length to the stage, one step
+        auto park = [&](uint32_t it) {
             uint64_t B, A;
-            packet_words<L, D>(P, job.shift, B, A);
+            packet_words<L, D>(P, shift, B, A);
             const uint32_t i = P.i0 + it;
             const bool valid = P.active && i < P.i1;
             const int s = stage_slot(lane * (int)nu + (int)it);
@@ -964,24 +973,53 @@ __device__ __forceinline__ void fused_task(const DevTask& t, const LaunchArgs& a
             st.A[s] = A;
             st.n[s] = valid ? (uint32_t)min((uint64_t)N, P.blk.length - (uint64_t)i * N) : 0u;
             packet_step<L, D>(P);
+        };
+        if (a.unroll >= 2 && (nu & 1u) == 0) {
+            // difference steps two at a time (a tiling knob)
+#pragma unroll 1
+            for (uint32_t it = 0; it < nu; it += 2) {
+                park(it);
+                park(it + 1);
+            }
+        } else {
+#pragma unroll 1
+            for (uint32_t it = 0; it < nu; it++) park(it);
         }
     }
     __syncwarp();
     const uint64_t Tm = a.jobs[t.job].Tm;
     const bool lefevre = G && (a.jobs[t.job].flags & TMD_LEFEVRE) != 0;
+    // lanes per line in the filter (a tiling knob: 1, 2 or 4): line s of a
+    // round is split into lp pieces of consecutive arguments, each lane
+    // bounding its piece's own line (B - A x0, A) over fewer points; the
+    // line fails when one of its pieces does, and its first lane carries it
+    const uint32_t lpl = a.lanes >= 4 ? 2u : (a.lanes >= 2 ? 1u : 0u);
+    const uint32_t lp = 1u << lpl, piece = (uint32_t)lane & (lp - 1u);
     uint32_t nfail = 0;  // general variant: failing lines listed in fl (warp-uniform)
 #pragma unroll 1
-    for (uint32_t r = 0; r < nu; r++) {
-        const int s = (int)r * 32 + lane;
+    for (uint32_t r = 0; r < (nu << lpl); r++) {
+        const int s = (int)(((r << 5) + (uint32_t)lane) >> lpl);
         const int slot = stage_slot(s);
         const uint32_t n = st.n[slot];
         const uint64_t B = st.B[slot];
         const uint64_t A = st.A[slot];
+        uint32_t np = n;
+        uint64_t Bp = B;
+        if (lpl) {
+            const uint32_t w = (n + lp - 1u) >> lpl, x0 = piece * w;
+            np = n > x0 ? min(w, n - x0) : 0u;
+            Bp = B - A * (uint64_t)x0;
+        }
         uint32_t hs = 0;
         uint64_t lb = ~0ull;
-        if (n) lb = lefevre ? lefevre_lower_bound<true>(B, A, n, &hs) : cf_lower_bound(B, A, n, &hs);
-        const bool fail = n && lb < Tm;
-        st_lines += n ? 1u : 0u;
+        if (np) lb = lefevre ? lefevre_lower_bound<true>(Bp, A, np, &hs) : cf_lower_bound(Bp, A, np, &hs);
+        bool fail = np && lb < Tm;
+        if (lpl) {
+            unsigned f = fail ? 1u : 0u;
+            for (uint32_t off = 1; off < lp; off <<= 1) f |= __shfl_xor_sync(FULLMASK, f, (int)off);
+            fail = f != 0 && piece == 0;
+        }
+        st_lines += (n && piece == 0) ? 1u : 0u;
         st_fail += fail ? 1u : 0u;
         st_half += hs;
         if (G) {
@@ -1030,7 +1068,7 @@ __device__ __forceinline__ void fused_task(const DevTask& t, const LaunchArgs& a
 
 template <int L, int D>
 __device__ __forceinline__ void generate_task(const DevTask& t, const LaunchArgs& a) {
-    const DevJob job = a.jobs[t.job];
+    const DevJob& job = a.jobs[t.job];
     Packet<L, D> P;
     packet_init<L, D>(P, t, job, a);
 #pragma unroll 1
@@ -1192,6 +1230,7 @@ __global__ void __launch_bounds__(256) k_search_lines(LineArgs a) {
             la.count = a.count;
             la.stats = a.stats;
             la.queue_head = nullptr;
+            la.lanes = la.unroll = 0;
             while (todo) {
                 const uint32_t jl = __shfl_sync(FULLMASK, job, __ffs(todo) - 1);
                 const bool mine = sound && fail && job == jl;
@@ -1290,7 +1329,7 @@ __device__ __forceinline__ CoeffJob block_coeff_job(const DevJob& jb, int e_out)
 }
 
 __global__ void __launch_bounds__(64) k_block_tables(const DevJob* jobs, const DevBlock* blocks, uint64_t n_blocks,
-                                                     uint64_t* tables, uint32_t* status) {
+                                                     uint64_t* tables, uint32_t* status, const uint64_t* ctab) {
     const uint64_t b = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (b >= n_blocks) return;
     const DevBlock bk = blocks[b];
@@ -1298,16 +1337,15 @@ __global__ void __launch_bounds__(64) k_block_tables(const DevJob* jobs, const D
     const CoeffJob J = block_coeff_job(jb, bk.e_out);
     const uint64_t M = (1ull << (jb.p - 1)) + bk.start;
     uint64_t c[(COEFF_MAX_DEG + 1) * COEFF_MAX_LIMBS];
-    const bool ok = block_coeffs<8>(J, M, 64, c_coeff, c);
+    const bool ok = block_coeffs<8>(J, M, 64, c_coeff, c, nullptr, ctab);
     if (ok) block_table_words(J, c, tables + bk.table_off);
-    if (ok && (jb.flags & TMD_SOUND))
-        for (int w = 0; w < (J.d + 1) * J.L; w++) tables[bk.table_off + (2 * J.d + 1) * J.L + w] = c[w];
+    if (ok && (jb.flags & TMD_SOUND)) coeffs_packed(J, c, tables + bk.table_off + (2 * J.d + 1) * J.L);
     status[b] = ok ? 0 : 1;
 }
 
 __global__ void __launch_bounds__(64) k_block_tables_wide(const DevJob* jobs, const DevBlock* blocks,
                                                           uint64_t n_blocks, uint64_t* tables, uint32_t* status,
-                                                          uint32_t* err) {
+                                                          uint32_t* err, const uint64_t* ctab) {
     const uint64_t b = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (b >= n_blocks || status[b] == 0) return;
     const DevBlock bk = blocks[b];
@@ -1315,10 +1353,9 @@ __global__ void __launch_bounds__(64) k_block_tables_wide(const DevJob* jobs, co
     const CoeffJob J = block_coeff_job(jb, bk.e_out);
     const uint64_t M = (1ull << (jb.p - 1)) + bk.start;
     uint64_t c[(COEFF_MAX_DEG + 1) * COEFF_MAX_LIMBS];
-    if (block_coeffs<12>(J, M, 320, c_coeff, c)) {
+    if (block_coeffs<12>(J, M, 320, c_coeff, c, nullptr, ctab)) {
         block_table_words(J, c, tables + bk.table_off);
-        if (jb.flags & TMD_SOUND)
-            for (int w = 0; w < (J.d + 1) * J.L; w++) tables[bk.table_off + (2 * J.d + 1) * J.L + w] = c[w];
+        if (jb.flags & TMD_SOUND) coeffs_packed(J, c, tables + bk.table_off + (2 * J.d + 1) * J.L);
         status[b] = 0;
     } else {
         atomicOr(err, (uint32_t)ERR_ROUNDING);
@@ -1329,13 +1366,29 @@ cudaError_t upload_coeff_consts(const CoeffConsts& C) {
     return cudaMemcpyToSymbol(c_coeff, &C, sizeof C);
 }
 
+// The exp and 2^x tables of the table-driven enclosures (coeffs.cuh), one
+// thread per entry; an entry that fails to enclose sets *err.
+__global__ void __launch_bounds__(64) k_coeff_tables(uint64_t* ctab, uint32_t* err) {
+    const int e = (int)(blockIdx.x * blockDim.x + threadIdx.x);
+    if (e >= 2 * CT_LEVELS * CT_ENTRIES) return;
+    const int base = e / (CT_LEVELS * CT_ENTRIES), level = (e / CT_ENTRIES) % CT_LEVELS, b = e % CT_ENTRIES;
+    if (!ct_entry(base, level, b, c_coeff, ctab + ct_index(base, level, b, 0), ctab + ct_index(base, level, b, 1)))
+        atomicOr(err, 1u);
+}
+
+cudaError_t launch_coeff_tables(uint64_t* ctab, uint32_t* err, cudaStream_t s) {
+    const int n = 2 * CT_LEVELS * CT_ENTRIES;
+    k_coeff_tables<<<(n + 63) / 64, 64, 0, s>>>(ctab, err);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_block_tables(const DevJob* jobs, const DevBlock* blocks, uint64_t n_blocks, uint64_t* tables,
-                                uint32_t* status, uint32_t* err, cudaStream_t s) {
+                                uint32_t* status, uint32_t* err, const uint64_t* ctab, cudaStream_t s) {
     if (n_blocks == 0) return cudaSuccess;
     // 64-thread CTAs spread the (few, long) threads over more SMs
     const unsigned grid = (unsigned)((n_blocks + 63) / 64);
-    k_block_tables<<<grid, 64, 0, s>>>(jobs, blocks, n_blocks, tables, status);
-    k_block_tables_wide<<<grid, 64, 0, s>>>(jobs, blocks, n_blocks, tables, status, err);
+    k_block_tables<<<grid, 64, 0, s>>>(jobs, blocks, n_blocks, tables, status, ctab);
+    k_block_tables_wide<<<grid, 64, 0, s>>>(jobs, blocks, n_blocks, tables, status, err, ctab);
     return cudaGetLastError();
 }
 

@@ -7,7 +7,7 @@
 #include <cstdint>
 #include <vector>
 
-#include "../../include/tmd.h"
+#include "../../include/tmd_probe.h"
 
 namespace tmd {
 namespace {

@@ -85,30 +85,38 @@ def test_large_batch_sample_exact(ctx):
         assert [r for r in got if r[0] == k] == sorted(want, key=lambda r: (r[0], r[2], r[3])), k
 
 
-@pytest.mark.parametrize("tiling", [(8, 1), (6, 2), (4, 3), (2, 1), (1, 2), (3, 0)])
+@pytest.mark.parametrize("tiling", [(8, 1), (6, 2), (4, 3), (2, 1), (1, 2), (3, 0), (8, 3, 2, 1), (8, 2, 4, 2),
+                                    (6, 3, 2, 2), (1, 1, 4, 1), (5, 0, 1, 2), (8, 0, 4, 0)])
 def test_every_tiling_gives_the_oracle_list(ctx, tiling):
     """The tiling only changes how the work is cut (packet length, resident
-    CTAs), never the records."""
+    CTAs, lanes per line in the filter, difference steps per iteration),
+    never the records."""
     want = oc.candidates(MIXED)
     d_cand, d_count = tmd.alloc_candidates(1 << 16)
     b = tmd.Batch(ctx, MIXED, d_cand, d_count, tiling=tiling)
     b.launch()
     got, n = batch_records(b, d_cand, d_count)
-    nu, per_sm = b.tiling()
+    nu, per_sm, lanes, unroll = b.tiling()
+    st = b.stats()
     b.close()
     assert got == want and n == len(want)
     assert nu == tiling[0]
     assert per_sm >= 1 and (tiling[1] == 0 or per_sm <= tiling[1])
+    t = tuple(tiling) + (0, 0)
+    assert lanes == (t[2] or 1) and unroll == (t[3] or 1)
+    assert st["lines"] == sum(__import__("oracle").plan.n_subintervals(j) for j in MIXED)
 
 
 def test_autotune_picks_a_valid_tiling_and_batches_use_it(ctx):
     jobs = wl.batched_jobs(njobs=6, m=24, size_log2_range=(24.0, 27.0))
     best = tmd.tmd_autotune(ctx, jobs)
     assert best["nu"] in (1, 2, 4, 6, 8) and best["ctas_per_sm"] >= 1 and best["ms"] > 0
+    assert best["lanes"] in (1, 2, 4) and best["unroll"] in (1, 2)
     d_cand, d_count = tmd.alloc_candidates(1 << 18)
     b = tmd.Batch(ctx, jobs, d_cand, d_count)      # takes the tuned tiling
-    nu, per_sm = b.tiling()
+    nu, per_sm, lanes, unroll = b.tiling()
     assert 1 <= nu <= best["nu"] and 1 <= per_sm <= best["ctas_per_sm"]
+    assert (lanes, unroll) == (best["lanes"], best["unroll"])
     b.launch()
     got, n = batch_records(b, d_cand, d_count)
     b.close()

@@ -113,3 +113,35 @@ def test_served_filter_variants_and_sound_jobs_equal_the_oracle():
             want = oc.job_candidates(job, 0)
         assert r["status"] == 0 and r["count"] == len(want)
         assert recs == sorted(want, key=lambda w: (w[0], w[2], w[3])), tag
+
+
+def test_scheduled_arrivals_equal_solo_runs_and_counters():
+    """A Poisson arrival stream replayed by the server's clock
+    (tmd_server_submit_many): every job is admitted no earlier than its
+    arrival, groups overlap on the device, each result equals the job's solo
+    run, and the server's counters cover every line of every job once."""
+    from oracle import plan
+    jobs = wl.serving_jobs(njobs=60, size_log2_range=(18.0, 26.0))
+    jobs = [j.replace(m=m) for j, m in zip(jobs, random.Random(9).choices([20, 24, 30], k=60))]
+    delays = wl.arrival_times(len(jobs), 20000.0, seed=3)
+    with tmd.Context(0) as ctx:
+        with tmd.Server(ctx, max_inflight=3, max_batch=16, cand_cap=1 << 16) as srv:
+            t0 = srv.clock()
+            srv.submit_many(jobs, list(range(len(jobs))), delays)
+            got = {}
+            deadline = time.time() + 120
+            while len(got) < len(jobs) and time.time() < deadline:
+                for r, recs in srv.poll(wait_ms=100):
+                    got[r["id"]] = (r, recs)
+            st = srv.stats()
+            assert srv.pending() == 0
+        assert len(got) == len(jobs)
+        for tag, job in enumerate(jobs):
+            r, recs = got[tag]
+            solo, n = tmd.run([job], ctx=ctx, fused=True, cap=1 << 16)
+            assert r["status"] == 0 and r["count"] == n and recs == solo, tag
+            assert r["t_submit"] >= t0 + delays[tag] - 1e-3
+            assert r["t_submit"] <= r["t_start"] <= r["t_done"]
+    assert st["lines"] == sum(plan.n_subintervals(j) for j in jobs)
+    assert st["count"] == sum(got[t][0]["count"] for t in got)
+    assert st["groups"] >= 4

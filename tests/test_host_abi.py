@@ -13,24 +13,27 @@ from oracle import plan, poly, search
 tmd = pytest.importorskip("paper_1211_3056_gb300")
 
 
-def declared_functions():
-    names = set()
-    for fn in os.listdir(os.path.join(ROOT, "include")):
-        if fn.endswith(".h"):
-            src = open(os.path.join(ROOT, "include", fn)).read()
-            src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
-            names |= set(re.findall(r"\b(tmd_\w+)\s*\(", src))
-    return names
+def declared_functions(header):
+    src = open(os.path.join(ROOT, "include", header)).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return set(re.findall(r"\b(tmd_\w+)\s*\(", src))
 
 
 def test_exports_every_declared_symbol():
+    """include/tmd.h is libtmd.so's boundary, include/tmd_probe.h
+    libtmd_probe.so's; every header of include/ is one of the two."""
     import ctypes
-    lib = ctypes.CDLL(tmd._lib.LIB_PATH)
-    names = declared_functions()
-    assert len(names) >= 12
-    for n in sorted(names):
-        assert hasattr(lib, n), n
-    assert set(tmd._lib.SIGNATURES) <= names
+    assert sorted(f for f in os.listdir(os.path.join(ROOT, "include")) if f.endswith(".h")) == \
+        ["tmd.h", "tmd_probe.h"]
+    for header, path, sigs in (("tmd.h", tmd._lib.LIB_PATH, tmd._lib.SIGNATURES),
+                               ("tmd_probe.h", tmd._lib.PROBE_PATH, tmd._lib.PROBE_SIGNATURES)):
+        lib = ctypes.CDLL(path)
+        names = declared_functions(header)
+        assert len(names) >= (12 if header == "tmd.h" else 1)
+        for n in sorted(names):
+            assert hasattr(lib, n), (header, n)
+        assert set(sigs) <= names
+    assert "tmd_pipe_rates" not in declared_functions("tmd.h")
 
 
 def test_version_and_status_strings():

@@ -11,6 +11,7 @@
 #include <condition_variable>
 #include <cstring>
 #include <deque>
+#include <functional>
 #include <map>
 #include <string>
 #include <mutex>
@@ -129,6 +130,61 @@ unsigned host_threads() {
     return n ? n : 1;
 }
 
+// A pool of host threads that stay parked between parallel runs (creating
+// threads for every plan costs ~10-20 us each).  run(n, fn) executes fn on
+// n threads, the caller being one of them; one run at a time (a second
+// caller meanwhile gets fresh threads).  The pool is never destroyed: its
+// parked threads end with the process.
+class HostPool {
+   public:
+    static HostPool& get() {
+        static HostPool* p = new HostPool();
+        return *p;
+    }
+    bool try_run(unsigned n, const std::function<void()>& fn) {
+        std::unique_lock<std::mutex> run_lk(run_mu_, std::try_to_lock);
+        if (!run_lk.owns_lock()) return false;
+        const unsigned helpers = n - 1;
+        {
+            std::lock_guard<std::mutex> lk(mu_);
+            while (workers_.size() < helpers) workers_.emplace_back([this] { loop(); });
+            fn_ = &fn;
+            want_ = helpers;
+            taken_ = 0;
+            done_ = 0;
+            gen_++;
+        }
+        cv_work_.notify_all();
+        fn();
+        std::unique_lock<std::mutex> lk(mu_);
+        cv_done_.wait(lk, [&] { return done_ == want_; });
+        fn_ = nullptr;
+        return true;
+    }
+
+   private:
+    void loop() {
+        uint64_t seen = 0;
+        std::unique_lock<std::mutex> lk(mu_);
+        for (;;) {
+            cv_work_.wait(lk, [&] { return gen_ != seen && taken_ < want_; });
+            seen = gen_;
+            taken_++;
+            const std::function<void()>* f = fn_;
+            lk.unlock();
+            (*f)();
+            lk.lock();
+            if (++done_ == want_) cv_done_.notify_all();
+        }
+    }
+    std::mutex run_mu_, mu_;
+    std::condition_variable cv_work_, cv_done_;
+    std::vector<std::thread> workers_;
+    const std::function<void()>* fn_ = nullptr;
+    uint64_t gen_ = 0;
+    unsigned want_ = 0, taken_ = 0, done_ = 0;
+};
+
 // fn() on n threads (the calling thread alone when n <= 1)
 template <class F>
 void run_threads(unsigned n, F&& fn) {
@@ -136,6 +192,8 @@ void run_threads(unsigned n, F&& fn) {
         fn();
         return;
     }
+    const std::function<void()> f = fn;
+    if (HostPool::get().try_run(n, f)) return;
     std::vector<std::thread> th;
     for (unsigned i = 0; i < n; i++) th.emplace_back(fn);
     for (auto& t : th) t.join();
@@ -194,13 +252,13 @@ tmd_status build_plan(const tmd_job* jobs, uint32_t njobs, Plan& P, bool host_ta
             for (size_t k = 0; k < sg.size(); k++) seg_of[j][k] = sg[k];
         }
     };
-    const unsigned nth = njobs >= 512 ? std::min<unsigned>(host_threads(), 32) : 1;
+    const unsigned nth = njobs >= 128 ? std::min<unsigned>({host_threads(), 32u, njobs / 32}) : 1;
     std::atomic<uint32_t> next_chunk(0);
     run_threads(nth, [&]() {
         for (;;) {
-            const uint32_t a = next_chunk.fetch_add(64);
+            const uint32_t a = next_chunk.fetch_add(32);
             if (a >= njobs) break;
-            seg_work(a, std::min<uint32_t>(njobs, a + 64));
+            seg_work(a, std::min<uint32_t>(njobs, a + 32));
         }
     });
     std::vector<Segment> segs;

@@ -197,27 +197,38 @@ TMD_HD bool exp_reduced(const CoeffJob& J, uint64_t M, unsigned PB, const CoeffC
     return true;
 }
 
-// Tables of the device path for exp and 2^x: entry (base, level i, b) is an
-// enclosure of base^(b 2^(-8 i)), i = 1..10, b < 256 (base 0: e, base 1: 2),
-// and level 0 of base e holds e^n, n < 4; lo and hi ends of CT_LIMBS limbs
-// with CT_BITS fractional bits.  An argument X = n + sum_i b_i 2^(-8 i) with
-// at most 80 fractional bits then has e^X (2^X) as the product of at most 11
-// entries (2^n exact), with no series per block (the table-driven method of
-// Tang's exponential, here with rigorous enclosures at every step).
-enum { CT_LEVELS = 11, CT_ENTRIES = 256, CT_LIMBS = 12, CT_BITS = 64 * CT_LIMBS - 68 };
+// Tables of the device path for exp, 2^x and log: entry (base, level i, b) is
+// an enclosure of base^(b 2^(-8 i)), i = 1..10, b < 256 (base 0: e, base 1:
+// 2), level 0 of base e holds e^n, n < 4, and level 0 of "base" 2 holds
+// log(256 + b); lo and hi ends of CT_LIMBS limbs with CT_BITS fractional
+// bits.  An argument X = n + sum_i b_i 2^(-8 i) with at most 80 fractional
+// bits then has e^X (2^X) as the product of at most 11 entries (2^n exact),
+// with no series per block (the table-driven method of Tang's exponential,
+// here with rigorous enclosures at every step); log X takes the entry of
+// the argument's top 9 bits g and a short atanh series of the rest.
+enum { CT_BASES = 3, CT_LEVELS = 11, CT_ENTRIES = 256, CT_LIMBS = 12, CT_BITS = 64 * CT_LIMBS - 68 };
 
 TMD_HD size_t ct_index(int base, int level, int b, int end) {
     return ((((size_t)base * CT_LEVELS + (size_t)level) * CT_ENTRIES + (size_t)b) * 2 + (size_t)end) * CT_LIMBS;
 }
 
-constexpr size_t CT_WORDS = 2 * CT_LEVELS * CT_ENTRIES * 2 * CT_LIMBS;
+constexpr size_t CT_WORDS = (size_t)CT_BASES * CT_LEVELS * CT_ENTRIES * 2 * CT_LIMBS;
 
 // Entry (base, level, b) of the tables at CT_BITS fractional bits; false if
 // an enclosure fails (it does not for the supported ranges).
 TMD_HD bool ct_entry(int base, int level, int b, const CoeffConsts& C, uint64_t* lo, uint64_t* hi) {
     using namespace fx;
     Enc<CT_LIMBS> f;
-    if (b == 0 || (base == 1 && level == 0)) {  // 1 (level 0 of base 2 is unused)
+    if (base == 2) {  // log(256 + b) at level 0 (the other levels are unused)
+        if (level != 0) {
+            set_zero(f.lo);
+            set_zero(f.hi);
+        } else {
+            Enc<CT_LIMBS> ln2;
+            cf_detail::ln2_at<CT_LIMBS>(C, CT_BITS, ln2.lo, ln2.hi);
+            if (!log_enc<CT_LIMBS>(256u + (uint64_t)b, 9, 9, CT_BITS, ln2, C.div, f)) return false;
+        }
+    } else if (b == 0 || (base == 1 && level == 0)) {  // 1 (level 0 of base 2 is unused)
         set_pow2(f.lo, CT_BITS);
         f.hi = f.lo;
     } else if (base == 0) {
@@ -319,13 +330,67 @@ TMD_HD void ct_load(const uint64_t* tab, int base, int level, int b, fx::U<NL>& 
 // shifted to PB bits.  False when the tables do not apply (log, exp above
 // [2, 4), more than 80 fractional bits), so that the caller takes the
 // series.
+// log X for X = M 2^(e_in - p): with g = the top 9 bits of M (256 <= g <
+// 512) and G = g 2^(p - 9), X = g (M / G) 2^(e_in - 9), so
+//   log X = log g + (e_in - 9) ln 2 + 2 atanh((M - G) / (M + G)),
+// the ratio below 2^-9: a series of ~P/18 terms instead of ~P/3.2 for the
+// direct atanh of (2^p - M)/(2^p + M) <= 1/3.  log g from the tables, ln 2
+// from the constants, all with PB fractional bits (PB + 8 <= PA).
 template <int NL>
-TMD_HD bool f_table(const CoeffJob& J, uint64_t M, unsigned PB, const uint64_t* tab, fx::Enc<NL>& f, bool& exact) {
+TMD_HD bool f_table_log(const CoeffJob& J, uint64_t M, unsigned PB, const uint64_t* tab, const CoeffConsts& C,
+                        fx::Enc<NL>& f) {
+    using namespace fx;
+    constexpr unsigned PA = 64u * NL - 68u;
+    if (J.p < 9 || J.p > 61) return false;
+    const unsigned sh = (unsigned)(J.p - 9);
+    const uint64_t g = M >> sh, G = g << sh;
+    if (g < 256 || g >= 512) return false;
+    U<NL> S;
+    uint64_t E;
+    if (!atanh_ratio<NL>(M - G, M + G, PB, C.div, S, E)) return false;
+    U<NL> tlo, thi;
+    ct_load<NL>(tab, 2, 0, (int)(g - 256), tlo, thi);
+    const unsigned s = PA - PB;
+    const bool up = low_bits(thi, s);
+    shr(tlo, s);
+    shr(thi, s);
+    if (up) add_u64(thi, 1);
+    U<NL> llo, lhi;
+    ln2_at<NL>(C, PB, llo, lhi);
+    const int e = J.e_in - 9;
+    const uint64_t ae = (uint64_t)(e < 0 ? -e : e);
+    // lower end: log g (lo) + 2 S +/- |e| ln 2 (lo when adding, hi when subtracting)
+    U<NL> lo = tlo, hi = thi, a = S, b = S;
+    mul_u64(a, 2);
+    add_u64(b, E);
+    mul_u64(b, 2);
+    add(lo, a);
+    add(hi, b);
+    U<NL> el = e < 0 ? lhi : llo, eh = e < 0 ? llo : lhi;
+    mul_u64(el, ae);
+    mul_u64(eh, ae);
+    if (e < 0) {
+        if (sub(lo, el)) return false;
+        if (sub(hi, eh)) return false;
+    } else {
+        add(lo, el);
+        add(hi, eh);
+    }
+    f.lo = lo;
+    f.hi = hi;
+    return true;
+}
+
+template <int NL>
+TMD_HD bool f_table(const CoeffJob& J, uint64_t M, unsigned PB, const uint64_t* tab, const CoeffConsts& C,
+                    fx::Enc<NL>& f, bool& exact) {
     using namespace fx;
     constexpr unsigned PA = 64u * NL - 68u;
     exact = false;
     const unsigned q = (unsigned)(J.p - J.e_in);
-    if (!tab || J.func == 2 || q > 80 || PB + 8 > PA) return false;
+    if (!tab || PB + 8 > PA) return false;
+    if (J.func == 2) return f_table_log<NL>(J, M, PB, tab, C, f);
+    if (q > 80) return false;
     if (J.func == 0 && J.red) return false;
     if (J.func == 1) {
         if (J.red) {  // 2^(X - red), X - red = (M - red 2^q) 2^-q in [0, 1)
@@ -464,9 +529,11 @@ TMD_HD bool f_anchored(const CoeffJob& J, uint64_t M, unsigned PB, const CoeffCo
 // slots zero).  Returns false when a rounding stays undecided at this width
 // (retry with a wider NL) or a width is exceeded.  With the device tables
 // f(X_t) comes from their products, with an anchor of the block's job from
-// the anchored short series, else from the direct series.  The loops over
-// the orders run to the largest degree with constant indices, so that the
-// caller's coefficient array can live in registers.
+// the anchored short series, else from the direct series.  (The order and
+// table-word loops stay rolled: unrolled to the largest degree they keep the
+// coefficients in registers but make the table kernel, one or two warps per
+// SM on small plans, wait on instruction fetches -- 44 against 63 us on the
+// 4096 blocks of a 2^36-argument slice.)
 template <int NL>
 TMD_HD bool block_coeffs(const CoeffJob& J, uint64_t M, int guard, const CoeffConsts& C, uint64_t* c,
                          const Anchor* anchor = nullptr, const uint64_t* tables = nullptr) {
@@ -481,7 +548,7 @@ TMD_HD bool block_coeffs(const CoeffJob& J, uint64_t M, int guard, const CoeffCo
     Enc<NL> f;
     bool exact = false;
     const bool integer_x = J.func == 1 && integer_arg(M, q);
-    if (!(tables && cf_detail::f_table<NL>(J, M, PB, tables, f, exact)))
+    if (!(tables && cf_detail::f_table<NL>(J, M, PB, tables, C, f, exact)))
         if (!(anchor && !integer_x && cf_detail::f_anchored<NL>(J, M, PB, C, *anchor, f)))
             if (!cf_detail::f_direct<NL>(J, M, PB, C, f, exact)) return false;
     if (J.func == 2) {  // log
@@ -491,7 +558,7 @@ TMD_HD bool block_coeffs(const CoeffJob& J, uint64_t M, int guard, const CoeffCo
         cf_detail::rn_shift(f.hi, (unsigned)s);
         if (!equal(f.lo, f.hi)) return false;
         cf_detail::store_mod_w(f.lo, false, J.L, c);
-#pragma unroll
+#pragma unroll 1
         for (int k = 1; k <= COEFF_MAX_DEG; k++) {
             if (k > J.d) {
 #pragma unroll
@@ -508,7 +575,7 @@ TMD_HD bool block_coeffs(const CoeffJob& J, uint64_t M, int guard, const CoeffCo
     U<NL> l2lo, l2hi;
     if (J.func == 1) cf_detail::ln2_at<NL>(C, P2, l2lo, l2hi);
     U<NL> plo = f.lo, phi = f.hi;  // f (ln 2)^k enclosure, updated per order
-#pragma unroll
+#pragma unroll 1
     for (int k = 0; k <= COEFF_MAX_DEG; k++) {
         if (k > J.d) {
 #pragma unroll
@@ -554,30 +621,30 @@ TMD_HD bool block_coeffs(const CoeffJob& J, uint64_t M, int guard, const CoeffCo
 // The 2d+1 table words from the coefficients c[k*COEFF_MAX_LIMBS + l]: w =
 // 0..d are Delta^w g0(0) with g0(i) = R(iN), w = d+1..2d are
 // Delta^(w-d-1) g1(0) with g1(i) = R(iN+1) - R(iN), all mod 2^W; table[w*L +
-// l] (the loops run to the largest degree with constant indices).
+// l].
 TMD_HD void block_table_words(const CoeffJob& J, const uint64_t* c, uint64_t* table) {
     using namespace fx;
     const int L = J.L, d = J.d;
     const uint64_t N = 1ull << J.log2_N;
     U<COEFF_MAX_LIMBS> g0[COEFF_MAX_DEG + 1], g1[COEFF_MAX_DEG];
-#pragma unroll
+#pragma unroll 1
     for (int i = 0; i <= COEFF_MAX_DEG; i++) {
         if (i > d) break;
-#pragma unroll
+#pragma unroll 1
         for (int pass = 0; pass < 2; pass++) {
             const uint64_t y = (uint64_t)i * N + (uint64_t)pass;
             // R(y) mod 2^W by Horner from the top coefficient
             U<COEFF_MAX_LIMBS> acc;
             set_zero(acc);
-#pragma unroll
+#pragma unroll 1
             for (int k = COEFF_MAX_DEG; k >= 0; k--) {
                 if (k > d) continue;
                 mul_u64(acc, y);
                 U<COEFF_MAX_LIMBS> ck;
-#pragma unroll
+#pragma unroll 1
                 for (int l = 0; l < COEFF_MAX_LIMBS; l++) ck.w[l] = c[k * COEFF_MAX_LIMBS + l];
                 add(acc, ck);
-#pragma unroll
+#pragma unroll 1
                 for (int l = 0; l < COEFF_MAX_LIMBS; l++)
                     if (l >= L) acc.w[l] = 0;  // mod 2^W
             }
@@ -586,42 +653,42 @@ TMD_HD void block_table_words(const CoeffJob& J, const uint64_t* c, uint64_t* ta
             } else if (i < d) {
                 U<COEFF_MAX_LIMBS> t = acc;
                 sub(t, g0[i]);
-#pragma unroll
+#pragma unroll 1
                 for (int l = 0; l < COEFF_MAX_LIMBS; l++)
                     if (l >= L) t.w[l] = 0;
                 g1[i < COEFF_MAX_DEG ? i : 0] = t;
             }
         }
     }
-#pragma unroll
+#pragma unroll 1
     for (int lev = 0; lev <= COEFF_MAX_DEG; lev++) {
         if (lev > d) break;
-#pragma unroll
+#pragma unroll 1
         for (int l = 0; l < COEFF_MAX_LIMBS; l++)
             if (l < L) table[lev * L + l] = g0[0].w[l];
-#pragma unroll
+#pragma unroll 1
         for (int i = 0; i < COEFF_MAX_DEG; i++) {  // g0[i] <- g0[i+1] - g0[i]  (mod 2^W)
             if (i + lev >= d) break;
             U<COEFF_MAX_LIMBS> t = g0[i + 1];
             sub(t, g0[i]);
-#pragma unroll
+#pragma unroll 1
             for (int l = 0; l < COEFF_MAX_LIMBS; l++)
                 if (l >= L) t.w[l] = 0;
             g0[i] = t;
         }
     }
-#pragma unroll
+#pragma unroll 1
     for (int lev = 0; lev < COEFF_MAX_DEG; lev++) {
         if (lev >= d) break;
-#pragma unroll
+#pragma unroll 1
         for (int l = 0; l < COEFF_MAX_LIMBS; l++)
             if (l < L) table[(d + 1 + lev) * L + l] = g1[0].w[l];
-#pragma unroll
+#pragma unroll 1
         for (int i = 0; i + 1 < COEFF_MAX_DEG; i++) {
             if (i + lev + 1 >= d) break;
             U<COEFF_MAX_LIMBS> t = g1[i + 1];
             sub(t, g1[i]);
-#pragma unroll
+#pragma unroll 1
             for (int l = 0; l < COEFF_MAX_LIMBS; l++)
                 if (l >= L) t.w[l] = 0;
             g1[i] = t;

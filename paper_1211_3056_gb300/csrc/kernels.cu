@@ -317,17 +317,12 @@ __device__ __forceinline__ uint64_t cf_lower_bound(uint64_t B, uint64_t A, uint3
         *hs = h;
         return d;
     }
-    // The choice between the subtraction (partial quotient 1) and the
-    // division path is taken by the active lanes together: the division path
-    // is exact for k = 1 as well, so when the lanes disagree they all take it
-    // (one path issued instead of both, and a warp-uniform branch needs no
-    // reconvergence).
 #pragma unroll 1
     for (int guard = 0; guard < 64; guard++) {
         // second half: k = floor(p/q); p -= k q; v += k u; if d >= p: d = (d - p) mod q
         {
             const uint64_t r = p - q;
-            if (__all_sync(__activemask(), r < q)) {
+            if (r < q) {
                 p = r;
                 v = min(v + u, n);
                 d = csub(d, p);  // d - p < k q = q
@@ -344,7 +339,7 @@ __device__ __forceinline__ uint64_t cf_lower_bound(uint64_t B, uint64_t A, uint3
         // first half: k = floor(q/p); q -= k p; u += k v; d = d mod p
         {
             const uint64_t r = q - p;
-            if (__all_sync(__activemask(), r < p)) {
+            if (r < p) {
                 q = r;
                 u = min(u + v, n);
                 d = csub(d, p);  // d < q < 2p
@@ -996,6 +991,41 @@ __device__ __forceinline__ void fused_task(const DevTask& t, const LaunchArgs& a
     const uint32_t lpl = a.lanes >= 4 ? 2u : (a.lanes >= 2 ? 1u : 0u);
     const uint32_t lp = 1u << lpl, piece = (uint32_t)lane & (lp - 1u);
     uint32_t nfail = 0;  // general variant: failing lines listed in fl (warp-uniform)
+    // one lane per line (the default) has a loop of its own: the pieces'
+    // bookkeeping costs the hot loop registers and ~2.5 % when shared
+    if (lpl == 0) {
+#pragma unroll 1
+    for (uint32_t r = 0; r < nu; r++) {
+        const int s = (int)r * 32 + lane;
+        const int slot = stage_slot(s);
+        const uint32_t n = st.n[slot];
+        const uint64_t B = st.B[slot];
+        const uint64_t A = st.A[slot];
+        uint32_t hs = 0;
+        uint64_t lb = ~0ull;
+        if (n) lb = lefevre ? lefevre_lower_bound<true>(B, A, n, &hs) : cf_lower_bound(B, A, n, &hs);
+        const bool fail = n && lb < Tm;
+        st_lines += n ? 1u : 0u;
+        st_fail += fail ? 1u : 0u;
+        st_half += hs;
+        if (G) {
+            // general variant: the failing lines of the task are listed and
+            // resolved 32 at a time below (one lane each), not round by round
+            // with a few active lanes
+            const unsigned fm = __ballot_sync(FULLMASK, fail);
+            if (fail) fl[nfail + (uint32_t)__popc(fm & ((1u << lane) - 1u))] = (uint16_t)s;
+            nfail += (uint32_t)__popc(fm);
+        } else if (__any_sync(FULLMASK, fail)) {
+            const uint32_t pk = (uint32_t)s / nu;
+            const uint32_t i = st.i0[pk] + (uint32_t)s % nu;
+            const DevBlock& bk = a.blocks[st.blk[pk]];
+            const DevJob& jb = a.jobs[t.job];
+            resolve_and_emit(fail, B, A, n ? n : 1u, Tm, (jb.flags & TMD_ALL_HITS) != 0, t.job,
+                             (uint32_t)(bk.first_sub + i), bk.start + ((uint64_t)i << jb.log2_N), a.cand,
+                             a.cap, a.count);
+        }
+    }
+    } else {
 #pragma unroll 1
     for (uint32_t r = 0; r < (nu << lpl); r++) {
         const int s = (int)(((r << 5) + (uint32_t)lane) >> lpl);
@@ -1038,6 +1068,7 @@ __device__ __forceinline__ void fused_task(const DevTask& t, const LaunchArgs& a
                              (uint32_t)(bk.first_sub + i), bk.start + ((uint64_t)i << jb.log2_N), a.cand,
                              a.cap, a.count);
         }
+    }
     }
     if (G && nfail) {
         __syncwarp();
@@ -1370,14 +1401,14 @@ cudaError_t upload_coeff_consts(const CoeffConsts& C) {
 // thread per entry; an entry that fails to enclose sets *err.
 __global__ void __launch_bounds__(64) k_coeff_tables(uint64_t* ctab, uint32_t* err) {
     const int e = (int)(blockIdx.x * blockDim.x + threadIdx.x);
-    if (e >= 2 * CT_LEVELS * CT_ENTRIES) return;
+    if (e >= CT_BASES * CT_LEVELS * CT_ENTRIES) return;
     const int base = e / (CT_LEVELS * CT_ENTRIES), level = (e / CT_ENTRIES) % CT_LEVELS, b = e % CT_ENTRIES;
     if (!ct_entry(base, level, b, c_coeff, ctab + ct_index(base, level, b, 0), ctab + ct_index(base, level, b, 1)))
         atomicOr(err, 1u);
 }
 
 cudaError_t launch_coeff_tables(uint64_t* ctab, uint32_t* err, cudaStream_t s) {
-    const int n = 2 * CT_LEVELS * CT_ENTRIES;
+    const int n = CT_BASES * CT_LEVELS * CT_ENTRIES;
     k_coeff_tables<<<(n + 63) / 64, 64, 0, s>>>(ctab, err);
     return cudaGetLastError();
 }

@@ -383,9 +383,10 @@ tmd_status tmd_batch_create_tiled(tmd_ctx* ctx, const tmd_job* jobs, uint32_t nj
  * its block sizes by hand, Sect. V-A): builds the batch with every tiling of
  * nu in {8, 6, 4, 2, 1} x ctas_per_sm in {occupancy .. 1} (one lane per line,
  * one step per iteration), then, for the fastest of those, lanes in {1, 2, 4}
- * x unroll in {1, 2}; times a few graph replays of each on `stream` (CUDA
- * events; records are counted, not stored), and keeps the fastest in the
- * context for batches of the same signature.  *best receives it, *best_ms
+ * x unroll in {1, 2}; times four graph replays of each on `stream` (CUDA
+ * events; records are counted, not stored), times the three fastest again
+ * with sixteen, and keeps the fastest of those in the context for batches of
+ * the same signature.  *best receives it, *best_ms
  * (may be NULL) its mean replay time.  Synchronises `stream`; allocates and
  * frees 8 bytes of device memory. */
 tmd_status tmd_autotune(tmd_ctx* ctx, const tmd_job* jobs, uint32_t njobs, void* stream,

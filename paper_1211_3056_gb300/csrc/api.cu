@@ -29,7 +29,8 @@ cudaError_t launch_persistent(uint32_t L, uint32_t D, bool G, const LaunchArgs& 
 cudaError_t persistent_occupancy(uint32_t L, uint32_t D, bool G, int* blocks_per_sm);
 cudaError_t upload_coeff_consts(const CoeffConsts& C);
 cudaError_t launch_block_tables(const DevJob* jobs, const DevBlock* blocks, uint64_t n_blocks, uint64_t* tables,
-                                uint32_t* status, uint32_t* err, const uint64_t* ctab, cudaStream_t s);
+                                uint32_t* status, uint32_t* err, const uint64_t* ctab, uint32_t func_mask,
+                                cudaStream_t s);
 cudaError_t launch_coeff_tables(uint64_t* ctab, uint32_t* err, cudaStream_t s);
 cudaError_t launch_plan(const DevJob* jobs, uint32_t n_jobs, DevBlock* blocks, uint64_t n_blocks,
                         const uint32_t* class_jobs, const uint64_t* class_task0, uint32_t n_entries,
@@ -454,9 +455,11 @@ cudaError_t expand_plan(const Plan& P, const Layout& L, char* d_arena, uint32_t*
                                 (const uint64_t*)(d_arena + L.o_ctask), (uint32_t)P.class_jobs.size(),
                                 (DevTask*)(d_arena + L.o_tasks), P.n_tasks, s);
     if (e != cudaSuccess) return e;
+    uint32_t func_mask = 0;
+    for (const DevJob& dj : P.jobs) func_mask |= 1u << (dj.func & 3);
     return launch_block_tables((const DevJob*)d_arena, (const DevBlock*)(d_arena + L.o_blocks), P.n_blocks,
                                (uint64_t*)(d_arena + L.o_tables), (uint32_t*)(d_arena + L.o_status), plan_err, ctab,
-                               s);
+                               func_mask, s);
 }
 
 // Arena layout: jobs | blocks | tasks | table status | tables.  The first
@@ -926,40 +929,54 @@ tmd_status tmd_autotune(tmd_ctx* c, const tmd_job* jobs, uint32_t njobs, void* s
         return TMD_ECUDA;
     }
     tmd_status st = TMD_OK;
-    tmd_tiling win = {0, 0, 0, 0};
-    float win_ms = 0.f;
+    // mean replay time of the batch under tiling t (one warm replay first)
+    auto time_tiling = [&](const tmd_tiling& t, int reps, float* out) -> tmd_status {
+        tmd_batch* b = nullptr;
+        tmd_status s2 = batch_create(c, jobs, njobs, nullptr, 0, d_cnt, stream, t, &b, nullptr);
+        if (s2 != TMD_OK) return s2;
+        float ms = 0.f;
+        if (cudaGraphLaunch(b->exec, s) != cudaSuccess || cudaEventRecord(e0, s) != cudaSuccess) s2 = TMD_ECUDA;
+        for (int r = 0; r < reps && s2 == TMD_OK; r++)
+            if (cudaGraphLaunch(b->exec, s) != cudaSuccess) s2 = TMD_ECUDA;
+        if (s2 == TMD_OK && (cudaEventRecord(e1, s) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess ||
+                             cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess))
+            s2 = TMD_ECUDA;
+        tmd_batch_destroy(b);
+        *out = ms / (float)reps;
+        return s2;
+    };
     // stage 1: packet length x resident CTAs (one lane per line, one step
     // per iteration); stage 2: lanes per line x steps per iteration for the
-    // stage-1 winner
+    // stage-1 winner; then the three fastest of all are timed again with
+    // more replays (single timings of a few replays differ by ~1-3 %)
     std::vector<tmd_tiling> cands;
+    std::vector<float> times;
     static const uint32_t nus[] = {8, 6, 4, 2, 1};
     for (uint32_t nu : nus)
         for (int k = occ; k >= 1; k--) cands.push_back(tmd_tiling{nu, (uint32_t)k, 1, 1});
     const size_t stage1 = cands.size();
     for (size_t ci = 0; ci < cands.size() && st == TMD_OK; ci++) {
         if (ci == stage1) {
+            const size_t w = (size_t)(std::min_element(times.begin(), times.end()) - times.begin());
             static const uint32_t lanes_unroll[][2] = {{1, 2}, {2, 1}, {2, 2}, {4, 1}, {4, 2}};
-            for (const auto& lu : lanes_unroll) cands.push_back(tmd_tiling{win.nu, win.ctas_per_sm, lu[0], lu[1]});
+            for (const auto& lu : lanes_unroll)
+                cands.push_back(tmd_tiling{cands[w].nu, cands[w].ctas_per_sm, lu[0], lu[1]});
         }
-        {
-            const tmd_tiling t = cands[ci];
-            tmd_batch* b = nullptr;
-            st = batch_create(c, jobs, njobs, nullptr, 0, d_cnt, stream, t, &b, nullptr);
-            if (st != TMD_OK) break;
-            // one warm replay, then the mean of a few
-            const int reps = 4;
+        float ms = 0.f;
+        st = time_tiling(cands[ci], 4, &ms);
+        times.push_back(ms);
+    }
+    tmd_tiling win = {0, 0, 0, 0};
+    float win_ms = 0.f;
+    if (st == TMD_OK) {
+        std::vector<size_t> order(cands.size());
+        for (size_t i = 0; i < order.size(); i++) order[i] = i;
+        std::sort(order.begin(), order.end(), [&](size_t x, size_t y) { return times[x] < times[y]; });
+        for (size_t r = 0; r < std::min<size_t>(3, order.size()) && st == TMD_OK; r++) {
             float ms = 0.f;
-            if (cudaGraphLaunch(b->exec, s) != cudaSuccess || cudaEventRecord(e0, s) != cudaSuccess) st = TMD_ECUDA;
-            for (int r = 0; r < reps && st == TMD_OK; r++)
-                if (cudaGraphLaunch(b->exec, s) != cudaSuccess) st = TMD_ECUDA;
-            if (st == TMD_OK && (cudaEventRecord(e1, s) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess ||
-                                 cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess))
-                st = TMD_ECUDA;
-            tmd_batch_destroy(b);
-            if (st != TMD_OK) break;
-            ms /= reps;
-            if (win.nu == 0 || ms < win_ms) {
-                win = t;
+            st = time_tiling(cands[order[r]], 16, &ms);
+            if (st == TMD_OK && (win.nu == 0 || ms < win_ms)) {
+                win = cands[order[r]];
                 win_ms = ms;
             }
         }

@@ -34,7 +34,8 @@ cudaError_t launch_block_tables(const DevJob* jobs, const DevBlock* blocks, uint
 cudaError_t launch_coeff_tables(uint64_t* ctab, uint32_t* err, cudaStream_t s);
 cudaError_t launch_plan(const DevJob* jobs, uint32_t n_jobs, DevBlock* blocks, uint64_t n_blocks,
                         const uint32_t* class_jobs, const uint64_t* class_task0, uint32_t n_entries,
-                        DevTask* tasks, uint64_t n_tasks, cudaStream_t s);
+                        DevTask* tasks, uint64_t n_tasks, uint32_t* plan_err, cudaStream_t s);
+cudaError_t launch_zero_counters(uint64_t* misc, uint32_t n_misc, uint64_t* count, cudaStream_t s);
 }  // namespace tmd
 
 namespace tmd {
@@ -102,6 +103,8 @@ struct tmd_ctx {
     size_t stage_cap = 0;
     cudaEvent_t stage_done = nullptr;
     bool stage_pending = false;
+    // pinned landing words of the result read-back (count, error words)
+    uint64_t* h_small = nullptr;
     Plan plan;
     bool resident = false;
     uint64_t upload_bytes = 0;
@@ -453,7 +456,7 @@ cudaError_t expand_plan(const Plan& P, const Layout& L, char* d_arena, uint32_t*
     cudaError_t e = launch_plan((const DevJob*)d_arena, (uint32_t)P.jobs.size(), (DevBlock*)(d_arena + L.o_blocks),
                                 P.n_blocks, (const uint32_t*)(d_arena + L.o_cjobs),
                                 (const uint64_t*)(d_arena + L.o_ctask), (uint32_t)P.class_jobs.size(),
-                                (DevTask*)(d_arena + L.o_tasks), P.n_tasks, s);
+                                (DevTask*)(d_arena + L.o_tasks), P.n_tasks, plan_err, s);
     if (e != cudaSuccess) return e;
     uint32_t func_mask = 0;
     for (const DevJob& dj : P.jobs) func_mask |= 1u << (dj.func & 3);
@@ -496,7 +499,8 @@ tmd_status upload_plan(tmd_ctx* c, cudaStream_t s) {
     c->off_blocks = Lo.o_blocks;
     c->off_tables = Lo.o_tables;
     c->off_tasks = Lo.o_tasks;
-    CK(cudaMemsetAsync(plan_err_ptr(c), 0, sizeof(uint32_t), s));
+    // the plan kernel clears the plan's error word; host-made tables have none
+    if (P.host_tables) CK(cudaMemsetAsync(plan_err_ptr(c), 0, sizeof(uint32_t), s));
     CK(expand_plan(P, Lo, c->d_arena, plan_err_ptr(c), c->d_ctab, s));
     return TMD_OK;
 }
@@ -531,8 +535,7 @@ LaunchArgs task_args(tmd_ctx* c) {
 }
 
 tmd_status reset_counters(tmd_ctx* c, uint64_t* d_count, cudaStream_t s) {
-    CK(cudaMemsetAsync(c->d_misc, 0, sizeof(uint64_t) * (ST_COUNT + 1), s));
-    if (d_count) CK(cudaMemsetAsync(d_count, 0, sizeof(uint64_t), s));
+    CK(launch_zero_counters(c->d_misc, ST_COUNT + 1, d_count, s));
     return TMD_OK;
 }
 
@@ -565,8 +568,9 @@ tmd_status tmd_create(tmd_ctx** out, int device) {
     c->device = device;
     if (cudaDeviceGetAttribute(&c->sms, cudaDevAttrMultiProcessorCount, device) != cudaSuccess ||
         cudaMalloc((void**)&c->d_misc, 64) != cudaSuccess ||
+        cudaHostAlloc((void**)&c->h_small, 64, cudaHostAllocDefault) != cudaSuccess ||
         cudaEventCreateWithFlags(&c->stage_done, cudaEventDisableTiming) != cudaSuccess) {
-        delete c;
+        tmd_destroy(c);
         return TMD_ECUDA;
     }
     cudaMemset(c->d_misc, 0, 64);
@@ -599,6 +603,7 @@ tmd_status tmd_destroy(tmd_ctx* c) {
     if (c->d_misc) cudaFree(c->d_misc);
     if (c->d_ctab) cudaFree(c->d_ctab);
     if (c->h_stage) cudaFreeHost(c->h_stage);
+    if (c->h_small) cudaFreeHost(c->h_small);
     if (c->stage_done) cudaEventDestroy(c->stage_done);
     delete c;
     return TMD_OK;
@@ -733,12 +738,16 @@ tmd_status tmd_candidates(tmd_ctx* c, const tmd_candidate* d_cand, const uint64_
     if (!c || !d_count || !n_out || (h_cap && !h_out)) return TMD_EINVAL;
     cudaStream_t s = (cudaStream_t)stream;
     CK(cudaSetDevice(c->device));
-    uint64_t count = 0;
-    uint32_t err = 0, perr = 0;
-    CK(cudaMemcpyAsync(&count, d_count, sizeof count, cudaMemcpyDeviceToHost, s));
-    CK(cudaMemcpyAsync(&err, err_ptr(c), sizeof err, cudaMemcpyDeviceToHost, s));
-    CK(cudaMemcpyAsync(&perr, plan_err_ptr(c), sizeof perr, cudaMemcpyDeviceToHost, s));
+    // two asynchronous copies into pinned words and one wait (copies to
+    // pageable memory would each wait for the stream)
+    uint64_t* hs = c->h_small;
+    CK(cudaMemcpyAsync(hs, d_count, sizeof(uint64_t), cudaMemcpyDeviceToHost, s));
+    CK(cudaMemcpyAsync(hs + 1, err_ptr(c), 3 * sizeof(uint32_t), cudaMemcpyDeviceToHost, s));
     CK(cudaStreamSynchronize(s));
+    const uint64_t count = hs[0];
+    uint32_t words[3];
+    memcpy(words, hs + 1, sizeof words);
+    const uint32_t err = words[0], perr = words[2];  // words[1]: the queue head
     if (perr) return TMD_EUNSUPPORTED;
     *n_out = count;
     uint64_t n = std::min(count, std::min(cand_cap, h_cap));

@@ -95,30 +95,36 @@ TMD_HD void store_mod_w(const fx::U<NL>& x, bool neg, int L, uint64_t* out) {
     }
 }
 
-// exact (-1)^(k-1) 2^sh / (k M^k) rounded to nearest, mod 2^W
+// c_k = (-1)^(k-1) 2^sh / (k M^k) rounded to nearest, mod 2^W, for k = 1..d
+// (halves rounded up for odd k and toward zero for even k), the slots above
+// d zeroed.  One chain of exact floors serves every order (floor(floor(a/b)
+// / c) = floor(a/(bc))): y_k = floor(2^(sh+1) / M^k), F = floor(y_k / k) =
+// floor(2^(sh+1) / (k M^k)); the rounded value is F/2 for even F and
+// (F+1)/2 for odd F, less one at a tie (the division exact) for even k.
 template <int NL>
-TMD_HD bool log_exact(uint64_t M, int k, int sh, const CoeffConsts& C, int L, uint64_t* out) {
+TMD_HD bool log_orders(uint64_t M, int d, int sh, const CoeffConsts& C, int L, uint64_t* c) {
     if (sh < 0 || sh + 2 >= 64 * NL) return false;
-    const bool neg = (k % 2) == 0;
-    fx::U<NL> den, x;
-    fx::set_zero(den);
-    den.w[0] = (uint64_t)k;
-    for (int i = 0; i < k; i++)
-        if (fx::mul_u64(den, M)) return false;
-    fx::set_pow2(x, (unsigned)sh + 1);
-    fx::add(x, den);
-    if (neg) {
-        fx::U<NL> one;
-        fx::set_zero(one);
-        one.w[0] = 1;
-        fx::sub(x, one);
-    }
-    // floor((2 num + den [- 1]) / (2 den)) as a chain of exact floors
-    fx::div_u64(x, C.div.r[2]);
-    fx::div_u64(x, C.div.r[k]);
     const fx::Recip RM = fx::make_recip(M);
-    for (int i = 0; i < k; i++) fx::div_u64(x, RM);
-    store_mod_w(x, neg, L, out);
+    fx::U<NL> y;
+    fx::set_pow2(y, (unsigned)sh + 1);
+    bool exact = true;
+#pragma unroll 1
+    for (int k = 1; k <= COEFF_MAX_DEG; k++) {
+        if (k > d) {
+#pragma unroll
+            for (int l = 0; l < COEFF_MAX_LIMBS; l++) c[k * COEFF_MAX_LIMBS + l] = 0;
+            continue;
+        }
+        const uint64_t ry = fx::div_u64(y, RM);
+        exact = exact && ry == 0;
+        fx::U<NL> F = y;
+        const uint64_t rk = fx::div_u64(F, C.div.r[k]);
+        const bool neg = (k % 2) == 0;
+        const bool up = (F.w[0] & 1) && !(neg && exact && rk == 0);
+        fx::shr(F, 1);
+        if (up) fx::add_u64(F, 1);
+        store_mod_w(F, neg, L, c + k * COEFF_MAX_LIMBS);
+    }
     return true;
 }
 
@@ -199,13 +205,14 @@ TMD_HD bool exp_reduced(const CoeffJob& J, uint64_t M, unsigned PB, const CoeffC
 
 // Tables of the device path for exp, 2^x and log: entry (base, level i, b) is
 // an enclosure of base^(b 2^(-8 i)), i = 1..10, b < 256 (base 0: e, base 1:
-// 2), level 0 of base e holds e^n, n < 4, and level 0 of "base" 2 holds
-// log(256 + b); lo and hi ends of CT_LIMBS limbs with CT_BITS fractional
-// bits.  An argument X = n + sum_i b_i 2^(-8 i) with at most 80 fractional
-// bits then has e^X (2^X) as the product of at most 11 entries (2^n exact),
-// with no series per block (the table-driven method of Tang's exponential,
-// here with rigorous enclosures at every step); log X takes the entry of
-// the argument's top 9 bits g and a short atanh series of the rest.
+// 2), level 0 of base e holds e^n, n < 4, level 0 of "base" 2 holds
+// log(256 + b) and its level 1 log(1 + b 2^-16); lo and hi ends of CT_LIMBS
+// limbs with CT_BITS fractional bits.  An argument X = n + sum_i b_i
+// 2^(-8 i) with at most 80 fractional bits then has e^X (2^X) as the product
+// of at most 11 entries (2^n exact), with no series per block (the
+// table-driven method of Tang's exponential, here with rigorous enclosures
+// at every step); log X takes the entries of the argument's top 9 bits and
+// of the next 8 and a short atanh series of the rest.
 enum { CT_BASES = 3, CT_LEVELS = 11, CT_ENTRIES = 256, CT_LIMBS = 12, CT_BITS = 64 * CT_LIMBS - 68 };
 
 TMD_HD size_t ct_index(int base, int level, int b, int end) {
@@ -219,8 +226,17 @@ constexpr size_t CT_WORDS = (size_t)CT_BASES * CT_LEVELS * CT_ENTRIES * 2 * CT_L
 TMD_HD bool ct_entry(int base, int level, int b, const CoeffConsts& C, uint64_t* lo, uint64_t* hi) {
     using namespace fx;
     Enc<CT_LIMBS> f;
-    if (base == 2) {  // log(256 + b) at level 0 (the other levels are unused)
-        if (level != 0) {
+    if (base == 2) {  // log(256 + b) at level 0, log(1 + b 2^-16) at level 1
+        if (level == 1 && b > 0) {  // 2 atanh(b / (2^17 + b))
+            U<CT_LIMBS> S;
+            uint64_t E;
+            if (!atanh_ratio<CT_LIMBS>((uint64_t)b, (1ull << 17) + (uint64_t)b, CT_BITS, C.div, S, E)) return false;
+            f.lo = S;
+            f.hi = S;
+            add_u64(f.hi, E);
+            mul_u64(f.lo, 2);
+            mul_u64(f.hi, 2);
+        } else if (level != 0) {  // log 1 and the unused levels
             set_zero(f.lo);
             set_zero(f.hi);
         } else {
@@ -322,20 +338,33 @@ TMD_HD void ct_load(const uint64_t* tab, int base, int level, int b, fx::U<NL>& 
     if (NL < CT_LIMBS) fx::add_u64(hi, 1);
 }
 
+// The lower end only (truncated to PA fractional bits).
+template <int NL>
+TMD_HD void ct_load_lo(const uint64_t* tab, int base, int level, int b, fx::U<NL>& lo) {
+    static_assert(NL <= CT_LIMBS, "table entries hold CT_LIMBS limbs");
+    const uint64_t* e = tab + ct_index(base, level, b, 0);
+#pragma unroll
+    for (int i = 0; i < NL; i++) lo.w[i] = e[CT_LIMBS - NL + i];
+}
+
 // Enclosure of f(X) 2^-red (exp with red = 0, 2^x) with PB fractional bits
 // from the tables: X = n + sum_i b_i 2^(-8 i) (the fraction of X = M 2^-q
 // left-aligned to 80 bits), f = e^n prod_i T(0, i, b_i) for exp and
 // 2^n prod_i T(1, i, b_i) for 2^x, the products formed at PA fractional bits
-// (lower end truncated, upper end raised by two units per product) and
-// shifted to PB bits.  False when the tables do not apply (log, exp above
+// (below CT_LIMBS limbs the lower ends' product and a bound on its error,
+// at CT_LIMBS limbs both ends) and shifted to PB bits.  False when the tables do not apply (log, exp above
 // [2, 4), more than 80 fractional bits), so that the caller takes the
 // series.
 // log X for X = M 2^(e_in - p): with g = the top 9 bits of M (256 <= g <
-// 512) and G = g 2^(p - 9), X = g (M / G) 2^(e_in - 9), so
-//   log X = log g + (e_in - 9) ln 2 + 2 atanh((M - G) / (M + G)),
-// the ratio below 2^-9: a series of ~P/18 terms instead of ~P/3.2 for the
-// direct atanh of (2^p - M)/(2^p + M) <= 1/3.  log g from the tables, ln 2
-// from the constants, all with PB fractional bits (PB + 8 <= PA).
+// 512), G = g 2^(p - 9), the next 8 bits h = floor((M - G) / (g 2^(p - 25)))
+// (h < 256; h = 0 for p < 25) and M' = G (1 + h 2^-16) = G + g h 2^(p - 25)
+// <= M, X = g (1 + h 2^-16) (M / M') 2^(e_in - 9), so
+//   log X = log g + log(1 + h 2^-16) + (e_in - 9) ln 2
+//           + 2 atanh((M - M') / (M + M')),
+// the ratio below 2^-17 (M - M' < G 2^-16): a series of ~P/34 terms instead
+// of ~P/3.2 for the direct atanh of (2^p - M)/(2^p + M) <= 1/3.  log g and
+// log(1 + h 2^-16) from the tables, ln 2 from the constants, all with PB
+// fractional bits (PB + 8 <= PA).
 template <int NL>
 TMD_HD bool f_table_log(const CoeffJob& J, uint64_t M, unsigned PB, const uint64_t* tab, const CoeffConsts& C,
                         fx::Enc<NL>& f) {
@@ -345,11 +374,24 @@ TMD_HD bool f_table_log(const CoeffJob& J, uint64_t M, unsigned PB, const uint64
     const unsigned sh = (unsigned)(J.p - 9);
     const uint64_t g = M >> sh, G = g << sh;
     if (g < 256 || g >= 512) return false;
+    uint32_t h = 0;
+    uint64_t Mp = G;
+    if (J.p >= 25) {
+        const unsigned s2 = (unsigned)(J.p - 25);
+        h = (uint32_t)((M - G) >> s2) / (uint32_t)g;  // (M - G) >> s2 < 2^16
+        Mp = G + (((uint64_t)g * h) << s2);
+    }
     U<NL> S;
     uint64_t E;
-    if (!atanh_ratio<NL>(M - G, M + G, PB, C.div, S, E)) return false;
+    if (!atanh_ratio<NL>(M - Mp, M + Mp, PB, C.div, S, E)) return false;
     U<NL> tlo, thi;
     ct_load<NL>(tab, 2, 0, (int)(g - 256), tlo, thi);
+    if (h) {
+        U<NL> ulo, uhi;
+        ct_load<NL>(tab, 2, 1, (int)h, ulo, uhi);
+        add(tlo, ulo);
+        add(thi, uhi);
+    }
     const unsigned s = PA - PB;
     const bool up = low_bits(thi, s);
     shr(tlo, s);
@@ -419,25 +461,58 @@ TMD_HD bool f_table(const CoeffJob& J, uint64_t M, unsigned PB, const uint64_t* 
     }
     const int base = J.func == 0 ? 0 : 1;
     U<NL> lo, hi;
-    if (base == 0) {
-        ct_load<NL>(tab, 0, 0, (int)n, lo, hi);
-    } else {
-        set_pow2(lo, PA + (unsigned)n);
-        hi = lo;
-    }
+    if (NL < CT_LIMBS) {
+        // One chain, of the lower ends, and a bound for the upper end.  With
+        // u = 2^-PA, every lower end t' of a factor t >= 1 (an entry truncated
+        // from CT_BITS to PA bits; the entries' own widths are far below u)
+        // has t - 2u < t' <= t, and every truncated product x' = mul_trunc(x,
+        // t') has x t' - 2u < x' <= x t'.  With P_k the exact product of the
+        // first k factors (P_k >= 1) and x_k its lower end,
+        //   P_k - x_k <= P_(k-1) (t - t') + (P_(k-1) - x_(k-1)) t + 2u,
+        // so (P_k - x_k) / P_k grows by at most 4u per product: at most 42u
+        // after the start and ten products, and P < 2^6 (X < 4) gives
+        // P - x < 2688u < 2^12 u.
+        if (base == 0) {
+            ct_load_lo<NL>(tab, 0, 0, (int)n, lo);
+        } else {
+            set_pow2(lo, PA + (unsigned)n);
+        }
 #pragma unroll 1
-    for (int i = 1; i <= 10; i++) {
-        const unsigned pos = 80u - 8u * (unsigned)i;  // bits [pos, pos + 8) of V
-        const unsigned b = pos >= 64 ? (unsigned)(vh >> (pos - 64)) & 255u
-                                     : (unsigned)((vl >> pos) | (pos > 56 ? vh << (64 - pos) : 0)) & 255u;
-        if (b == 0) continue;
-        U<NL> tlo, thi, r;
-        ct_load<NL>(tab, base, i, (int)b, tlo, thi);
-        mul_trunc<NL>(lo, tlo, r);
-        lo = r;
-        mul_trunc<NL>(hi, thi, r);
-        hi = r;
-        add_u64(hi, 2);
+        for (int i = 1; i <= 10; i++) {
+            const unsigned pos = 80u - 8u * (unsigned)i;  // bits [pos, pos + 8) of V
+            const unsigned b = pos >= 64 ? (unsigned)(vh >> (pos - 64)) & 255u
+                                         : (unsigned)((vl >> pos) | (pos > 56 ? vh << (64 - pos) : 0)) & 255u;
+            if (b == 0) continue;
+            U<NL> t, r;
+            ct_load_lo<NL>(tab, base, i, (int)b, t);
+            mul_trunc<NL>(lo, t, r);
+            lo = r;
+        }
+        hi = lo;
+        add_u64(hi, 1ull << 12);
+    } else {
+        // at the entries' own width: both ends, each product's upper end
+        // raised by two units
+        if (base == 0) {
+            ct_load<NL>(tab, 0, 0, (int)n, lo, hi);
+        } else {
+            set_pow2(lo, PA + (unsigned)n);
+            hi = lo;
+        }
+#pragma unroll 1
+        for (int i = 1; i <= 10; i++) {
+            const unsigned pos = 80u - 8u * (unsigned)i;
+            const unsigned b = pos >= 64 ? (unsigned)(vh >> (pos - 64)) & 255u
+                                         : (unsigned)((vl >> pos) | (pos > 56 ? vh << (64 - pos) : 0)) & 255u;
+            if (b == 0) continue;
+            U<NL> tlo, thi, r;
+            ct_load<NL>(tab, base, i, (int)b, tlo, thi);
+            mul_trunc<NL>(lo, tlo, r);
+            lo = r;
+            mul_trunc<NL>(hi, thi, r);
+            hi = r;
+            add_u64(hi, 2);
+        }
     }
     const unsigned s = PA - PB;
     const bool up = low_bits(hi, s);
@@ -558,23 +633,33 @@ TMD_HD bool block_coeffs(const CoeffJob& J, uint64_t M, int guard, const CoeffCo
         cf_detail::rn_shift(f.hi, (unsigned)s);
         if (!equal(f.lo, f.hi)) return false;
         cf_detail::store_mod_w(f.lo, false, J.L, c);
-#pragma unroll 1
-        for (int k = 1; k <= COEFF_MAX_DEG; k++) {
-            if (k > J.d) {
-#pragma unroll
-                for (int l = 0; l < COEFF_MAX_LIMBS; l++) c[k * COEFF_MAX_LIMBS + l] = 0;
-                continue;
-            }
-            const int Ek = E0 + k * (J.e_in - J.p);
-            if (!cf_detail::log_exact<NL>(M, k, Ek + k * (int)q, C, J.L, c + k * COEFF_MAX_LIMBS)) return false;
-        }
-        return true;
+        // the order-k coefficient's scale 2^(E0 + k (e_in - p)) times the
+        // k-th power of the argument's 2^(p - e_in) leaves 2^E0 for every k
+        return cf_detail::log_orders<NL>(M, J.d, E0, C, J.L, c);
     }
     // exp or 2^x: the enclosure of f(X_t) has P2 = PB fractional bits
     const unsigned P2 = PB;
     U<NL> l2lo, l2hi;
     if (J.func == 1) cf_detail::ln2_at<NL>(C, P2, l2lo, l2hi);
     U<NL> plo = f.lo, phi = f.hi;  // f (ln 2)^k enclosure, updated per order
+    // 2^x: one chain of lower ends x_k = floor(x_(k-1) l / 2^P2), l the lower
+    // ln 2 (l <= L2 = 2^P2 ln 2 < l + 2), and a bound w_k on the distance of
+    // x_k to v_k = 2^P2 f (ln 2)^k instead of a second chain: v_k - x_k <=
+    // (v_(k-1) (L2 - l) + (v_(k-1) - x_(k-1)) l) / 2^P2 + 1 < 2 Bf + (3/4)
+    // w_(k-1) + 1 with f < Bf, starting from the width of f's enclosure
+    // (both ends kept when that width or f is too large for the bound)
+    bool one_chain = false;
+    uint64_t wk = 0, Bf2 = 0;
+    if (J.func == 1) {
+        U<NL> wd = f.hi;
+        sub(wd, f.lo);
+        const unsigned fb = bit_length(f.hi);
+        if (bit_length(wd) <= 32 && fb <= P2 + 32) {
+            one_chain = true;
+            wk = wd.w[0];
+            Bf2 = 2ull << (fb > P2 ? fb - P2 : 0);
+        }
+    }
 #pragma unroll 1
     for (int k = 0; k <= COEFF_MAX_DEG; k++) {
         if (k > J.d) {
@@ -586,11 +671,17 @@ TMD_HD bool block_coeffs(const CoeffJob& J, uint64_t M, int guard, const CoeffCo
             U<NL> t;
             mul_shr(plo, l2lo, P2, t);
             plo = t;
-            // upper end: ceil of the product
-            U<NL> hprod;
-            mul_shr(phi, l2hi, P2, hprod);
-            add_u64(hprod, 1);
-            phi = hprod;
+            if (one_chain) {
+                wk = wk - wk / 4 + Bf2 + 2;
+                phi = plo;
+                add_u64(phi, wk);
+            } else {
+                // upper end: ceil of the product
+                U<NL> hprod;
+                mul_shr(phi, l2hi, P2, hprod);
+                add_u64(hprod, 1);
+                phi = hprod;
+            }
             exact = false;
         }
         U<NL> lo = plo, hi = phi;
@@ -621,78 +712,80 @@ TMD_HD bool block_coeffs(const CoeffJob& J, uint64_t M, int guard, const CoeffCo
 // The 2d+1 table words from the coefficients c[k*COEFF_MAX_LIMBS + l]: w =
 // 0..d are Delta^w g0(0) with g0(i) = R(iN), w = d+1..2d are
 // Delta^(w-d-1) g1(0) with g1(i) = R(iN+1) - R(iN), all mod 2^W; table[w*L +
-// l].
+// l].  Closed forms instead of values and differences: as polynomials in i,
+// g0(i) = sum_j a_j i^j with a_j = c_j N^j, and g1(i) = sum_{j<d} b_j i^j
+// with b_j = N^j sum_{k>j} C(k, j) c_k (R shifted by one, less R).  The
+// w-th forward difference of i^j at i = 0 is w! S(j, w) (S the Stirling
+// numbers of the second kind; w! S(j, w) counts the maps of a j-set onto a
+// w-set), so
+//     Delta^w g0(0) = sum_{j>=w} a_j w! S(j, w),
+//     Delta^w g1(0) = sum_{j>=w} b_j w! S(j, w).
+// Every step is a ring operation, so the words equal the differences of the
+// values mod 2^W exactly; N^j is a shift.  The coefficients above d are zero.
+namespace cf_detail {
+// acc += m x (mod 2^(64 COEFF_MAX_LIMBS)) for a small constant m
+TMD_HD void add_mul_small(fx::U<COEFF_MAX_LIMBS>& acc, const fx::U<COEFF_MAX_LIMBS>& x, uint32_t m) {
+    if (m == 0) return;
+    if (m == 1) {
+        fx::add(acc, x);
+        return;
+    }
+    fx::U<COEFF_MAX_LIMBS> t = x;
+    fx::mul_u64(t, m);
+    fx::add(acc, t);
+}
+}  // namespace cf_detail
+
 TMD_HD void block_table_words(const CoeffJob& J, const uint64_t* c, uint64_t* table) {
     using namespace fx;
+    using V = U<COEFF_MAX_LIMBS>;
+    constexpr int D = COEFF_MAX_DEG;
+    static_assert(D == 4, "the constants below cover degrees up to 4");
+    // binom[k][j] = C(k, j); surj[j][w] = w! S(j, w)
+    constexpr uint32_t binom[D + 1][D + 1] = {
+        {1, 0, 0, 0, 0}, {1, 1, 0, 0, 0}, {1, 2, 1, 0, 0}, {1, 3, 3, 1, 0}, {1, 4, 6, 4, 1}};
+    constexpr uint32_t surj[D + 1][D + 1] = {
+        {1, 0, 0, 0, 0}, {0, 1, 0, 0, 0}, {0, 1, 2, 0, 0}, {0, 1, 6, 6, 0}, {0, 1, 14, 36, 24}};
     const int L = J.L, d = J.d;
-    const uint64_t N = 1ull << J.log2_N;
-    U<COEFF_MAX_LIMBS> g0[COEFF_MAX_DEG + 1], g1[COEFF_MAX_DEG];
-#pragma unroll 1
-    for (int i = 0; i <= COEFF_MAX_DEG; i++) {
-        if (i > d) break;
-#pragma unroll 1
-        for (int pass = 0; pass < 2; pass++) {
-            const uint64_t y = (uint64_t)i * N + (uint64_t)pass;
-            // R(y) mod 2^W by Horner from the top coefficient
-            U<COEFF_MAX_LIMBS> acc;
-            set_zero(acc);
-#pragma unroll 1
-            for (int k = COEFF_MAX_DEG; k >= 0; k--) {
-                if (k > d) continue;
-                mul_u64(acc, y);
-                U<COEFF_MAX_LIMBS> ck;
-#pragma unroll 1
-                for (int l = 0; l < COEFF_MAX_LIMBS; l++) ck.w[l] = c[k * COEFF_MAX_LIMBS + l];
-                add(acc, ck);
-#pragma unroll 1
-                for (int l = 0; l < COEFF_MAX_LIMBS; l++)
-                    if (l >= L) acc.w[l] = 0;  // mod 2^W
-            }
-            if (pass == 0) {
-                g0[i] = acc;
-            } else if (i < d) {
-                U<COEFF_MAX_LIMBS> t = acc;
-                sub(t, g0[i]);
-#pragma unroll 1
-                for (int l = 0; l < COEFF_MAX_LIMBS; l++)
-                    if (l >= L) t.w[l] = 0;
-                g1[i < COEFF_MAX_DEG ? i : 0] = t;
-            }
-        }
+    const unsigned lg = (unsigned)J.log2_N;
+    V ck[D + 1], a[D + 1], b[D];
+#pragma unroll
+    for (int k = 0; k <= D; k++)
+#pragma unroll
+        for (int l = 0; l < COEFF_MAX_LIMBS; l++) ck[k].w[l] = c[k * COEFF_MAX_LIMBS + l];
+#pragma unroll
+    for (int j = 0; j <= D; j++) {
+        a[j] = ck[j];
+        shl(a[j], (unsigned)j * lg);
     }
-#pragma unroll 1
-    for (int lev = 0; lev <= COEFF_MAX_DEG; lev++) {
-        if (lev > d) break;
-#pragma unroll 1
-        for (int l = 0; l < COEFF_MAX_LIMBS; l++)
-            if (l < L) table[lev * L + l] = g0[0].w[l];
-#pragma unroll 1
-        for (int i = 0; i < COEFF_MAX_DEG; i++) {  // g0[i] <- g0[i+1] - g0[i]  (mod 2^W)
-            if (i + lev >= d) break;
-            U<COEFF_MAX_LIMBS> t = g0[i + 1];
-            sub(t, g0[i]);
-#pragma unroll 1
-            for (int l = 0; l < COEFF_MAX_LIMBS; l++)
-                if (l >= L) t.w[l] = 0;
-            g0[i] = t;
-        }
+#pragma unroll
+    for (int j = 0; j < D; j++) {
+        set_zero(b[j]);
+#pragma unroll
+        for (int k = j + 1; k <= D; k++) cf_detail::add_mul_small(b[j], ck[k], binom[k][j]);
+        shl(b[j], (unsigned)j * lg);
     }
-#pragma unroll 1
-    for (int lev = 0; lev < COEFF_MAX_DEG; lev++) {
-        if (lev >= d) break;
-#pragma unroll 1
+#pragma unroll
+    for (int w = 0; w <= D; w++) {
+        if (w > d) break;
+        V t;
+        set_zero(t);
+#pragma unroll
+        for (int j = w; j <= D; j++) cf_detail::add_mul_small(t, a[j], surj[j][w]);
+#pragma unroll
         for (int l = 0; l < COEFF_MAX_LIMBS; l++)
-            if (l < L) table[(d + 1 + lev) * L + l] = g1[0].w[l];
-#pragma unroll 1
-        for (int i = 0; i + 1 < COEFF_MAX_DEG; i++) {
-            if (i + lev + 1 >= d) break;
-            U<COEFF_MAX_LIMBS> t = g1[i + 1];
-            sub(t, g1[i]);
-#pragma unroll 1
-            for (int l = 0; l < COEFF_MAX_LIMBS; l++)
-                if (l >= L) t.w[l] = 0;
-            g1[i] = t;
-        }
+            if (l < L) table[w * L + l] = t.w[l];
+    }
+#pragma unroll
+    for (int w = 0; w < D; w++) {
+        if (w >= d) break;
+        V t;
+        set_zero(t);
+#pragma unroll
+        for (int j = w; j < D; j++) cf_detail::add_mul_small(t, b[j], surj[j][w]);
+#pragma unroll
+        for (int l = 0; l < COEFF_MAX_LIMBS; l++)
+            if (l < L) table[(d + 1 + w) * L + l] = t.w[l];
     }
 }
 

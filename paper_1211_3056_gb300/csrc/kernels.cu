@@ -1296,52 +1296,66 @@ __global__ void __launch_bounds__(256) k_lower_bounds(const uint64_t* B, const u
 // Block and task records from the per-job segment table (Sect. III-A split
 // and Sect. IV blocks: blocks of T arguments from each segment start, the
 // last one of a segment shorter; packets of nu sub-intervals per block).
-__global__ void __launch_bounds__(256) k_plan_blocks(const DevJob* jobs, uint32_t n_jobs, DevBlock* blocks,
-                                                     uint64_t n_blocks) {
-    const uint64_t b = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (b >= n_blocks) return;
-    uint32_t lo = 0, hi = n_jobs - 1;
-    while (lo < hi) {  // last job whose first block is <= b
-        const uint32_t mid = (lo + hi + 1) >> 1;
-        if (jobs[mid].block_off <= b) lo = mid; else hi = mid - 1;
+// One thread per block record and per task record (one launch for both);
+// thread 0 also clears the plan's error word before the table kernels run.
+// Blocks: the last job whose first block is <= b.  Tasks are laid out class
+// by class (class_jobs lists the jobs of each (limbs, degree) class in
+// order; class_task0 their first task), 32 packets per task within a job.
+__global__ void __launch_bounds__(256) k_plan(const DevJob* jobs, uint32_t n_jobs, DevBlock* blocks, uint64_t n_blocks,
+                                              const uint32_t* class_jobs, const uint64_t* class_task0,
+                                              uint32_t n_entries, DevTask* tasks, uint64_t n_tasks,
+                                              uint32_t* plan_err) {
+    const uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i == 0) *plan_err = 0;
+    if (i < n_blocks) {
+        uint32_t lo = 0, hi = n_jobs - 1;
+        while (lo < hi) {
+            const uint32_t mid = (lo + hi + 1) >> 1;
+            if (jobs[mid].block_off <= i) lo = mid; else hi = mid - 1;
+        }
+        blocks[i] = block_record(jobs[lo], lo, i - jobs[lo].block_off);
     }
-    blocks[b] = block_record(jobs[lo], lo, b - jobs[lo].block_off);
-}
-
-// Tasks are laid out class by class (class_jobs lists the jobs of each
-// (limbs, degree) class in order; class_task0 their first task), 32 packets
-// per task within a job.
-__global__ void __launch_bounds__(256) k_plan_tasks(const DevJob* jobs, const uint32_t* class_jobs,
-                                                    const uint64_t* class_task0, uint32_t n_entries,
-                                                    DevTask* tasks, uint64_t n_tasks) {
-    const uint64_t t = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (t >= n_tasks) return;
-    uint32_t lo = 0, hi = n_entries - 1;
-    while (lo < hi) {
-        const uint32_t mid = (lo + hi + 1) >> 1;
-        if (class_task0[mid] <= t) lo = mid; else hi = mid - 1;
+    if (i < n_tasks) {
+        uint32_t lo = 0, hi = n_entries - 1;
+        while (lo < hi) {
+            const uint32_t mid = (lo + hi + 1) >> 1;
+            if (class_task0[mid] <= i) lo = mid; else hi = mid - 1;
+        }
+        const uint32_t j = class_jobs[lo];
+        tasks[i] = task_record(jobs[j], j, i - class_task0[lo]);
     }
-    const uint32_t j = class_jobs[lo];
-    tasks[t] = task_record(jobs[j], j, t - class_task0[lo]);
 }
 
 cudaError_t launch_plan(const DevJob* jobs, uint32_t n_jobs, DevBlock* blocks, uint64_t n_blocks,
                         const uint32_t* class_jobs, const uint64_t* class_task0, uint32_t n_entries,
-                        DevTask* tasks, uint64_t n_tasks, cudaStream_t s) {
-    if (n_blocks) k_plan_blocks<<<(unsigned)((n_blocks + 255) / 256), 256, 0, s>>>(jobs, n_jobs, blocks, n_blocks);
-    if (n_tasks)
-        k_plan_tasks<<<(unsigned)((n_tasks + 255) / 256), 256, 0, s>>>(jobs, class_jobs, class_task0, n_entries,
-                                                                       tasks, n_tasks);
+                        DevTask* tasks, uint64_t n_tasks, uint32_t* plan_err, cudaStream_t s) {
+    const uint64_t n = n_blocks > n_tasks ? n_blocks : n_tasks;
+    k_plan<<<(unsigned)((n + 255) / 256 + (n == 0)), 256, 0, s>>>(jobs, n_jobs, blocks, n_blocks, class_jobs,
+                                                                   class_task0, n_entries, tasks, n_tasks, plan_err);
+    return cudaGetLastError();
+}
+
+// The statistics and error words (n_misc words) and a candidate count, in one
+// launch instead of two memsets.
+__global__ void k_zero_counters(uint64_t* misc, uint32_t n_misc, uint64_t* count) {
+    const uint32_t i = threadIdx.x;
+    if (i < n_misc) misc[i] = 0;
+    if (i == 0 && count) *count = 0;
+}
+
+cudaError_t launch_zero_counters(uint64_t* misc, uint32_t n_misc, uint64_t* count, cudaStream_t s) {
+    k_zero_counters<<<1, 32, 0, s>>>(misc, n_misc, count);
     return cudaGetLastError();
 }
 
 // ---------------------------------------------------------- block tables
 // One thread per Taylor block: correctly rounded coefficients of R_t and the
 // 2d+1 step-N difference words (the host path runs the same routine).  Pass
-// 0 works with 512-bit words and 64 guard bits; pass 1, a kernel of its own
-// (its 768-bit code stays out of pass 0's instruction cache), redoes only
-// the blocks left undecided with 320 guard bits (Ziv); a block still
-// undecided raises ERR_ROUNDING in the error word.  (The per-job anchors of
+// 0 works with 384-bit words and 32 guard bits; pass 1, a kernel of its own
+// (its wider code stays out of pass 0's instruction cache), redoes only the
+// blocks left undecided, at 512 bits with 64 guard bits, then at 768 bits
+// with 320 (Ziv); a block still undecided raises ERR_ROUNDING in the error
+// word.  (The per-job anchors of
 // the host path are not used here: on the device the anchor's own
 // evaluation would sit in front of every block's on the critical path.)
 __constant__ CoeffConsts c_coeff;
@@ -1376,7 +1390,10 @@ __global__ void __launch_bounds__(64) k_block_tables(const DevJob* jobs, const D
     J.func = F;
     const uint64_t M = (1ull << (jb.p - 1)) + bk.start;
     uint64_t c[(COEFF_MAX_DEG + 1) * COEFF_MAX_LIMBS];
-    const bool ok = block_coeffs<8>(J, M, 64, c_coeff, c, nullptr, ctab);
+    // 384 bits with 32 guard bits below the coefficients' last place: an
+    // undecided rounding (odds ~2^-40 per coefficient) or a job whose words
+    // need more bits goes to k_block_tables_wide (512, then 768 bits)
+    const bool ok = block_coeffs<6>(J, M, 32, c_coeff, c, nullptr, ctab);
     if (ok) block_table_words(J, c, tables + bk.table_off);
     if (ok && (jb.flags & TMD_SOUND)) coeffs_packed(J, c, tables + bk.table_off + (2 * J.d + 1) * J.L);
     status[b] = ok ? 0 : 1;
@@ -1392,7 +1409,7 @@ __global__ void __launch_bounds__(64) k_block_tables_wide(const DevJob* jobs, co
     const CoeffJob J = block_coeff_job(jb, bk.e_out);
     const uint64_t M = (1ull << (jb.p - 1)) + bk.start;
     uint64_t c[(COEFF_MAX_DEG + 1) * COEFF_MAX_LIMBS];
-    if (block_coeffs<12>(J, M, 320, c_coeff, c, nullptr, ctab)) {
+    if (block_coeffs<8>(J, M, 64, c_coeff, c, nullptr, ctab) || block_coeffs<12>(J, M, 320, c_coeff, c, nullptr, ctab)) {
         block_table_words(J, c, tables + bk.table_off);
         if (jb.flags & TMD_SOUND) coeffs_packed(J, c, tables + bk.table_off + (2 * J.d + 1) * J.L);
         status[b] = 0;

@@ -41,6 +41,15 @@ class Context:
         check(lib().tmd_create(ctypes.byref(h), int(device)), "tmd_create")
         self.handle = h
         self.device = int(device)
+        self._h_out = None  # host record buffer of tmd_candidates, reused
+
+    def host_records(self, n: int):
+        """A host array of at least n candidate records, kept between calls
+        (a fresh one per call costs a zeroed allocation of its whole size)."""
+        n = max(1, int(n))
+        if self._h_out is None or len(self._h_out) < n:
+            self._h_out = (_lib.tmd_candidate * n)()
+        return self._h_out
 
     def close(self):
         if self.handle:
@@ -128,7 +137,7 @@ def tmd_candidates(ctx: Context, d_cand, d_count, h_cap: Optional[int] = None, s
     cap = 0 if d_cand is None else (d_cand.numel() * d_cand.element_size()) // CANDIDATE_BYTES
     if h_cap is None:
         h_cap = cap
-    out = (_lib.tmd_candidate * max(1, h_cap))()
+    out = ctx.host_records(h_cap)
     n = ctypes.c_uint64(0)
     st = lib().tmd_candidates(ctx.handle, _ptr(d_cand), _ptr(d_count), cap, out, h_cap,
                               ctypes.byref(n), _stream_ptr(stream))
@@ -312,8 +321,12 @@ class Server:
 
     def poll(self, cap: int = 256, rec_cap: int = 1 << 16, wait_ms: int = 0):
         """[(result dict, [(job, subint, arg_index, value), ...]), ...]"""
-        res = (_lib.tmd_job_result * cap)()
-        recs = (_lib.tmd_candidate * max(1, rec_cap))()
+        # result and record arrays kept between polls (fresh zeroed arrays of
+        # rec_cap records would cost more than a poll)
+        if getattr(self, "_poll_bufs", None) is None or len(self._poll_bufs[0]) < cap \
+                or len(self._poll_bufs[1]) < max(1, rec_cap):
+            self._poll_bufs = ((_lib.tmd_job_result * cap)(), (_lib.tmd_candidate * max(1, rec_cap))())
+        res, recs = self._poll_bufs
         n = ctypes.c_uint32(0)
         nr = ctypes.c_uint64(0)
         check(lib().tmd_server_poll(self.handle, res, cap, ctypes.byref(n), recs, rec_cap, ctypes.byref(nr),

@@ -102,7 +102,8 @@ TMD_HD void store_mod_w(const fx::U<NL>& x, bool neg, int L, uint64_t* out) {
 // floor(2^(sh+1) / (k M^k)); the rounded value is F/2 for even F and
 // (F+1)/2 for odd F, less one at a tie (the division exact) for even k.
 template <int NL>
-TMD_HD bool log_orders(uint64_t M, int d, int sh, const CoeffConsts& C, int L, uint64_t* c) {
+TMD_HD bool log_orders(uint64_t M, int d, int sh, const CoeffConsts& C, int L, uint64_t* c, int part = 0,
+                       int step = 1) {
     if (sh < 0 || sh + 2 >= 64 * NL) return false;
     const fx::Recip RM = fx::make_recip(M);
     fx::U<NL> y;
@@ -111,12 +112,14 @@ TMD_HD bool log_orders(uint64_t M, int d, int sh, const CoeffConsts& C, int L, u
 #pragma unroll 1
     for (int k = 1; k <= COEFF_MAX_DEG; k++) {
         if (k > d) {
+            if (k % step == part)
 #pragma unroll
-            for (int l = 0; l < COEFF_MAX_LIMBS; l++) c[k * COEFF_MAX_LIMBS + l] = 0;
+                for (int l = 0; l < COEFF_MAX_LIMBS; l++) c[k * COEFF_MAX_LIMBS + l] = 0;
             continue;
         }
         const uint64_t ry = fx::div_u64(y, RM);
         exact = exact && ry == 0;
+        if (k % step != part) continue;
         fx::U<NL> F = y;
         const uint64_t rk = fx::div_u64(F, C.div.r[k]);
         const bool neg = (k % 2) == 0;
@@ -608,10 +611,14 @@ TMD_HD bool f_anchored(const CoeffJob& J, uint64_t M, unsigned PB, const CoeffCo
 // table-word loops stay rolled: unrolled to the largest degree they keep the
 // coefficients in registers but make the table kernel, one or two warps per
 // SM on small plans, wait on instruction fetches -- 44 against 63 us on the
-// 4096 blocks of a 2^36-argument slice.)
+// 4096 blocks of a 2^36-argument slice.)  With step > 1 the caller splits
+// the orders over `step` threads: this one writes the slots of the orders k
+// with k % step == part (f(X_t), and the chains of 2^x and log, are formed
+// by each).
 template <int NL>
 TMD_HD bool block_coeffs(const CoeffJob& J, uint64_t M, int guard, const CoeffConsts& C, uint64_t* c,
-                         const Anchor* anchor = nullptr, const uint64_t* tables = nullptr) {
+                         const Anchor* anchor = nullptr, const uint64_t* tables = nullptr, int part = 0,
+                         int step = 1) {
     using namespace fx;
     const int W = 64 * J.L;
     const int E0 = W + J.scale_log2 + J.red;  // f(X_t) is enclosed as 2^red g
@@ -632,10 +639,10 @@ TMD_HD bool block_coeffs(const CoeffJob& J, uint64_t M, int guard, const CoeffCo
         cf_detail::rn_shift(f.lo, (unsigned)s);
         cf_detail::rn_shift(f.hi, (unsigned)s);
         if (!equal(f.lo, f.hi)) return false;
-        cf_detail::store_mod_w(f.lo, false, J.L, c);
+        if (part == 0) cf_detail::store_mod_w(f.lo, false, J.L, c);
         // the order-k coefficient's scale 2^(E0 + k (e_in - p)) times the
         // k-th power of the argument's 2^(p - e_in) leaves 2^E0 for every k
-        return cf_detail::log_orders<NL>(M, J.d, E0, C, J.L, c);
+        return cf_detail::log_orders<NL>(M, J.d, E0, C, J.L, c, part, step);
     }
     // exp or 2^x: the enclosure of f(X_t) has P2 = PB fractional bits
     const unsigned P2 = PB;
@@ -663,8 +670,9 @@ TMD_HD bool block_coeffs(const CoeffJob& J, uint64_t M, int guard, const CoeffCo
 #pragma unroll 1
     for (int k = 0; k <= COEFF_MAX_DEG; k++) {
         if (k > J.d) {
+            if (k % step == part)
 #pragma unroll
-            for (int l = 0; l < COEFF_MAX_LIMBS; l++) c[k * COEFF_MAX_LIMBS + l] = 0;
+                for (int l = 0; l < COEFF_MAX_LIMBS; l++) c[k * COEFF_MAX_LIMBS + l] = 0;
             continue;
         }
         if (J.func == 1 && k > 0) {
@@ -684,6 +692,7 @@ TMD_HD bool block_coeffs(const CoeffJob& J, uint64_t M, int guard, const CoeffCo
             }
             exact = false;
         }
+        if (k % step != part) continue;
         U<NL> lo = plo, hi = phi;
         if (k >= 2) {
             div_u64(lo, C.div.r[fact[k]]);
@@ -722,6 +731,7 @@ TMD_HD bool block_coeffs(const CoeffJob& J, uint64_t M, int guard, const CoeffCo
 //     Delta^w g1(0) = sum_{j>=w} b_j w! S(j, w).
 // Every step is a ring operation, so the words equal the differences of the
 // values mod 2^W exactly; N^j is a shift.  The coefficients above d are zero.
+// With step > 1 this thread writes the words w with w % step == part.
 namespace cf_detail {
 // acc += m x (mod 2^(64 COEFF_MAX_LIMBS)) for a small constant m
 TMD_HD void add_mul_small(fx::U<COEFF_MAX_LIMBS>& acc, const fx::U<COEFF_MAX_LIMBS>& x, uint32_t m) {
@@ -736,7 +746,7 @@ TMD_HD void add_mul_small(fx::U<COEFF_MAX_LIMBS>& acc, const fx::U<COEFF_MAX_LIM
 }
 }  // namespace cf_detail
 
-TMD_HD void block_table_words(const CoeffJob& J, const uint64_t* c, uint64_t* table) {
+TMD_HD void block_table_words(const CoeffJob& J, const uint64_t* c, uint64_t* table, int part = 0, int step = 1) {
     using namespace fx;
     using V = U<COEFF_MAX_LIMBS>;
     constexpr int D = COEFF_MAX_DEG;
@@ -768,6 +778,7 @@ TMD_HD void block_table_words(const CoeffJob& J, const uint64_t* c, uint64_t* ta
 #pragma unroll
     for (int w = 0; w <= D; w++) {
         if (w > d) break;
+        if (w % step != part) continue;
         V t;
         set_zero(t);
 #pragma unroll
@@ -779,6 +790,7 @@ TMD_HD void block_table_words(const CoeffJob& J, const uint64_t* c, uint64_t* ta
 #pragma unroll
     for (int w = 0; w < D; w++) {
         if (w >= d) break;
+        if ((d + 1 + w) % step != part) continue;
         V t;
         set_zero(t);
 #pragma unroll

@@ -1377,26 +1377,69 @@ __device__ __forceinline__ CoeffJob block_coeff_job(const DevJob& jb, int e_out)
 // enclosure and coefficient code, so a warp fetches less code (the kernel
 // waits on instruction fetches: the served 10k-job stream ran 1.4-1.6e14
 // args/s with one kernel for all three functions, 1.7-1.9e14 with three);
-// the blocks of the other functions return at once.
-template <int F>
+// the blocks of the other functions return at once.  LPB threads per block:
+// with few blocks (one wave of a few warps per SM) the kernel is bound by the
+// latency of each thread's serial multiword chain, so LPB = 4 consecutive
+// lanes share a block -- each forms f(X_t), rounds the orders k with k % 4
+// equal to its part and writes a quarter of the words, the coefficients
+// passing through shared memory -- and a block's table is kept only if all
+// four parts' roundings were decided.
+template <int F, int LPB>
 __global__ void __launch_bounds__(64) k_block_tables(const DevJob* jobs, const DevBlock* blocks, uint64_t n_blocks,
                                                      uint64_t* tables, uint32_t* status, const uint64_t* ctab) {
-    const uint64_t b = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (b >= n_blocks) return;
-    const DevBlock bk = blocks[b];
-    const DevJob jb = jobs[bk.job];
-    if (jb.func != F) return;
-    CoeffJob J = block_coeff_job(jb, bk.e_out);
-    J.func = F;
-    const uint64_t M = (1ull << (jb.p - 1)) + bk.start;
-    uint64_t c[(COEFF_MAX_DEG + 1) * COEFF_MAX_LIMBS];
-    // 384 bits with 32 guard bits below the coefficients' last place: an
-    // undecided rounding (odds ~2^-40 per coefficient) or a job whose words
-    // need more bits goes to k_block_tables_wide (512, then 768 bits)
-    const bool ok = block_coeffs<6>(J, M, 32, c_coeff, c, nullptr, ctab);
-    if (ok) block_table_words(J, c, tables + bk.table_off);
-    if (ok && (jb.flags & TMD_SOUND)) coeffs_packed(J, c, tables + bk.table_off + (2 * J.d + 1) * J.L);
-    status[b] = ok ? 0 : 1;
+    static_assert(LPB == 1 || LPB == 2 || LPB == 4, "a block's parts are consecutive lanes of one warp");
+    constexpr int NC = (COEFF_MAX_DEG + 1) * COEFF_MAX_LIMBS;
+    const uint64_t g = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (LPB == 1) {
+        const uint64_t b = g;
+        if (b >= n_blocks) return;
+        const DevBlock bk = blocks[b];
+        const DevJob jb = jobs[bk.job];
+        if (jb.func != F) return;
+        CoeffJob J = block_coeff_job(jb, bk.e_out);
+        J.func = F;
+        const uint64_t M = (1ull << (jb.p - 1)) + bk.start;
+        uint64_t c[NC];
+        // 384 bits with 32 guard bits below the coefficients' last place: an
+        // undecided rounding (odds ~2^-40 per coefficient) or a job whose
+        // words need more bits goes to k_block_tables_wide (512, then 768 bits)
+        const bool ok = block_coeffs<6>(J, M, 32, c_coeff, c, nullptr, ctab);
+        if (ok) block_table_words(J, c, tables + bk.table_off);
+        if (ok && (jb.flags & TMD_SOUND)) coeffs_packed(J, c, tables + bk.table_off + (2 * J.d + 1) * J.L);
+        status[b] = ok ? 0 : 1;
+        return;
+    }
+    __shared__ uint64_t sc[LPB > 1 ? 64 / LPB : 1][NC];
+    const uint64_t b = g / LPB;
+    const int part = (int)(g % LPB);
+    bool act = b < n_blocks;
+    DevBlock bk;
+    DevJob jb;
+    CoeffJob J;
+    if (act) {
+        bk = blocks[b];
+        jb = jobs[bk.job];
+        act = jb.func == F;
+    }
+    bool ok = false;
+    uint64_t* c = sc[threadIdx.x / LPB];
+    if (act) {
+        J = block_coeff_job(jb, bk.e_out);
+        J.func = F;
+        const uint64_t M = (1ull << (jb.p - 1)) + bk.start;
+        ok = block_coeffs<6>(J, M, 32, c_coeff, c, nullptr, ctab, part, LPB);
+    }
+    // every lane of the warp votes (inactive ones with ok = false): the vote
+    // must not sit behind a short-circuited condition
+    const unsigned vote = __ballot_sync(0xffffffffu, ok);
+    const unsigned lane = threadIdx.x & 31u;
+    const unsigned mine = ((1u << LPB) - 1u) << (lane & ~(unsigned)(LPB - 1));
+    const bool all_ok = act && (vote & mine) == mine;
+    __syncwarp();
+    if (all_ok) block_table_words(J, c, tables + bk.table_off, part, LPB);
+    if (all_ok && part == 0 && (jb.flags & TMD_SOUND))
+        coeffs_packed(J, c, tables + bk.table_off + (2 * J.d + 1) * J.L);
+    if (act && part == 0) status[b] = all_ok ? 0 : 1;
 }
 
 __global__ void __launch_bounds__(64) k_block_tables_wide(const DevJob* jobs, const DevBlock* blocks,
@@ -1439,15 +1482,27 @@ cudaError_t launch_coeff_tables(uint64_t* ctab, uint32_t* err, cudaStream_t s) {
 }
 
 // func_mask: bit f set when the plan holds blocks of function f
+// plans of up to this many blocks take four threads per block (16 k blocks:
+// 64 k threads, ~13 warps per SM)
+constexpr uint64_t TABLE_SPLIT_MAX_BLOCKS = 16384;
+
 cudaError_t launch_block_tables(const DevJob* jobs, const DevBlock* blocks, uint64_t n_blocks, uint64_t* tables,
                                 uint32_t* status, uint32_t* err, const uint64_t* ctab, uint32_t func_mask,
                                 cudaStream_t s) {
     if (n_blocks == 0) return cudaSuccess;
-    // 64-thread CTAs spread the (few, long) threads over more SMs
+    // 64-thread CTAs spread the (few, long) threads over more SMs; four
+    // threads per block while the plan is one wave of a few warps per SM
     const unsigned grid = (unsigned)((n_blocks + 63) / 64);
-    if (func_mask & 1u) k_block_tables<0><<<grid, 64, 0, s>>>(jobs, blocks, n_blocks, tables, status, ctab);
-    if (func_mask & 2u) k_block_tables<1><<<grid, 64, 0, s>>>(jobs, blocks, n_blocks, tables, status, ctab);
-    if (func_mask & 4u) k_block_tables<2><<<grid, 64, 0, s>>>(jobs, blocks, n_blocks, tables, status, ctab);
+    if (n_blocks <= TABLE_SPLIT_MAX_BLOCKS) {
+        const unsigned grid4 = (unsigned)((4 * n_blocks + 63) / 64);
+        if (func_mask & 1u) k_block_tables<0, 4><<<grid4, 64, 0, s>>>(jobs, blocks, n_blocks, tables, status, ctab);
+        if (func_mask & 2u) k_block_tables<1, 4><<<grid4, 64, 0, s>>>(jobs, blocks, n_blocks, tables, status, ctab);
+        if (func_mask & 4u) k_block_tables<2, 4><<<grid4, 64, 0, s>>>(jobs, blocks, n_blocks, tables, status, ctab);
+    } else {
+        if (func_mask & 1u) k_block_tables<0, 1><<<grid, 64, 0, s>>>(jobs, blocks, n_blocks, tables, status, ctab);
+        if (func_mask & 2u) k_block_tables<1, 1><<<grid, 64, 0, s>>>(jobs, blocks, n_blocks, tables, status, ctab);
+        if (func_mask & 4u) k_block_tables<2, 1><<<grid, 64, 0, s>>>(jobs, blocks, n_blocks, tables, status, ctab);
+    }
     k_block_tables_wide<<<grid, 64, 0, s>>>(jobs, blocks, n_blocks, tables, status, err, ctab);
     return cudaGetLastError();
 }

@@ -34,8 +34,14 @@ cudaError_t launch_block_tables(const DevJob* jobs, const DevBlock* blocks, uint
 cudaError_t launch_coeff_tables(uint64_t* ctab, uint32_t* err, cudaStream_t s);
 cudaError_t launch_plan(const DevJob* jobs, uint32_t n_jobs, DevBlock* blocks, uint64_t n_blocks,
                         const uint32_t* class_jobs, const uint64_t* class_task0, uint32_t n_entries,
-                        DevTask* tasks, uint64_t n_tasks, uint32_t* plan_err, cudaStream_t s);
+                        DevTask* tasks, uint64_t n_tasks, uint32_t* plan_err, uint64_t* misc, uint32_t n_misc,
+                        uint64_t* count, cudaStream_t s);
 cudaError_t launch_zero_counters(uint64_t* misc, uint32_t n_misc, uint64_t* count, cudaStream_t s);
+cudaError_t launch_readback(const uint64_t* count, const uint32_t* words, uint64_t* host, cudaStream_t s);
+cudaError_t launch_plan_inline(const InlinePlan& src, uint32_t n_words, uint64_t* arena, uint32_t n_jobs,
+                               uint64_t o_cjobs, uint64_t o_ctask, uint32_t n_entries, uint64_t o_blocks,
+                               uint64_t n_blocks, uint64_t o_tasks, uint64_t n_tasks, uint32_t* plan_err,
+                               uint64_t* misc, uint32_t n_misc, uint64_t* count, cudaStream_t s);
 }  // namespace tmd
 
 namespace tmd {
@@ -103,8 +109,10 @@ struct tmd_ctx {
     size_t stage_cap = 0;
     cudaEvent_t stage_done = nullptr;
     bool stage_pending = false;
-    // pinned landing words of the result read-back (count, error words)
+    // mapped pinned landing words of the result read-back (count, error
+    // words) and their device address
     uint64_t* h_small = nullptr;
+    uint64_t* d_small = nullptr;
     Plan plan;
     bool resident = false;
     uint64_t upload_bytes = 0;
@@ -450,13 +458,24 @@ void pack_plan(const Plan& P, const Layout& L, char* dst) {
 }
 
 // after the upload: blocks, tasks and tables on the device (unless host mode)
+// zero_misc / zero_count (optional): counters of the search that follows,
+// cleared by the planning kernel (not when the tables came from the host:
+// the caller clears them then).
+// inl (optional): the uploaded words, passed to the planning kernel as its
+// parameter instead of having been copied to d_arena.
 cudaError_t expand_plan(const Plan& P, const Layout& L, char* d_arena, uint32_t* plan_err, const uint64_t* ctab,
-                        cudaStream_t s) {
+                        cudaStream_t s, uint64_t* zero_misc = nullptr, uint32_t n_misc = 0,
+                        uint64_t* zero_count = nullptr, const InlinePlan* inl = nullptr) {
     if (P.host_tables) return cudaSuccess;
-    cudaError_t e = launch_plan((const DevJob*)d_arena, (uint32_t)P.jobs.size(), (DevBlock*)(d_arena + L.o_blocks),
-                                P.n_blocks, (const uint32_t*)(d_arena + L.o_cjobs),
-                                (const uint64_t*)(d_arena + L.o_ctask), (uint32_t)P.class_jobs.size(),
-                                (DevTask*)(d_arena + L.o_tasks), P.n_tasks, plan_err, s);
+    cudaError_t e =
+        inl ? launch_plan_inline(*inl, (uint32_t)(L.upload / sizeof(uint64_t)), (uint64_t*)d_arena,
+                                 (uint32_t)P.jobs.size(), L.o_cjobs, L.o_ctask, (uint32_t)P.class_jobs.size(),
+                                 L.o_blocks, P.n_blocks, L.o_tasks, P.n_tasks, plan_err, zero_misc, n_misc, zero_count,
+                                 s)
+            : launch_plan((const DevJob*)d_arena, (uint32_t)P.jobs.size(), (DevBlock*)(d_arena + L.o_blocks),
+                          P.n_blocks, (const uint32_t*)(d_arena + L.o_cjobs), (const uint64_t*)(d_arena + L.o_ctask),
+                          (uint32_t)P.class_jobs.size(), (DevTask*)(d_arena + L.o_tasks), P.n_tasks, plan_err,
+                          zero_misc, n_misc, zero_count, s);
     if (e != cudaSuccess) return e;
     uint32_t func_mask = 0;
     for (const DevJob& dj : P.jobs) func_mask |= 1u << (dj.func & 3);
@@ -465,10 +484,12 @@ cudaError_t expand_plan(const Plan& P, const Layout& L, char* d_arena, uint32_t*
                                func_mask, s);
 }
 
-// Arena layout: jobs | blocks | tasks | table status | tables.  The first
-// three sections are uploaded; the tables are uploaded when they were made
-// on the host, else written by the table kernel on the device.
-tmd_status upload_plan(tmd_ctx* c, cudaStream_t s) {
+// Arena layout: jobs | class job lists | class first tasks | blocks | tasks |
+// table status | tables.  The first three sections are uploaded (as the
+// planning kernel's parameter when they fit in it); the tables are uploaded
+// when they were made on the host, else written by the table kernel on the
+// device.
+tmd_status upload_plan(tmd_ctx* c, cudaStream_t s, uint64_t* zero_count, bool* zeroed) {
     Plan& P = c->plan;
     const Layout Lo = plan_layout(P);
     if (c->stage_pending) {
@@ -490,10 +511,18 @@ tmd_status upload_plan(tmd_ctx* c, cudaStream_t s) {
         CK(cudaMalloc((void**)&c->d_arena, cap));
         c->arena_cap = cap;
     }
-    pack_plan(P, Lo, c->h_stage);
-    CK(cudaMemcpyAsync(c->d_arena, c->h_stage, Lo.upload, cudaMemcpyHostToDevice, s));
-    CK(cudaEventRecord(c->stage_done, s));
-    c->stage_pending = true;
+    // a small plan's records travel as the planning kernel's parameter (no
+    // separate copy to wait for); larger ones through the pinned stage
+    const bool inline_upload = !P.host_tables && Lo.upload <= sizeof(InlinePlan);
+    InlinePlan inl;
+    if (inline_upload) {
+        pack_plan(P, Lo, (char*)inl.w);
+    } else {
+        pack_plan(P, Lo, c->h_stage);
+        CK(cudaMemcpyAsync(c->d_arena, c->h_stage, Lo.upload, cudaMemcpyHostToDevice, s));
+        CK(cudaEventRecord(c->stage_done, s));
+        c->stage_pending = true;
+    }
     c->upload_bytes = Lo.upload;
     c->off_jobs = 0;
     c->off_blocks = Lo.o_blocks;
@@ -501,7 +530,10 @@ tmd_status upload_plan(tmd_ctx* c, cudaStream_t s) {
     c->off_tasks = Lo.o_tasks;
     // the plan kernel clears the plan's error word; host-made tables have none
     if (P.host_tables) CK(cudaMemsetAsync(plan_err_ptr(c), 0, sizeof(uint32_t), s));
-    CK(expand_plan(P, Lo, c->d_arena, plan_err_ptr(c), c->d_ctab, s));
+    const bool z = zeroed && !P.host_tables;
+    CK(expand_plan(P, Lo, c->d_arena, plan_err_ptr(c), c->d_ctab, s, z ? c->d_misc : nullptr, z ? ST_COUNT + 1 : 0,
+                   z ? zero_count : nullptr, inline_upload ? &inl : nullptr));
+    if (zeroed) *zeroed = z;
     return TMD_OK;
 }
 
@@ -510,12 +542,16 @@ bool same_jobs(const tmd_ctx* c, const tmd_job* jobs, uint32_t njobs) {
     return memcmp(c->plan.key.data(), jobs, njobs * sizeof(tmd_job)) == 0;
 }
 
-tmd_status make_resident(tmd_ctx* c, const tmd_job* jobs, uint32_t njobs, cudaStream_t s) {
+// zeroed (optional): set when the planning kernel also cleared the search
+// counters and *zero_count (a fresh plan made on the device)
+tmd_status make_resident(tmd_ctx* c, const tmd_job* jobs, uint32_t njobs, cudaStream_t s,
+                         uint64_t* zero_count = nullptr, bool* zeroed = nullptr) {
+    if (zeroed) *zeroed = false;
     if (same_jobs(c, jobs, njobs)) return TMD_OK;
     c->resident = false;
     tmd_status st = build_plan(jobs, njobs, c->plan, /*host_tables=*/false);
     if (st != TMD_OK) return st;
-    st = upload_plan(c, s);
+    st = upload_plan(c, s, zero_count, zeroed);
     if (st != TMD_OK) return st;
     c->resident = true;
     return TMD_OK;
@@ -568,7 +604,8 @@ tmd_status tmd_create(tmd_ctx** out, int device) {
     c->device = device;
     if (cudaDeviceGetAttribute(&c->sms, cudaDevAttrMultiProcessorCount, device) != cudaSuccess ||
         cudaMalloc((void**)&c->d_misc, 64) != cudaSuccess ||
-        cudaHostAlloc((void**)&c->h_small, 64, cudaHostAllocDefault) != cudaSuccess ||
+        cudaHostAlloc((void**)&c->h_small, 64, cudaHostAllocMapped) != cudaSuccess ||
+        cudaHostGetDevicePointer((void**)&c->d_small, c->h_small, 0) != cudaSuccess ||
         cudaEventCreateWithFlags(&c->stage_done, cudaEventDisableTiming) != cudaSuccess) {
         tmd_destroy(c);
         return TMD_ECUDA;
@@ -696,10 +733,13 @@ tmd_status tmd_search(tmd_ctx* c, const tmd_job* jobs, uint32_t njobs, const voi
     if (!c || !jobs || njobs == 0 || !d_count || (cand_cap && !d_cand)) return TMD_EINVAL;
     cudaStream_t s = (cudaStream_t)stream;
     CK(cudaSetDevice(c->device));
-    tmd_status st = make_resident(c, jobs, njobs, s);
+    bool zeroed = false;
+    tmd_status st = make_resident(c, jobs, njobs, s, d_count, &zeroed);
     if (st != TMD_OK) return st;
-    st = reset_counters(c, d_count, s);
-    if (st != TMD_OK) return st;
+    if (!zeroed) {
+        st = reset_counters(c, d_count, s);
+        if (st != TMD_OK) return st;
+    }
     c->last_count = d_count;
     if (d_lin) {
         LineArgs a;
@@ -738,16 +778,14 @@ tmd_status tmd_candidates(tmd_ctx* c, const tmd_candidate* d_cand, const uint64_
     if (!c || !d_count || !n_out || (h_cap && !h_out)) return TMD_EINVAL;
     cudaStream_t s = (cudaStream_t)stream;
     CK(cudaSetDevice(c->device));
-    // two asynchronous copies into pinned words and one wait (copies to
-    // pageable memory would each wait for the stream)
-    uint64_t* hs = c->h_small;
-    CK(cudaMemcpyAsync(hs, d_count, sizeof(uint64_t), cudaMemcpyDeviceToHost, s));
-    CK(cudaMemcpyAsync(hs + 1, err_ptr(c), 3 * sizeof(uint32_t), cudaMemcpyDeviceToHost, s));
+    // one small kernel writes the count and the error words into mapped
+    // host memory, then one wait (copies to pageable memory would each wait
+    // for the stream)
+    volatile uint64_t* hs = c->h_small;
+    CK(launch_readback(d_count, err_ptr(c), c->d_small, s));
     CK(cudaStreamSynchronize(s));
     const uint64_t count = hs[0];
-    uint32_t words[3];
-    memcpy(words, hs + 1, sizeof words);
-    const uint32_t err = words[0], perr = words[2];  // words[1]: the queue head
+    const uint32_t err = (uint32_t)hs[1], perr = (uint32_t)hs[2];  // hs[1] >> 32: the queue head
     if (perr) return TMD_EUNSUPPORTED;
     *n_out = count;
     uint64_t n = std::min(count, std::min(cand_cap, h_cap));

@@ -97,7 +97,7 @@ TMD_HD void store_mod_w(const fx::U<NL>& x, bool neg, int L, uint64_t* out) {
 
 // c_k = (-1)^(k-1) 2^sh / (k M^k) rounded to nearest, mod 2^W, for k = 1..d
 // (halves rounded up for odd k and toward zero for even k), the slots above
-// d zeroed.  One chain of exact floors serves every order (floor(floor(a/b)
+// d zeroed; with step > 1 only the orders k = part (mod step).  One chain of exact floors serves every order (floor(floor(a/b)
 // / c) = floor(a/(bc))): y_k = floor(2^(sh+1) / M^k), F = floor(y_k / k) =
 // floor(2^(sh+1) / (k M^k)); the rounded value is F/2 for even F and
 // (F+1)/2 for odd F, less one at a tie (the division exact) for even k.
@@ -109,17 +109,20 @@ TMD_HD bool log_orders(uint64_t M, int d, int sh, const CoeffConsts& C, int L, u
     fx::U<NL> y;
     fx::set_pow2(y, (unsigned)sh + 1);
     bool exact = true;
+    int have = 0;  // y = floor(2^(sh+1) / M^have)
 #pragma unroll 1
-    for (int k = 1; k <= COEFF_MAX_DEG; k++) {
+    for (int k = part == 0 ? step : part; k <= COEFF_MAX_DEG; k += step) {
         if (k > d) {
-            if (k % step == part)
 #pragma unroll
-                for (int l = 0; l < COEFF_MAX_LIMBS; l++) c[k * COEFF_MAX_LIMBS + l] = 0;
+            for (int l = 0; l < COEFF_MAX_LIMBS; l++) c[k * COEFF_MAX_LIMBS + l] = 0;
             continue;
         }
-        const uint64_t ry = fx::div_u64(y, RM);
-        exact = exact && ry == 0;
-        if (k % step != part) continue;
+#pragma unroll 1
+        while (have < k) {
+            const uint64_t ry = fx::div_u64(y, RM);
+            exact = exact && ry == 0;
+            have++;
+        }
         fx::U<NL> F = y;
         const uint64_t rk = fx::div_u64(F, C.div.r[k]);
         const bool neg = (k % 2) == 0;
@@ -613,8 +616,8 @@ TMD_HD bool f_anchored(const CoeffJob& J, uint64_t M, unsigned PB, const CoeffCo
 // SM on small plans, wait on instruction fetches -- 44 against 63 us on the
 // 4096 blocks of a 2^36-argument slice.)  With step > 1 the caller splits
 // the orders over `step` threads: this one writes the slots of the orders k
-// with k % step == part (f(X_t), and the chains of 2^x and log, are formed
-// by each).
+// = part (mod step), every thread running the same code on its own order (f
+// and the chains of 2^x and log, up to its order, are formed by each).
 template <int NL>
 TMD_HD bool block_coeffs(const CoeffJob& J, uint64_t M, int guard, const CoeffConsts& C, uint64_t* c,
                          const Anchor* anchor = nullptr, const uint64_t* tables = nullptr, int part = 0,
@@ -667,15 +670,17 @@ TMD_HD bool block_coeffs(const CoeffJob& J, uint64_t M, int guard, const CoeffCo
             Bf2 = 2ull << (fb > P2 ? fb - P2 : 0);
         }
     }
+    int have = 0;  // factors of ln 2 applied to (plo, phi)
 #pragma unroll 1
-    for (int k = 0; k <= COEFF_MAX_DEG; k++) {
+    for (int k = part; k <= COEFF_MAX_DEG; k += step) {
         if (k > J.d) {
-            if (k % step == part)
 #pragma unroll
-                for (int l = 0; l < COEFF_MAX_LIMBS; l++) c[k * COEFF_MAX_LIMBS + l] = 0;
+            for (int l = 0; l < COEFF_MAX_LIMBS; l++) c[k * COEFF_MAX_LIMBS + l] = 0;
             continue;
         }
-        if (J.func == 1 && k > 0) {
+#pragma unroll 1
+        while (J.func == 1 && have < k) {
+            have++;
             U<NL> t;
             mul_shr(plo, l2lo, P2, t);
             plo = t;
@@ -692,7 +697,6 @@ TMD_HD bool block_coeffs(const CoeffJob& J, uint64_t M, int guard, const CoeffCo
             }
             exact = false;
         }
-        if (k % step != part) continue;
         U<NL> lo = plo, hi = phi;
         if (k >= 2) {
             div_u64(lo, C.div.r[fact[k]]);
@@ -731,7 +735,8 @@ TMD_HD bool block_coeffs(const CoeffJob& J, uint64_t M, int guard, const CoeffCo
 //     Delta^w g1(0) = sum_{j>=w} b_j w! S(j, w).
 // Every step is a ring operation, so the words equal the differences of the
 // values mod 2^W exactly; N^j is a shift.  The coefficients above d are zero.
-// With step > 1 this thread writes the words w with w % step == part.
+// With step > 1 this thread writes the words w = part (mod step), each by the
+// same code with its own constants (block_table_words_split).
 namespace cf_detail {
 // acc += m x (mod 2^(64 COEFF_MAX_LIMBS)) for a small constant m
 TMD_HD void add_mul_small(fx::U<COEFF_MAX_LIMBS>& acc, const fx::U<COEFF_MAX_LIMBS>& x, uint32_t m) {
@@ -746,7 +751,13 @@ TMD_HD void add_mul_small(fx::U<COEFF_MAX_LIMBS>& acc, const fx::U<COEFF_MAX_LIM
 }
 }  // namespace cf_detail
 
+TMD_HD void block_table_words_split(const CoeffJob& J, const uint64_t* c, uint64_t* table, int part, int step);
+
 TMD_HD void block_table_words(const CoeffJob& J, const uint64_t* c, uint64_t* table, int part = 0, int step = 1) {
+    if (step > 1) {
+        block_table_words_split(J, c, table, part, step);
+        return;
+    }
     using namespace fx;
     using V = U<COEFF_MAX_LIMBS>;
     constexpr int D = COEFF_MAX_DEG;
@@ -778,7 +789,6 @@ TMD_HD void block_table_words(const CoeffJob& J, const uint64_t* c, uint64_t* ta
 #pragma unroll
     for (int w = 0; w <= D; w++) {
         if (w > d) break;
-        if (w % step != part) continue;
         V t;
         set_zero(t);
 #pragma unroll
@@ -790,7 +800,6 @@ TMD_HD void block_table_words(const CoeffJob& J, const uint64_t* c, uint64_t* ta
 #pragma unroll
     for (int w = 0; w < D; w++) {
         if (w >= d) break;
-        if ((d + 1 + w) % step != part) continue;
         V t;
         set_zero(t);
 #pragma unroll
@@ -798,6 +807,54 @@ TMD_HD void block_table_words(const CoeffJob& J, const uint64_t* c, uint64_t* ta
 #pragma unroll
         for (int l = 0; l < COEFF_MAX_LIMBS; l++)
             if (l < L) table[(d + 1 + w) * L + l] = t.w[l];
+    }
+}
+
+// The words w = part (mod step) of block_table_words, every word by the same
+// code: the sums run over all j with the multipliers w! S(j, w) (zero for j <
+// w) read from packed constants, g0's or g1's coefficients selected per word.
+TMD_HD void block_table_words_split(const CoeffJob& J, const uint64_t* c, uint64_t* table, int part, int step) {
+    using namespace fx;
+    using V = U<COEFF_MAX_LIMBS>;
+    constexpr int D = COEFF_MAX_DEG;
+    static_assert(D == 4, "the constants below cover degrees up to 4");
+    // byte w of SURJ[j] is w! S(j, w)
+    constexpr uint64_t SURJ[D + 1] = {0x01ull, 0x0100ull, 0x020100ull, 0x06060100ull, 0x18240E0100ull};
+    constexpr uint32_t binom[D + 1][D + 1] = {
+        {1, 0, 0, 0, 0}, {1, 1, 0, 0, 0}, {1, 2, 1, 0, 0}, {1, 3, 3, 1, 0}, {1, 4, 6, 4, 1}};
+    const int L = J.L, d = J.d;
+    const unsigned lg = (unsigned)J.log2_N;
+    V ck[D + 1], a[D + 1], b[D + 1];
+#pragma unroll
+    for (int k = 0; k <= D; k++)
+#pragma unroll
+        for (int l = 0; l < COEFF_MAX_LIMBS; l++) ck[k].w[l] = c[k * COEFF_MAX_LIMBS + l];
+#pragma unroll
+    for (int j = 0; j <= D; j++) {
+        a[j] = ck[j];
+        shl(a[j], (unsigned)j * lg);
+        set_zero(b[j]);
+#pragma unroll
+        for (int k = j + 1; k <= D; k++) cf_detail::add_mul_small(b[j], ck[k], binom[k][j]);
+        shl(b[j], (unsigned)j * lg);
+    }
+#pragma unroll 1
+    for (int om = part; om <= 2 * d; om += step) {
+        const bool g0 = om <= d;
+        const unsigned w = (unsigned)(g0 ? om : om - d - 1);
+        V t;
+        set_zero(t);
+#pragma unroll
+        for (int j = 0; j <= D; j++) {
+            V x;
+#pragma unroll
+            for (int l = 0; l < COEFF_MAX_LIMBS; l++) x.w[l] = g0 ? a[j].w[l] : b[j].w[l];
+            mul_u64(x, (SURJ[j] >> (8u * w)) & 0xffu);
+            add(t, x);
+        }
+#pragma unroll
+        for (int l = 0; l < COEFF_MAX_LIMBS; l++)
+            if (l < L) table[om * L + l] = t.w[l];
     }
 }
 

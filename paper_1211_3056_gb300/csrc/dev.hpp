@@ -78,6 +78,14 @@ enum { ERR_BAD_LENGTH = 1, ERR_ROUNDING = 2 };
 enum { ST_LINES = 0, ST_FAIL = 1, ST_EXH = 2, ST_HALF = 3, ST_REF = 4, ST_COUNT = 5 };
 
 // Launch-side description of one fused/unfused launch.
+// The uploaded part of a small plan (job records, class lists) passed by
+// value as the planning kernel's parameter (3 KB, under the classic 4 KB
+// limit of kernel parameters) instead of a host-to-device copy.
+constexpr int INLINE_PLAN_WORDS = 384;
+struct InlinePlan {
+    uint64_t w[INLINE_PLAN_WORDS];
+};
+
 struct LaunchArgs {
     const DevJob* jobs;
     const DevBlock* blocks;

@@ -1297,16 +1297,20 @@ __global__ void __launch_bounds__(256) k_lower_bounds(const uint64_t* B, const u
 // and Sect. IV blocks: blocks of T arguments from each segment start, the
 // last one of a segment shorter; packets of nu sub-intervals per block).
 // One thread per block record and per task record (one launch for both);
-// thread 0 also clears the plan's error word before the table kernels run.
+// thread 0 also clears the plan's error word before the table kernels run,
+// and, when given, the first threads clear a search's counters (n_misc
+// statistics and error words and the candidate count).
 // Blocks: the last job whose first block is <= b.  Tasks are laid out class
 // by class (class_jobs lists the jobs of each (limbs, degree) class in
 // order; class_task0 their first task), 32 packets per task within a job.
-__global__ void __launch_bounds__(256) k_plan(const DevJob* jobs, uint32_t n_jobs, DevBlock* blocks, uint64_t n_blocks,
-                                              const uint32_t* class_jobs, const uint64_t* class_task0,
-                                              uint32_t n_entries, DevTask* tasks, uint64_t n_tasks,
-                                              uint32_t* plan_err) {
-    const uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+__device__ __forceinline__ void plan_records(uint64_t i, const DevJob* jobs, uint32_t n_jobs, DevBlock* blocks,
+                                             uint64_t n_blocks, const uint32_t* class_jobs,
+                                             const uint64_t* class_task0, uint32_t n_entries, DevTask* tasks,
+                                             uint64_t n_tasks, uint32_t* plan_err, uint64_t* misc, uint32_t n_misc,
+                                             uint64_t* count) {
     if (i == 0) *plan_err = 0;
+    if (misc && i < n_misc) misc[i] = 0;
+    if (count && i == 0) *count = 0;
     if (i < n_blocks) {
         uint32_t lo = 0, hi = n_jobs - 1;
         while (lo < hi) {
@@ -1326,12 +1330,55 @@ __global__ void __launch_bounds__(256) k_plan(const DevJob* jobs, uint32_t n_job
     }
 }
 
+__global__ void __launch_bounds__(256) k_plan(const DevJob* jobs, uint32_t n_jobs, DevBlock* blocks, uint64_t n_blocks,
+                                              const uint32_t* class_jobs, const uint64_t* class_task0,
+                                              uint32_t n_entries, DevTask* tasks, uint64_t n_tasks,
+                                              uint32_t* plan_err, uint64_t* misc, uint32_t n_misc,
+                                              uint64_t* count) {
+    const uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    plan_records(i, jobs, n_jobs, blocks, n_blocks, class_jobs, class_task0, n_entries, tasks, n_tasks, plan_err,
+                 misc, n_misc, count);
+}
+
+// The same with the uploaded part of a small plan (job records and class
+// lists, n_words words) passed as the kernel's parameter instead of copied
+// to the device first: the threads read the records from the parameter and
+// write them to the arena's start for the kernels that follow.
+__global__ void __launch_bounds__(256) k_plan_inline(const __grid_constant__ InlinePlan src, uint32_t n_words,
+                                                     uint64_t* arena, uint32_t n_jobs, uint64_t o_cjobs,
+                                                     uint64_t o_ctask, uint32_t n_entries, uint64_t o_blocks,
+                                                     uint64_t n_blocks, uint64_t o_tasks, uint64_t n_tasks,
+                                                     uint32_t* plan_err, uint64_t* misc, uint32_t n_misc,
+                                                     uint64_t* count) {
+    const uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n_words) arena[i] = src.w[i];
+    const char* base = (const char*)src.w;
+    char* a = (char*)arena;
+    plan_records(i, (const DevJob*)base, n_jobs, (DevBlock*)(a + o_blocks), n_blocks,
+                 (const uint32_t*)(base + o_cjobs), (const uint64_t*)(base + o_ctask), n_entries,
+                 (DevTask*)(a + o_tasks), n_tasks, plan_err, misc, n_misc, count);
+}
+
 cudaError_t launch_plan(const DevJob* jobs, uint32_t n_jobs, DevBlock* blocks, uint64_t n_blocks,
                         const uint32_t* class_jobs, const uint64_t* class_task0, uint32_t n_entries,
-                        DevTask* tasks, uint64_t n_tasks, uint32_t* plan_err, cudaStream_t s) {
+                        DevTask* tasks, uint64_t n_tasks, uint32_t* plan_err, uint64_t* misc, uint32_t n_misc,
+                        uint64_t* count, cudaStream_t s) {
     const uint64_t n = n_blocks > n_tasks ? n_blocks : n_tasks;
     k_plan<<<(unsigned)((n + 255) / 256 + (n == 0)), 256, 0, s>>>(jobs, n_jobs, blocks, n_blocks, class_jobs,
-                                                                   class_task0, n_entries, tasks, n_tasks, plan_err);
+                                                                   class_task0, n_entries, tasks, n_tasks, plan_err,
+                                                                   misc, n_misc, count);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_plan_inline(const InlinePlan& src, uint32_t n_words, uint64_t* arena, uint32_t n_jobs,
+                               uint64_t o_cjobs, uint64_t o_ctask, uint32_t n_entries, uint64_t o_blocks,
+                               uint64_t n_blocks, uint64_t o_tasks, uint64_t n_tasks, uint32_t* plan_err,
+                               uint64_t* misc, uint32_t n_misc, uint64_t* count, cudaStream_t s) {
+    uint64_t n = n_blocks > n_tasks ? n_blocks : n_tasks;
+    if (n < n_words) n = n_words;
+    k_plan_inline<<<(unsigned)((n + 255) / 256 + (n == 0)), 256, 0, s>>>(
+        src, n_words, arena, n_jobs, o_cjobs, o_ctask, n_entries, o_blocks, n_blocks, o_tasks, n_tasks, plan_err,
+        misc, n_misc, count);
     return cudaGetLastError();
 }
 
@@ -1341,6 +1388,21 @@ __global__ void k_zero_counters(uint64_t* misc, uint32_t n_misc, uint64_t* count
     const uint32_t i = threadIdx.x;
     if (i < n_misc) misc[i] = 0;
     if (i == 0 && count) *count = 0;
+}
+
+// The candidate count and three error words of a search into mapped host
+// memory (one launch and one wait instead of two copies).
+__global__ void k_readback(const uint64_t* count, const uint32_t* words, uint64_t* host) {
+    if (threadIdx.x == 0) {
+        host[0] = *count;
+        host[1] = (uint64_t)words[0] | ((uint64_t)words[1] << 32);
+        host[2] = words[2];
+    }
+}
+
+cudaError_t launch_readback(const uint64_t* count, const uint32_t* words, uint64_t* host, cudaStream_t s) {
+    k_readback<<<1, 32, 0, s>>>(count, words, host);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_zero_counters(uint64_t* misc, uint32_t n_misc, uint64_t* count, cudaStream_t s) {
@@ -1384,9 +1446,19 @@ __device__ __forceinline__ CoeffJob block_coeff_job(const DevJob& jb, int e_out)
 // equal to its part and writes a quarter of the words, the coefficients
 // passing through shared memory -- and a block's table is kept only if all
 // four parts' roundings were decided.
+// threads per CTA: 64 with four threads per block (small plans: one wave of
+// a few warps per SM, more SMs fetching the code in parallel), 256 with one
+// (large plans: several warps per scheduler share the fetched code; the
+// served groups' tables ran 0.85-0.97x the time of 64-thread CTAs)
+template <int LPB>
+__host__ __device__ constexpr int table_tpb() {
+    return LPB > 1 ? 64 : 256;
+}
+
 template <int F, int LPB>
-__global__ void __launch_bounds__(64) k_block_tables(const DevJob* jobs, const DevBlock* blocks, uint64_t n_blocks,
-                                                     uint64_t* tables, uint32_t* status, const uint64_t* ctab) {
+__global__ void __launch_bounds__(table_tpb<LPB>()) k_block_tables(const DevJob* jobs, const DevBlock* blocks,
+                                                            uint64_t n_blocks, uint64_t* tables, uint32_t* status,
+                                                            const uint64_t* ctab) {
     static_assert(LPB == 1 || LPB == 2 || LPB == 4, "a block's parts are consecutive lanes of one warp");
     constexpr int NC = (COEFF_MAX_DEG + 1) * COEFF_MAX_LIMBS;
     const uint64_t g = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -1409,7 +1481,7 @@ __global__ void __launch_bounds__(64) k_block_tables(const DevJob* jobs, const D
         status[b] = ok ? 0 : 1;
         return;
     }
-    __shared__ uint64_t sc[LPB > 1 ? 64 / LPB : 1][NC];
+    __shared__ uint64_t sc[LPB > 1 ? table_tpb<LPB>() / LPB : 1][NC];
     const uint64_t b = g / LPB;
     const int part = (int)(g % LPB);
     bool act = b < n_blocks;
@@ -1494,14 +1566,17 @@ cudaError_t launch_block_tables(const DevJob* jobs, const DevBlock* blocks, uint
     // threads per block while the plan is one wave of a few warps per SM
     const unsigned grid = (unsigned)((n_blocks + 63) / 64);
     if (n_blocks <= TABLE_SPLIT_MAX_BLOCKS) {
-        const unsigned grid4 = (unsigned)((4 * n_blocks + 63) / 64);
-        if (func_mask & 1u) k_block_tables<0, 4><<<grid4, 64, 0, s>>>(jobs, blocks, n_blocks, tables, status, ctab);
-        if (func_mask & 2u) k_block_tables<1, 4><<<grid4, 64, 0, s>>>(jobs, blocks, n_blocks, tables, status, ctab);
-        if (func_mask & 4u) k_block_tables<2, 4><<<grid4, 64, 0, s>>>(jobs, blocks, n_blocks, tables, status, ctab);
+        constexpr int T4 = table_tpb<4>();
+        const unsigned g4 = (unsigned)((4 * n_blocks + T4 - 1) / T4);
+        if (func_mask & 1u) k_block_tables<0, 4><<<g4, T4, 0, s>>>(jobs, blocks, n_blocks, tables, status, ctab);
+        if (func_mask & 2u) k_block_tables<1, 4><<<g4, T4, 0, s>>>(jobs, blocks, n_blocks, tables, status, ctab);
+        if (func_mask & 4u) k_block_tables<2, 4><<<g4, T4, 0, s>>>(jobs, blocks, n_blocks, tables, status, ctab);
     } else {
-        if (func_mask & 1u) k_block_tables<0, 1><<<grid, 64, 0, s>>>(jobs, blocks, n_blocks, tables, status, ctab);
-        if (func_mask & 2u) k_block_tables<1, 1><<<grid, 64, 0, s>>>(jobs, blocks, n_blocks, tables, status, ctab);
-        if (func_mask & 4u) k_block_tables<2, 1><<<grid, 64, 0, s>>>(jobs, blocks, n_blocks, tables, status, ctab);
+        constexpr int T1 = table_tpb<1>();
+        const unsigned g1 = (unsigned)((n_blocks + T1 - 1) / T1);
+        if (func_mask & 1u) k_block_tables<0, 1><<<g1, T1, 0, s>>>(jobs, blocks, n_blocks, tables, status, ctab);
+        if (func_mask & 2u) k_block_tables<1, 1><<<g1, T1, 0, s>>>(jobs, blocks, n_blocks, tables, status, ctab);
+        if (func_mask & 4u) k_block_tables<2, 1><<<g1, T1, 0, s>>>(jobs, blocks, n_blocks, tables, status, ctab);
     }
     k_block_tables_wide<<<grid, 64, 0, s>>>(jobs, blocks, n_blocks, tables, status, err, ctab);
     return cudaGetLastError();

@@ -244,8 +244,10 @@ tmd_status tmd_block_tables(const tmd_job* job, uint64_t block, uint64_t* coeffs
 
 /* ---- the three core calls ------------------------------------------------ */
 
-/* Stage 1: plan, correctly rounded block tables (host, multithreaded),
- * upload, and the generation kernel: packet starts by the straightforward
+/* Stage 1: plan (the host computes each job's segment table: output-binade
+ * cuts and prefix offsets; the device expands them into block and task
+ * records), the correctly rounded block tables (device kernels), and the
+ * generation kernel: packet starts by the straightforward
  * shift, then tabulated-difference stepping, writing the search words of
  * every sub-interval of every job (jobs in order, sub-intervals in plan
  * order) into d_lin as two arrays: B[n] then A[n] (uint64), where
@@ -255,7 +257,7 @@ tmd_status tmd_block_tables(const tmd_job* job, uint64_t block, uint64_t* coeffs
  * *lin_bytes_needed = 16 * total sub-intervals.  With d_lin == NULL or
  * lin_bytes too small only the size is reported (TMD_ENOMEM if d_lin was
  * given).  The plan and tables stay resident in the context for tmd_search.
- * Asynchronous on `stream` apart from the host table computation. */
+ * Asynchronous on `stream` apart from the host planning. */
 tmd_status tmd_generate(tmd_ctx* ctx, const tmd_job* jobs, uint32_t njobs,
                         void* d_lin, size_t lin_bytes, size_t* lin_bytes_needed,
                         void* stream);

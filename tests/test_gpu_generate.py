@@ -72,6 +72,35 @@ def test_batch_words_in_job_order(ctx):
     assert off == len(B)
 
 
+def test_table_forms_agree_and_match_oracle(ctx):
+    """Plans of up to 16 k blocks build their tables with four threads per
+    block, larger plans with one thread per block: the same jobs give the
+    same words in both.  The small plan mixes the three functions with a
+    block count that leaves warps partly filled (lanes of other functions
+    and past the plan's end share warps with working ones) and is checked
+    against the oracle too."""
+    small = [GEN_JOBS[1], GEN_JOBS[2],
+             wl.Job(wl.FUNC_EXP, 0, 53, 40, 14, 3, 24, 3, wl.plain_start(), 5 << 24), GEN_JOBS[4]]
+    big = wl.Job(wl.FUNC_EXP2, 0, 53, 40, 8, 2, 12, 1, 3 << 36, 1 << 27)    # 32768 blocks
+    n_small = sum(len(plan.blocks(j)) for j in small)
+    assert n_small <= 16384 and n_small % 8 != 0
+    assert n_small + len(plan.blocks(big)) > 16384
+    B1, A1 = generated_words(ctx, small)
+    B2, A2 = generated_words(ctx, small + [big])
+    n = len(B1)
+    assert (B2[:n] == B1).all() and (A2[:n] == A1).all()
+    off = 0
+    for job in small + [big]:
+        blocks = plan.blocks(job)
+        for b in sorted({0, len(blocks) - 1}):
+            _, ob, oa, _ = oc.block_lines(job, blocks[b])
+            s = off + blocks[b].first_sub
+            assert list(B2[s:s + len(ob)]) == list(ob), (job, b)
+            assert list(A2[s:s + len(oa)]) == list(oa), (job, b)
+        off += plan.n_subintervals(job)
+    assert off == len(B2)
+
+
 @pytest.mark.parametrize("fused", [True, False])
 def test_toy_candidates_exact(ctx, fused):
     job = wl.toy_job()

@@ -793,7 +793,8 @@ __device__ __forceinline__ Word<L> poly_at(const Word<L>* c, uint64_t y) {
 // cut into 32 pieces of n2 = ceil(N/32) arguments, one per lane; each lane
 // forms its piece's own line from the block polynomial (R_t at the piece
 // start and the next argument, the search words shifted by eps2) and keeps
-// the piece if its exact minimum is below 2 eps2 (phase 2).  Phase 3 takes
+// the piece if its exact minimum is below 2 eps2 (phase 2; Algorithm 4's
+// bound clears most pieces before the exact minimum is formed).  Phase 3 takes
 // the kept pieces one at a time with the whole warp.  A piece of more than
 // 64 arguments is first cut the same way into 32 sub-pieces of
 // ceil(n2/32) arguments, tested against their own half-width eps2s, and R_t
@@ -811,6 +812,11 @@ __device__ __forceinline__ bool piece_line_fails(const Word<L>& r0, Word<L> r1, 
     for (int l = 0; l + 1 < L; l++) low |= r1.l[l];
     const uint64_t B = r0.l[L - 1] + shift;
     const uint64_t A = ~r1.l[L - 1] + (low == 0 ? 1ull : 0ull);
+    // Algorithm 4's lower bound first: a piece whose bound reaches T cannot
+    // come within it (most pieces; the exact minimum costs several 64-bit
+    // divisions per level), the others are decided exactly
+    uint32_t hs;
+    if (cf_lower_bound(B, A, len, &hs) >= T) return false;
     uint32_t xm;
     return exact_min(B, A, len, &xm) < T;
 }

@@ -97,8 +97,9 @@ TMD_HD void store_mod_w(const fx::U<NL>& x, bool neg, int L, uint64_t* out) {
 
 // c_k = (-1)^(k-1) 2^sh / (k M^k) rounded to nearest, mod 2^W, for k = 1..d
 // (halves rounded up for odd k and toward zero for even k), the slots above
-// d zeroed; with step > 1 only the orders k = part (mod step).  One chain of exact floors serves every order (floor(floor(a/b)
-// / c) = floor(a/(bc))): y_k = floor(2^(sh+1) / M^k), F = floor(y_k / k) =
+// d zeroed; with step > 1 only the orders k = part (mod step).  One chain
+// of exact floors serves every order (floor(floor(a/b) / c) =
+// floor(a/(bc))): y_k = floor(2^(sh+1) / M^k), F = floor(y_k / k) =
 // floor(2^(sh+1) / (k M^k)); the rounded value is F/2 for even F and
 // (F+1)/2 for odd F, less one at a tie (the division exact) for even k.
 template <int NL>
@@ -358,9 +359,9 @@ TMD_HD void ct_load_lo(const uint64_t* tab, int base, int level, int b, fx::U<NL
 // left-aligned to 80 bits), f = e^n prod_i T(0, i, b_i) for exp and
 // 2^n prod_i T(1, i, b_i) for 2^x, the products formed at PA fractional bits
 // (below CT_LIMBS limbs the lower ends' product and a bound on its error,
-// at CT_LIMBS limbs both ends) and shifted to PB bits.  False when the tables do not apply (log, exp above
-// [2, 4), more than 80 fractional bits), so that the caller takes the
-// series.
+// at CT_LIMBS limbs both ends) and shifted to PB bits.  False when the
+// tables do not apply (log, exp above [2, 4), more than 80 fractional
+// bits), so that the caller takes the series.
 // log X for X = M 2^(e_in - p): with g = the top 9 bits of M (256 <= g <
 // 512), G = g 2^(p - 9), the next 8 bits h = floor((M - G) / (g 2^(p - 25)))
 // (h < 256; h = 0 for p < 25) and M' = G (1 + h 2^-16) = G + g h 2^(p - 25)

@@ -1530,7 +1530,8 @@ __global__ void __launch_bounds__(64) k_block_tables_wide(const DevJob* jobs, co
     const CoeffJob J = block_coeff_job(jb, bk.e_out);
     const uint64_t M = (1ull << (jb.p - 1)) + bk.start;
     uint64_t c[(COEFF_MAX_DEG + 1) * COEFF_MAX_LIMBS];
-    if (block_coeffs<8>(J, M, 64, c_coeff, c, nullptr, ctab) || block_coeffs<12>(J, M, 320, c_coeff, c, nullptr, ctab)) {
+    if (block_coeffs<8>(J, M, 64, c_coeff, c, nullptr, ctab) ||
+        block_coeffs<12>(J, M, 320, c_coeff, c, nullptr, ctab)) {
         block_table_words(J, c, tables + bk.table_off);
         if (jb.flags & TMD_SOUND) coeffs_packed(J, c, tables + bk.table_off + (2 * J.d + 1) * J.L);
         status[b] = 0;

@@ -278,24 +278,42 @@ struct Recip {
     unsigned sh;  // the shift
 };
 
-// v = floor(((2^64 - 1 - dn) 2^64 + 2^64 - 1) / dn) by shift-subtract
-// (the high word 2^64 - 1 - dn is below dn because dn >= 2^63)
+// v = floor((2^128 - 1) / dn) - 2^64 from a double-precision estimate and
+// exact integer corrections.  x = fl(2^64 / fl(dn)) has relative error
+// below 2^-52, so v0 = floor((x - 1) 2^64) is within 2^13 + 2 of v; from
+// v0 - 2^14 (not above v) the remainder r = 2^128 - 1 - (2^64 + v0) dn is
+// exact, non-negative and below 2^80; its quotient by dn, estimated in
+// double precision less one (never above the exact one), and at most a few
+// unit steps give v with 0 <= r < dn.
 TMD_HD Recip make_recip(uint64_t d) {
     Recip R;
     R.sh = (unsigned)clz64(d);
     R.dn = d << R.sh;
-    uint64_t rem = ~R.dn;  // 2^64 - 1 - dn < dn
-    uint64_t q = 0;
-    for (int i = 63; i >= 0; i--) {
-        const bool top = (rem >> 63) != 0;
-        rem = (rem << 1) | 1ull;  // next bit of the low word (all ones)
-        q <<= 1;
-        if (top || rem >= R.dn) {
-            rem -= R.dn;
-            q |= 1ull;
-        }
+    const uint64_t dn = R.dn;
+    const double two64 = 18446744073709551616.0;
+    const double x = two64 / (double)dn;  // in [1, 2]
+    const double e = (x - 1.0) * two64;   // exact scaling; below 2^64 + 2^13
+    uint64_t v = e >= 18446744073709549568.0 ? ~0ull : (uint64_t)e;  // 2^64 - 2^11
+    v = v > 16384 ? v - 16384 : 0;
+    // r = 2^128 - 1 - (2^64 + v) dn: the product's high word dn + hi(v dn)
+    // stays below 2^64 since v is not above the exact quotient
+    const uint64_t plo = v * dn, phi = mulhi(v, dn) + dn;
+    uint64_t rl = ~plo, rh = ~phi;
+    const double rd = (double)rh * two64 + (double)rl;
+    uint64_t del = (uint64_t)(rd / (double)dn);
+    del = del > 0 ? del - 1 : 0;
+    const uint64_t dlo = del * dn, dhi = mulhi(del, dn);
+    const uint64_t b = rl < dlo ? 1ull : 0ull;
+    rl -= dlo;
+    rh -= dhi + b;
+    v += del;
+#pragma unroll 1
+    for (int it = 0; it < 8 && (rh != 0 || rl >= dn); it++) {
+        rh -= rl < dn ? 1ull : 0ull;
+        rl -= dn;
+        v++;
     }
-    R.v = q;
+    R.v = v;
     return R;
 }
 

@@ -95,6 +95,22 @@ def test_plan_and_tables_match_oracle(job):
         assert tab == ot
 
 
+@pytest.mark.parametrize("log2_N", [2, 16])
+@pytest.mark.parametrize("limbs", [1, 2, 3])
+@pytest.mark.parametrize("d", [1, 2, 3, 4])
+def test_difference_words_every_degree_width_and_length(d, limbs, log2_N):
+    """The table words, formed from closed forms in the coefficients, equal
+    the forward differences of Horner values for every degree and word
+    width, at the shortest and a long sub-interval (N^j shifts past W)."""
+    job = wl.Job(wl.FUNC_EXP, 1, 53, 30, log2_N, d, max(log2_N, 18), limbs, 12345 << 18, 1 << 20)
+    ob = plan.blocks(job)
+    for b in sorted({0, len(ob) - 1}):
+        c, tab, _ = tmd.tmd_block_tables(job, b)
+        oc, ot = oracle_table(job, ob[b])
+        assert c == oc
+        assert tab == ot
+
+
 def test_toy_every_block_table():
     job = wl.toy_job()
     for b, blk in enumerate(plan.blocks(job)):
